@@ -1,0 +1,18 @@
+"""CPU oracle for tiled QR (thesis Chapter 3).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import anything under ``oracle/``.
+The library (``paper_1303_3182_gb300``) never imports it, and it imports nothing from
+the library; the two share only the seeded generators of ``synthetic``.
+
+* ``elimlists``  - the elimination-list generators, the validity conditions, the tile
+  task graph and its critical path (integer-exact).
+* ``householder`` - unblocked FP64 Householder QR, the four TT tile kernels applied one
+  reflector at a time, the tiled algorithm, apply-Q, back substitution, least squares.
+* ``refine``     - FP64 least-squares checks (backward error, residual).
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py`` (thesis tables,
+closed forms, brute force against unblocked QR and LAPACK), except the ASAP critical
+path of the 128 x 64 case, where the thesis prints 1748 and this oracle gives 1734
+(parity unpinned for that one cell; GrASAP does not depend on it).
+"""
