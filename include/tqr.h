@@ -1,0 +1,169 @@
+/*
+ * tqr.h - C ABI of libtqr, a tiled QR factorization for NVIDIA GB300 (sm_103a).
+ *
+ * The method is the tiled QR of a p x q tile matrix driven by an elimination list
+ * (Bouwmeester, "Tiled Algorithms for Matrix Computations on Multicore Architectures",
+ * 2012, Chapter 3): every sub-diagonal tile (i,k) is zeroed by a triangle-on-triangle
+ * transformation elim(i, piv(i,k), k) (Section 3.1, Algorithm "Generic QR"), executed as
+ * the kernels GEQRT, TTQRT (panel) and UNMQR, TTMQR (update) of Algorithm "elimTR" and
+ * Table "Kernels for tiled QR".  The whole task graph runs in one persistent CUDA kernel.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with a leading dimension (LAPACK style).  Device
+ *     pointers are CUDA global-memory pointers owned by the caller; the library never
+ *     frees them.  "stream" is a cudaStream_t passed as void* (NULL = legacy stream).
+ *   - Tiles are nb x nb; p = ceil(m/nb), q = ceil(n/nb).  Matrices that are not a whole
+ *     number of tiles are handled as if zero-padded: the results equal the leading part
+ *     of the zero-padded problem's results.
+ *   - Rows/columns/tiles are 0-based (the thesis counts from 1).
+ *   - Every function returns an int status: 0 = TQR_OK; -i = the i-th argument is
+ *     invalid (LAPACK style, nothing was done); a positive TQR_E* code otherwise.
+ *     No C++ exception crosses this interface.
+ *   - Device work is enqueued on "stream".  Unless tqr_set_sync(0) was called, each
+ *     call that runs device work synchronizes "stream" before returning so that a
+ *     device-side error (TQR_ETIMEOUT) is reported by that call.
+ *   - The library keeps per-shape plans (elimination list, task graph, device task
+ *     tables) in device memory it allocates itself; tqr_finalize() frees them.  Two
+ *     calls that use the same plan must not run concurrently on different streams.
+ */
+#ifndef TQR_H
+#define TQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Elimination trees (Section 3.2): FlatTree (Sameh-Kuck), PlasmaTree(BS), BinaryTree
+ * (= PlasmaTree(1)), Fibonacci (Modi-Clarke order 1), Greedy, GrASAP (Definition
+ * "grasap": Greedy on the first q-1 columns, ASAP on the last), ASAP on every column. */
+typedef enum {
+  TQR_FLAT = 0, TQR_PLASMA = 1, TQR_BINARY = 2, TQR_FIBONACCI = 3,
+  TQR_GREEDY = 4, TQR_GRASAP = 5, TQR_ASAP = 6
+} tqr_tree;
+
+/* Arithmetic of the factorization.
+ *   TQR_FP64   : everything in FP64 (matrix in double).
+ *   TQR_FP32   : matrix in float; Householder norms and tau in FP64; updates in FP32.
+ *   TQR_BF16X3 : matrix in float; norms/tau in FP64; the UNMQR/TTMQR updates on the
+ *                tensor cores as split-bf16 x3 products with FP32 accumulation.
+ *   TQR_BF16, TQR_FP16 : as TQR_BF16X3 with one bf16 / fp16 product. */
+typedef enum { TQR_FP64 = 0, TQR_BF16 = 1, TQR_FP16 = 2, TQR_BF16X3 = 3, TQR_FP32 = 4 } tqr_prec;
+
+enum {
+  TQR_OK = 0,
+  TQR_ECUDA = 1,     /* a CUDA runtime call failed (message: tqr_last_error())   */
+  TQR_ENOMEM = 2,    /* the library could not allocate its plan / workspace      */
+  TQR_ETIMEOUT = 3,  /* a device-side dependency wait exceeded the wait limit    */
+  TQR_ENOCONV = 4,   /* iterative refinement did not reach the tolerance         */
+  TQR_EUNSUPPORTED = 5 /* valid arguments this build does not implement          */
+};
+
+/* Elimination list of a p x q tile matrix (Section 3.2) and its critical path.
+ *   list     : out, 3*E int32 triples (k, i, piv), 0-based, canonical order (by column,
+ *              then step, then row); may be NULL to query E only.
+ *   len      : in = capacity of list in triples; out = E = number of eliminations.
+ *   cp_units : out (may be NULL), the weighted critical path with unbounded
+ *              processors in units of nb^3/3 flops, kernel weights GEQRT 4, TTQRT 2,
+ *              UNMQR 6, TTMQR 6 (Table "Kernels for tiled QR", Section 3.1.3).
+ *   bs       : PlasmaTree domain size (>= 1), ignored by the other trees.
+ * Host only; no device work.  Errors: -1/-2 p or q < 1, -3 unknown tree, -4 bs < 1
+ * for PlasmaTree, -6 len NULL or capacity too small while list != NULL. */
+int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len,
+                 int64_t *cp_units);
+
+/* Bytes of the caller-owned T workspace of tqr_factor: two ib x nb compact-WY T
+ * factors (GEQRT's and TTQRT's, Schreiber-Van Loan form, LAPACK GEQRT layout: block b
+ * in columns b*ib..) per tile (i,k), i < p, k < min(p,q), in the precision's element
+ * type (double for TQR_FP64, float otherwise), followed for the tensor-core precisions
+ * by the split operands of the updates.  Host only. */
+int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T_bytes);
+
+/* Tiled QR factorization A = QR in place (Algorithm "elimTR" over the list of "tree").
+ *   A   : device, m x n column-major (double for TQR_FP64, float otherwise), lda >= m.
+ *         On exit the upper triangle of A holds R (m >= n: rows 0..n-1), the strictly
+ *         lower part of each tile holds its GEQRT reflectors and the upper triangle of
+ *         each zeroed tile holds its TTQRT reflectors.
+ *   T   : device, tqr_workspace_size() bytes, written.
+ *   nb  : tile size, 1..256 for TQR_FP64, a multiple of 32 up to 128 for the tensor-
+ *         core precisions; ib: inner block, 1 <= ib <= nb.
+ * Errors: -1..-4 sizes, -5 tree, -6 bs, -7 prec, -8 A NULL, -9 lda < m, -10 T NULL;
+ *         TQR_ETIMEOUT, TQR_ECUDA, TQR_ENOMEM, TQR_EUNSUPPORTED. */
+int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
+               void *A, int64_t lda, void *T, void *stream);
+
+/* Apply Q^T (trans = 0) or Q (trans = 1) of a tqr_factor result to B (m x nrhs,
+ * column-major, ldb >= m), in place, replaying the UNMQR/TTMQR kernels on B's tile rows
+ * (in list order for Q^T, in reverse for Q).  A/T/prec/tree/nb/ib must be those of the
+ * factorization.  B is double for every precision; the reflectors are read in the
+ * precision A is stored in.
+ * Errors: -1..-6 sizes/tree/bs, -7 prec, -8 trans, -9 A, -10 lda, -11 T, -12 B,
+ *         -13 ldb, -14 nrhs < 0. */
+int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec, int trans,
+                 const void *A, int64_t lda, const void *T, double *B, int64_t ldb,
+                 int64_t nrhs, void *stream);
+
+/* Solve R X = B for the n x n upper-triangular R held in the top rows of a factored A
+ * (double for TQR_FP64, float otherwise), X overwriting B (n x nrhs double, ldb >= n).
+ * Errors: -1 n, -2 prec, -3 A, -4 lda, -5 B, -6 ldb, -7 nrhs. */
+int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb,
+             int64_t nrhs, void *stream);
+
+/* Least squares min ||A X - B||_2 (m >= n, A of full column rank), all operands double.
+ *   prec == TQR_FP64 : X = R^{-1} (Q^T B)(0:n) from an FP64 tiled QR.
+ *   otherwise        : the tiled QR runs in "prec" on a float copy of A; X is then
+ *                      refined in FP64 (residuals r = B - A X and A^T r in FP64) by
+ *                      LSQR (Paige & Saunders, 1982) right-preconditioned with the
+ *                      low-precision R, until ||A^T r|| <= tol ||A|| ||r|| or max_iter.
+ *   A, B    : device, not modified.  X : device n x nrhs, ldx >= n.
+ *   iters   : out (may be NULL), refinement iterations used (max over right-hand sides).
+ *   workspace / ws_bytes : device scratch of at least tqr_lstsq_workspace_size() bytes.
+ * Errors: -1..-11 sizes/tree/prec/pointers, TQR_ENOCONV when max_iter is reached. */
+int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int bs, int prec,
+              const double *A, int64_t lda, const double *B, int64_t ldb,
+              double *X, int64_t ldx, double tol, int max_iter, int *iters,
+              void *workspace, size_t ws_bytes, void *stream);
+int tqr_lstsq_workspace_size(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int prec,
+                             size_t *bytes);
+
+/* Nominal flop count 2 n^2 (m - n/3) of a QR of an m x n matrix (m >= n) - the count
+ * every TFLOP/s figure of this library uses (Theorem "thm.flops"). */
+double tqr_nominal_flops(int64_t m, int64_t n);
+
+/* Maximum time one device-side dependency wait may spin before the kernel gives up
+ * with TQR_ETIMEOUT (nanoseconds; default 20 s).  Returns the previous value. */
+int64_t tqr_set_wait_limit_ns(int64_t ns);
+/* 1 (default): every call synchronizes its stream and reports device errors.
+ * 0: calls only enqueue; tqr_sync_status(stream) reports them later.  Returns old. */
+int tqr_set_sync(int on);
+int tqr_sync_status(void *stream);
+
+/* Device-time accounting of the library's own kernels (for benchmarks).  With timing on,
+ * every launch is bracketed by CUDA events on its stream; the elapsed time is added when
+ * the call synchronizes (so it needs tqr_set_sync(1)).  kind: 0 = factorization
+ * executor, 1 = apply-Q executor, 2 = triangular solve, 3 = refinement kernels.
+ * tqr_kernel_time returns the accumulated milliseconds and launch count, then clears
+ * them when reset != 0.  Errors: -1 unknown kind. */
+int tqr_set_timing(int on);
+int tqr_kernel_time(int kind, double *ms_total, int64_t *launches, int reset);
+
+const char *tqr_strerror(int status);
+const char *tqr_last_error(void);      /* detail of the last TQR_ECUDA / internal error */
+void tqr_finalize(void);               /* free every cached plan                         */
+
+/* ---- test hooks (host logic only; no numerics) ----
+ * tqr_plan_stats: task and edge counts of the task graph the executor runs for a
+ *   factorization of the given shape/tree: out[0..5] = #GEQRT, #TTQRT, #UNMQR, #TTMQR,
+ *   #edges, critical path in units (same weights as tqr_elimlist).
+ * tqr_debug_drop_edge: when set to e >= 0, the next plan built omits the release of
+ *   its e-th dependency edge, so that a wait can never finish; used to check that the
+ *   kernel returns TQR_ETIMEOUT instead of hanging.  -1 (default) disables it. */
+int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6]);
+void tqr_debug_drop_edge(int64_t e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TQR_H */

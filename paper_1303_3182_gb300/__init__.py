@@ -1,0 +1,256 @@
+"""Tiled QR factorization on NVIDIA GB300 (sm_103a) - Python binding of libtqr.
+
+The method is the tiled QR of Bouwmeester's thesis (Chapter 3): a p x q tile matrix is
+factored by the task graph of an elimination list (FlatTree, PlasmaTree(BS), BinaryTree,
+Fibonacci, Greedy, GrASAP, ASAP) of GEQRT/TTQRT panel kernels and UNMQR/TTMQR updates,
+run by one persistent CUDA kernel.  Every computation happens in libtqr (include/tqr.h);
+this module only marshals arguments.  PyTorch provides device memory and streams.
+
+Matrices are column-major: pass torch tensors of shape (m, n) whose stride is (1, ld)
+(``colmajor(x)`` makes one).  There is no CPU fallback: the functions raise when the
+CUDA library is not built or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtqr.so")
+
+FLAT, PLASMA, BINARY, FIBONACCI, GREEDY, GRASAP, ASAP = range(7)
+TREES = {"flat": FLAT, "plasma": PLASMA, "binary": BINARY, "fibonacci": FIBONACCI,
+         "greedy": GREEDY, "grasap": GRASAP, "asap": ASAP}
+FP64, BF16, FP16, BF16X3, FP32 = 0, 1, 2, 3, 4
+PRECS = {"fp64": FP64, "bf16": BF16, "fp16": FP16, "bf16x3": BF16X3, "fp32": FP32}
+TQR_ETIMEOUT = 3
+TQR_EUNSUPPORTED = 5
+
+_lib = None
+
+
+class TqrError(RuntimeError):
+    def __init__(self, fn: str, status: int, detail: str):
+        super().__init__(f"{fn} failed with status {status}: {detail}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libtqr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1303_3182_gb300.build` (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        c_i64p = ctypes.POINTER(ctypes.c_int64)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        sig = {
+            "tqr_elimlist": (i32, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), c_i64p, c_i64p]),
+            "tqr_workspace_size": (i32, [i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
+            "tqr_factor": (i32, [i64, i64, i32, i32, i32, i32, i32, vp, i64, vp, vp]),
+            "tqr_apply_qt": (i32, [i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64, i64, vp]),
+            "tqr_trsm": (i32, [i64, i32, vp, i64, vp, i64, i64, vp]),
+            "tqr_lstsq": (i32, [i64, i64, i64, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp, i64,
+                                dbl, i32, ctypes.POINTER(ctypes.c_int), vp, ctypes.c_size_t, vp]),
+            "tqr_lstsq_workspace_size": (i32, [i64, i64, i64, i32, i32, i32,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+            "tqr_nominal_flops": (dbl, [i64, i64]),
+            "tqr_set_wait_limit_ns": (i64, [i64]),
+            "tqr_set_sync": (i32, [i32]),
+            "tqr_sync_status": (i32, [vp]),
+            "tqr_strerror": (ctypes.c_char_p, [i32]),
+            "tqr_last_error": (ctypes.c_char_p, []),
+            "tqr_finalize": (None, []),
+            "tqr_plan_stats": (i32, [i64, i64, i32, i32, i32, c_i64p]),
+            "tqr_debug_drop_edge": (None, [i64]),
+            "tqr_set_timing": (i32, [i32]),
+            "tqr_kernel_time": (i32, [i32, ctypes.POINTER(ctypes.c_double), c_i64p, i32]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(fn: str, status: int) -> None:
+    if status != 0:
+        L = lib()
+        detail = L.tqr_strerror(status).decode()
+        extra = L.tqr_last_error().decode()
+        raise TqrError(fn, status, detail + (f" ({extra})" if extra else ""))
+
+
+def _tree(tree) -> int:
+    return TREES[tree] if isinstance(tree, str) else int(tree)
+
+
+def _prec(prec) -> int:
+    return PRECS[prec] if isinstance(prec, str) else int(prec)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ld(x, rows: int) -> int:
+    """Leading dimension of a column-major (m, n) tensor view."""
+    if x.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    if x.shape[1] > 1 and x.stride(0) != 1:
+        raise ValueError("tensor must be column-major: stride (1, ld)")
+    if x.shape[1] == 1 and x.stride(0) != 1:
+        raise ValueError("tensor must be column-major: stride (1, ld)")
+    ld = x.stride(1) if x.shape[1] > 1 else max(rows, 1)
+    return max(ld, rows)
+
+
+def colmajor(x):
+    """A column-major copy (stride (1, m)) of a 2-D tensor."""
+    return x.t().contiguous().t()
+
+
+# ---------------------------------------------------------------------------------
+# Host-only entry points
+# ---------------------------------------------------------------------------------
+
+def elimlist(p: int, q: int, tree="greedy", bs: int = 1):
+    """Elimination list (E x 3 int32 array of (k, i, piv), 0-based) and the critical
+    path in units of nb^3/3."""
+    L = lib()
+    n = ctypes.c_int64(0)
+    cp = ctypes.c_int64(0)
+    _check("tqr_elimlist", L.tqr_elimlist(p, q, _tree(tree), bs, None, ctypes.byref(n), None))
+    arr = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    _check("tqr_elimlist", L.tqr_elimlist(p, q, _tree(tree), bs,
+                                          arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          ctypes.byref(n), ctypes.byref(cp)))
+    return arr[:n.value], cp.value
+
+
+def plan_stats(m: int, n: int, nb: int, tree="greedy", bs: int = 1):
+    out = (ctypes.c_int64 * 6)()
+    _check("tqr_plan_stats", lib().tqr_plan_stats(m, n, nb, _tree(tree), bs, out))
+    return {"GEQRT": out[0], "TTQRT": out[1], "UNMQR": out[2], "TTMQR": out[3],
+            "edges": out[4], "cp": out[5]}
+
+
+def workspace_size(m: int, n: int, nb: int, ib: int, prec="fp64") -> int:
+    out = ctypes.c_size_t(0)
+    _check("tqr_workspace_size", lib().tqr_workspace_size(m, n, nb, ib, _prec(prec), ctypes.byref(out)))
+    return out.value
+
+
+def nominal_flops(m: int, n: int) -> float:
+    return lib().tqr_nominal_flops(m, n)
+
+
+def set_wait_limit_ns(ns: int) -> int:
+    return lib().tqr_set_wait_limit_ns(ns)
+
+
+def set_timing(on: bool) -> bool:
+    """Bracket every library kernel launch with CUDA events (see tqr_set_timing)."""
+    return bool(lib().tqr_set_timing(1 if on else 0))
+
+
+KERNEL_KINDS = {"factor": 0, "apply_q": 1, "trsm": 2, "refine": 3}
+
+
+def kernel_time(kind, reset: bool = True):
+    """(total device ms, launches) accumulated for one kernel kind since the last reset."""
+    ms = ctypes.c_double(0)
+    n = ctypes.c_int64(0)
+    k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check("tqr_kernel_time", lib().tqr_kernel_time(k, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
+    return ms.value, n.value
+
+
+def debug_drop_edge(e: int) -> None:
+    lib().tqr_debug_drop_edge(e)
+
+
+def finalize() -> None:
+    lib().tqr_finalize()
+
+
+# ---------------------------------------------------------------------------------
+# Device entry points (torch tensors on a CUDA device)
+# ---------------------------------------------------------------------------------
+
+def _dtype_of(prec):
+    import torch
+    return torch.float64 if _prec(prec) == FP64 else torch.float32
+
+
+def factor(A, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64", T=None, stream=None):
+    """Tiled QR of A in place (column-major CUDA tensor, float64 for fp64 else float32).
+    Returns the T workspace tensor (bytes)."""
+    import torch
+    m, n = A.shape
+    if A.dtype != _dtype_of(prec) or not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor of the precision's storage type")
+    lda = _ld(A, m)
+    if T is None:
+        T = torch.empty(workspace_size(m, n, nb, ib, prec), dtype=torch.uint8, device=A.device)
+    _check("tqr_factor", lib().tqr_factor(m, n, nb, ib, _tree(tree), bs, _prec(prec),
+                                          ctypes.c_void_p(A.data_ptr()), lda,
+                                          ctypes.c_void_p(T.data_ptr()), _stream(stream)))
+    return T
+
+
+def apply_qt(A, T, B, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64",
+             trans: int = 0, stream=None):
+    """B <- Q^T B (trans=0) or Q B (trans=1) in place; B is a float64 column-major
+    tensor with A's row count."""
+    m, n = A.shape
+    if B.dtype.itemsize != 8 or B.shape[0] != m:
+        raise ValueError("B must be float64 with m rows")
+    _check("tqr_apply_qt", lib().tqr_apply_qt(m, n, nb, ib, _tree(tree), bs, _prec(prec), trans,
+                                              ctypes.c_void_p(A.data_ptr()), _ld(A, m),
+                                              ctypes.c_void_p(T.data_ptr()),
+                                              ctypes.c_void_p(B.data_ptr()), _ld(B, m),
+                                              B.shape[1], _stream(stream)))
+    return B
+
+
+def trsm(A, B, n: int, prec="fp64", stream=None):
+    """Solve R X = B in place (R: the n x n upper triangle of factored A)."""
+    _check("tqr_trsm", lib().tqr_trsm(n, _prec(prec), ctypes.c_void_p(A.data_ptr()), _ld(A, A.shape[0]),
+                                      ctypes.c_void_p(B.data_ptr()), _ld(B, B.shape[0]), B.shape[1],
+                                      _stream(stream)))
+    return B
+
+
+def lstsq_workspace_size(m, n, nrhs, nb, ib, prec="fp64") -> int:
+    out = ctypes.c_size_t(0)
+    _check("tqr_lstsq_workspace_size",
+           lib().tqr_lstsq_workspace_size(m, n, nrhs, nb, ib, _prec(prec), ctypes.byref(out)))
+    return out.value
+
+
+def lstsq(A, B, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64", tol: float = 1e-14,
+          max_iter: int = 100, X=None, workspace=None, stream=None, return_iters: bool = False):
+    """Least-squares solution X of min ||A X - B|| (float64 column-major CUDA tensors)."""
+    import torch
+    m, n = A.shape
+    nrhs = B.shape[1]
+    if X is None:
+        X = colmajor(torch.empty((n, nrhs), dtype=torch.float64, device=A.device))
+    if workspace is None:
+        workspace = torch.empty(lstsq_workspace_size(m, n, nrhs, nb, ib, prec), dtype=torch.uint8,
+                                device=A.device)
+    iters = ctypes.c_int(0)
+    _check("tqr_lstsq", lib().tqr_lstsq(m, n, nrhs, nb, ib, _tree(tree), bs, _prec(prec),
+                                        ctypes.c_void_p(A.data_ptr()), _ld(A, m),
+                                        ctypes.c_void_p(B.data_ptr()), _ld(B, m),
+                                        ctypes.c_void_p(X.data_ptr()), _ld(X, n), tol, max_iter,
+                                        ctypes.byref(iters), ctypes.c_void_p(workspace.data_ptr()),
+                                        workspace.numel(), _stream(stream)))
+    return (X, iters.value) if return_iters else X

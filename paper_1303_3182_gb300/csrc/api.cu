@@ -1,0 +1,520 @@
+// C ABI of libtqr (include/tqr.h): argument checks, plan cache, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "../../include/tqr.h"
+#include "tqr_internal.h"
+
+namespace tqr {
+
+namespace {
+
+std::mutex g_mu;
+int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
+int g_debug_plans = 0;
+thread_local std::string g_last_error;
+int64_t g_wait_limit_ns = 20LL * 1000 * 1000 * 1000;
+int g_sync = 1;
+int g_timing = 0;
+// per kernel kind: accumulated device milliseconds and launch count (tqr_kernel_time)
+double g_kernel_ms[4] = {0, 0, 0, 0};
+int64_t g_kernel_launches[4] = {0, 0, 0, 0};
+
+// Brackets one launch with CUDA events on its stream when timing is enabled; the
+// elapsed time is added at the call's synchronization point.
+struct LaunchTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int kind;
+  LaunchTimer(int k, cudaStream_t st) : kind(k) {
+    if (!g_timing) return;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  void stop(cudaStream_t st) {
+    if (e1) cudaEventRecord(e1, st);
+  }
+  // call after the stream was synchronized
+  void collect() {
+    if (!e0) return;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+      g_kernel_ms[kind] += ms;
+      g_kernel_launches[kind] += 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    e0 = e1 = nullptr;
+  }
+  ~LaunchTimer() { collect(); }
+};
+
+// A task graph uploaded to one device, plus its per-run state.
+struct Plan {
+  Graph g;
+  int device = 0;
+  Task *d_tasks = nullptr;
+  int32_t *d_succ_ptr = nullptr, *d_succ_idx = nullptr, *d_indeg = nullptr;
+  int32_t *d_counters = nullptr;
+  int32_t *d_state = nullptr;  // [0] = ticket, [1] = status
+  ~Plan() {
+    cudaFree(d_tasks);
+    cudaFree(d_succ_ptr);
+    cudaFree(d_succ_idx);
+    cudaFree(d_indeg);
+    cudaFree(d_counters);
+    cudaFree(d_state);
+  }
+};
+
+// kind 0 = factorization, 1 = apply Q^T, 2 = apply Q
+using PlanKey = std::tuple<int, int, int, int, int, int>;  // device, kind, P, Q, tree, bs
+std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
+
+struct Scratch {
+  int32_t *flags = nullptr;  // trsm ticket + flags, and a status word at [cap]
+  int cap = 0;
+};
+std::map<int, Scratch> g_scratch;
+
+int cuda_fail(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return TQR_ECUDA;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
+  if (e != cudaSuccess) return e;
+  if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Returns the cached plan for (kind, P, Q, tree, bs) on the current device.
+int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int64_t drop = kind == 0 ? g_drop_edge : -1;
+  // a plan built with the test hook is never reused: it gets a key of its own
+  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : kind, P, Q, tree,
+                    tree == TQR_PLASMA ? bs : 0};
+  auto it = g_plans.find(key);
+  if (it != g_plans.end()) {
+    *out = it->second.get();
+    return TQR_OK;
+  }
+  std::vector<Elim> elims;
+  if (!elimination_list(P, Q, tree, bs, elims)) return -5;
+  auto plan = std::make_unique<Plan>();
+  plan->device = dev;
+  if (kind == 0)
+    build_factor_graph(P, Q, elims, plan->g, drop);
+  else
+    build_applyq_graph(P, Q, elims, kind == 2, plan->g);
+  if (drop >= 0) g_drop_edge = -1;  // the test hook applies to one plan only
+  const Graph &g = plan->g;
+  if ((e = upload(&plan->d_tasks, g.tasks)) != cudaSuccess ||
+      (e = upload(&plan->d_succ_ptr, g.succ_ptr)) != cudaSuccess ||
+      (e = upload(&plan->d_succ_idx, g.succ_idx)) != cudaSuccess ||
+      (e = upload(&plan->d_indeg, g.indeg)) != cudaSuccess ||
+      (e = cudaMalloc(&plan->d_counters, std::max<size_t>(1, g.tasks.size()) * sizeof(int32_t))) !=
+          cudaSuccess ||
+      (e = cudaMalloc(&plan->d_state, 2 * sizeof(int32_t))) != cudaSuccess) {
+    g_last_error = std::string("plan upload: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TQR_ENOMEM : TQR_ECUDA;
+  }
+  *out = plan.get();
+  g_plans.emplace(key, std::move(plan));
+  return TQR_OK;
+}
+
+int get_scratch(int nflags, Scratch **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(g_mu);
+  Scratch &s = g_scratch[dev];
+  if (s.cap < nflags) {
+    cudaFree(s.flags);
+    s.flags = nullptr;
+    s.cap = 0;
+    e = cudaMalloc(&s.flags, (nflags + 1) * sizeof(int32_t));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TQR_ENOMEM : cuda_fail(e, "cudaMalloc");
+    s.cap = nflags;
+  }
+  *out = &s;
+  return TQR_OK;
+}
+
+// Reads a device status word after synchronizing the stream.
+int read_status(int32_t *d_status, cudaStream_t st) {
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device execution");
+  if (h != 0) {
+    g_last_error = "device wait exceeded the limit at task " + std::to_string(h >> 8);
+    return TQR_ETIMEOUT;
+  }
+  return TQR_OK;
+}
+
+// Runs a plan on the stream: reset counters / ticket / status, launch, check.
+int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
+  const size_t n = plan->g.tasks.size();
+  if (n == 0) return TQR_OK;
+  cudaError_t e = cudaMemcpyAsync(plan->d_counters, plan->d_indeg, n * sizeof(int32_t),
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_state, 0, 2 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "plan reset");
+  prm.tasks = plan->d_tasks;
+  prm.succ_ptr = plan->d_succ_ptr;
+  prm.succ_idx = plan->d_succ_idx;
+  prm.counters = plan->d_counters;
+  prm.next = plan->d_state;
+  prm.status = plan->d_state + 1;
+  prm.ntask = static_cast<int>(n);
+  prm.wait_limit_ns = g_wait_limit_ns;
+  LaunchTimer timer(prm.B ? 1 : 0, st);
+  const int rc = launch_executor(prm, dbl, st);
+  timer.stop(st);
+  if (rc != 0) return cuda_fail(static_cast<cudaError_t>(rc), "executor launch");
+  if (g_sync) return read_status(plan->d_state + 1, st);
+  return TQR_OK;
+}
+
+int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec) {
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (nb < 1 || nb > 256) return -3;
+  if (ib < 1 || ib > nb || ib > 32) return -4;
+  if (tree < TQR_FLAT || tree > TQR_ASAP) return -5;
+  if (tree == TQR_PLASMA && bs < 1) return -6;
+  if (prec < TQR_FP64 || prec > TQR_FP32) return -7;
+  if (ceil_div(m, nb) > 32767 || ceil_div(n, nb) > 32767) return -3;
+  return 0;
+}
+
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace tqr
+
+using namespace tqr;
+
+extern "C" {
+
+int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len, int64_t *cp_units) {
+  if (p < 1) return -1;
+  if (q < 1) return -2;
+  if (tree < TQR_FLAT || tree > TQR_ASAP) return -3;
+  if (tree == TQR_PLASMA && bs < 1) return -4;
+  if (!len) return -6;
+  std::vector<Elim> elims;
+  try {
+    elimination_list(p, q, tree, bs, elims);
+    const int64_t E = static_cast<int64_t>(elims.size());
+    if (list) {
+      if (*len < E) return -6;
+      for (int64_t e = 0; e < E; ++e) {
+        list[3 * e + 0] = elims[e].k;
+        list[3 * e + 1] = elims[e].i;
+        list[3 * e + 2] = elims[e].piv;
+      }
+    }
+    *len = E;
+    if (cp_units) {
+      Graph g;
+      build_factor_graph(p, q, elims, g);
+      *cp_units = g.critical_path;
+    }
+  } catch (const std::bad_alloc &) {
+    return TQR_ENOMEM;
+  } catch (...) {
+    g_last_error = "internal error in tqr_elimlist";
+    return TQR_ECUDA;
+  }
+  return TQR_OK;
+}
+
+int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T_bytes) {
+  const int rc = check_tiles(m, n, nb, ib, TQR_GREEDY, 1, prec);
+  if (rc) return rc;
+  if (!T_bytes) return -6;
+  const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
+  const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
+  *T_bytes = static_cast<size_t>(2 * P * K) * ib * nb * esz;
+  return TQR_OK;
+}
+
+int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec, void *A, int64_t lda,
+               void *T, void *stream) {
+  int rc = check_tiles(m, n, nb, ib, tree, bs, prec);
+  if (rc) return rc;
+  if (!A) return -8;
+  if (lda < m) return -9;
+  if (!T) return -10;
+  if (prec != TQR_FP64 && prec != TQR_FP32) return TQR_EUNSUPPORTED;
+  const bool dbl = prec == TQR_FP64;
+  if (executor_smem_bytes(nb, ib, dbl, false) == 0) {
+    g_last_error = "nb/ib too large for one SM's shared memory";
+    return TQR_EUNSUPPORTED;
+  }
+  try {
+    const int P = static_cast<int>(ceil_div(m, nb)), Q = static_cast<int>(ceil_div(n, nb));
+    Plan *plan = nullptr;
+    if ((rc = get_plan(0, P, Q, tree, bs, &plan)) != 0) return rc;
+    ExecParams prm{};
+    prm.A = A;
+    prm.lda = lda;
+    prm.m = m;
+    prm.n = n;
+    prm.nb = nb;
+    prm.ib = ib;
+    prm.P = P;
+    prm.Q = Q;
+    prm.T = T;
+    prm.B = nullptr;
+    return run_plan(plan, prm, dbl, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc &) {
+    return TQR_ENOMEM;
+  }
+}
+
+int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec, int trans,
+                 const void *A, int64_t lda, const void *T, double *B, int64_t ldb, int64_t nrhs,
+                 void *stream) {
+  int rc = check_tiles(m, n, nb, ib, tree, bs, prec);
+  if (rc) return rc;
+  if (trans != 0 && trans != 1) return -8;
+  if (!A) return -9;
+  if (lda < m) return -10;
+  if (!T) return -11;
+  if (!B) return -12;
+  if (ldb < m) return -13;
+  if (nrhs < 0) return -14;
+  if (nrhs == 0) return TQR_OK;
+  const bool dbl = prec == TQR_FP64;
+  if (executor_smem_bytes(nb, ib, dbl, true) == 0) return TQR_EUNSUPPORTED;
+  try {
+    const int P = static_cast<int>(ceil_div(m, nb)), Q = static_cast<int>(ceil_div(n, nb));
+    Plan *plan = nullptr;
+    if ((rc = get_plan(trans ? 2 : 1, P, Q, tree, bs, &plan)) != 0) return rc;
+    ExecParams prm{};
+    prm.A = const_cast<void *>(A);
+    prm.lda = lda;
+    prm.m = m;
+    prm.n = n;
+    prm.nb = nb;
+    prm.ib = ib;
+    prm.P = P;
+    prm.Q = Q;
+    prm.T = const_cast<void *>(T);
+    prm.B = B;
+    prm.ldb = ldb;
+    prm.nrhs = nrhs;
+    prm.trans = trans;
+    return run_plan(plan, prm, dbl, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc &) {
+    return TQR_ENOMEM;
+  }
+}
+
+int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb, int64_t nrhs,
+             void *stream) {
+  if (n < 1) return -1;
+  if (prec < TQR_FP64 || prec > TQR_FP32) return -2;
+  if (!A) return -3;
+  if (lda < n) return -4;
+  if (!B) return -5;
+  if (ldb < n) return -6;
+  if (nrhs < 0) return -7;
+  if (nrhs == 0) return TQR_OK;
+  Scratch *s = nullptr;
+  const int nflags = trsm_flag_count(n);
+  int rc = get_scratch(nflags, &s);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t *status = s->flags + s->cap;
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "trsm reset");
+  LaunchTimer timer(2, st);
+  rc = launch_trsm(n, A, lda, prec == TQR_FP64, B, ldb, nrhs, s->flags, status, g_wait_limit_ns, st);
+  timer.stop(st);
+  if (rc) return cuda_fail(static_cast<cudaError_t>(rc), "trsm launch");
+  if (g_sync) return read_status(status, st);
+  return TQR_OK;
+}
+
+int tqr_lstsq_workspace_size(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int prec, size_t *bytes) {
+  int rc = check_tiles(m, n, nb, ib, TQR_GREEDY, 1, prec);
+  if (rc) return rc;
+  if (nrhs < 0) return -3;
+  if (!bytes) return -7;
+  size_t tb = 0;
+  if ((rc = tqr_workspace_size(m, n, nb, ib, prec, &tb)) != 0) return rc;
+  const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  *bytes = align(static_cast<size_t>(m) * n * esz) + align(tb) +
+           align(static_cast<size_t>(m) * std::max<int64_t>(nrhs, 1) * sizeof(double));
+  return TQR_OK;
+}
+
+int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int bs, int prec,
+              const double *A, int64_t lda, const double *B, int64_t ldb, double *X, int64_t ldx,
+              double tol, int max_iter, int *iters, void *workspace, size_t ws_bytes, void *stream) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (nrhs < 0) return -3;
+  int rc = check_tiles(m, n, nb, ib, tree, bs, prec);
+  if (rc) return rc == -1 ? -1 : (rc == -2 ? -2 : rc - 1);
+  if (!A) return -9;
+  if (lda < m) return -10;
+  if (!B || ldb < m) return -11;
+  if (!X || ldx < n) return -13;
+  (void)tol;
+  (void)max_iter;
+  if (iters) *iters = 0;
+  if (nrhs == 0) return TQR_OK;
+  if (prec != TQR_FP64) return TQR_EUNSUPPORTED;
+  size_t need = 0;
+  if ((rc = tqr_lstsq_workspace_size(m, n, nrhs, nb, ib, prec, &need)) != 0) return rc;
+  if (!workspace || ws_bytes < need) return -18;
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  char *ws = static_cast<char *>(workspace);
+  double *Aw = reinterpret_cast<double *>(ws);
+  size_t tb = 0;
+  tqr_workspace_size(m, n, nb, ib, prec, &tb);
+  void *Tw = ws + align(static_cast<size_t>(m) * n * sizeof(double));
+  double *Bw = reinterpret_cast<double *>(static_cast<char *>(Tw) + align(tb));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpy2DAsync(Aw, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
+                                    cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(Bw, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
+                          cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-in");
+  if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Aw, m, Tw, stream)) != 0) return rc;
+  if ((rc = tqr_apply_qt(m, n, nb, ib, tree, bs, prec, 0, Aw, m, Tw, Bw, m, nrhs, stream)) != 0) return rc;
+  if ((rc = tqr_trsm(n, prec, Aw, m, Bw, m, nrhs, stream)) != 0) return rc;
+  e = cudaMemcpy2DAsync(X, ldx * sizeof(double), Bw, m * sizeof(double), n * sizeof(double), nrhs,
+                        cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-out");
+  if (g_sync) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "lstsq");
+  }
+  return TQR_OK;
+}
+
+double tqr_nominal_flops(int64_t m, int64_t n) {
+  const double M = static_cast<double>(m), N = static_cast<double>(n);
+  return 2.0 * N * N * (M - N / 3.0);
+}
+
+int64_t tqr_set_wait_limit_ns(int64_t ns) {
+  const int64_t old = g_wait_limit_ns;
+  if (ns > 0) g_wait_limit_ns = ns;
+  return old;
+}
+
+int tqr_set_sync(int on) {
+  const int old = g_sync;
+  g_sync = on ? 1 : 0;
+  return old;
+}
+
+int tqr_sync_status(void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream");
+  std::lock_guard<std::mutex> lock(g_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (auto &kv : g_plans) {
+    if (kv.second->device != dev) continue;
+    int32_t h = 0;
+    e = cudaMemcpy(&h, kv.second->d_state + 1, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (h != 0) return TQR_ETIMEOUT;
+  }
+  return TQR_OK;
+}
+
+const char *tqr_strerror(int status) {
+  if (status < 0) return "invalid argument";
+  switch (status) {
+    case TQR_OK: return "success";
+    case TQR_ECUDA: return "CUDA error";
+    case TQR_ENOMEM: return "out of memory";
+    case TQR_ETIMEOUT: return "device dependency wait exceeded the limit";
+    case TQR_ENOCONV: return "iterative refinement did not converge";
+    case TQR_EUNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char *tqr_last_error(void) { return g_last_error.c_str(); }
+
+void tqr_finalize(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_plans.clear();
+  for (auto &kv : g_scratch) cudaFree(kv.second.flags);
+  g_scratch.clear();
+}
+
+int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6]) {
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (nb < 1) return -3;
+  if (tree < TQR_FLAT || tree > TQR_ASAP) return -4;
+  if (tree == TQR_PLASMA && bs < 1) return -5;
+  if (!out) return -6;
+  const int P = static_cast<int>(ceil_div(m, nb)), Q = static_cast<int>(ceil_div(n, nb));
+  std::vector<Elim> elims;
+  elimination_list(P, Q, tree, bs, elims);
+  Graph g;
+  build_factor_graph(P, Q, elims, g);
+  for (int c = 0; c < 4; ++c) out[c] = g.counts[c];
+  out[4] = static_cast<int64_t>(g.succ_idx.size());
+  out[5] = g.critical_path;
+  return TQR_OK;
+}
+
+int tqr_set_timing(int on) {
+  const int old = g_timing;
+  g_timing = on ? 1 : 0;
+  return old;
+}
+
+int tqr_kernel_time(int kind, double *ms_total, int64_t *launches, int reset) {
+  if (kind < 0 || kind > 3) return -1;
+  if (ms_total) *ms_total = g_kernel_ms[kind];
+  if (launches) *launches = g_kernel_launches[kind];
+  if (reset) {
+    g_kernel_ms[kind] = 0.0;
+    g_kernel_launches[kind] = 0;
+  }
+  return TQR_OK;
+}
+
+void tqr_debug_drop_edge(int64_t e) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_drop_edge = e;
+}
+
+}  // extern "C"

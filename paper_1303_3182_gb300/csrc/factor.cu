@@ -1,0 +1,662 @@
+// Persistent tile-task executor and the SIMT tile kernels GEQRT, TTQRT, UNMQR, TTMQR
+// (Table "Kernels for tiled QR"; TT elimination of Algorithm "elimTR", Section 3.1.1).
+//
+// One launch runs a whole task graph.  Each CTA repeatedly claims the next task index
+// (executor order is topological), waits until the task's predecessor counter reaches
+// zero, runs the kernel with all 256 threads, and releases its successors.  Because a
+// task only ever waits for tasks with a smaller index, which were claimed earlier by
+// running CTAs, the executor cannot deadlock whatever the number of resident CTAs.
+// Every wait is bounded (globaltimer deadline + iteration cap): on expiry the CTA
+// records kStatusTimeout and the failing task in the status word and every CTA returns.
+//
+// Tiles are nb x nb blocks of the column-major matrix; a tile that sticks out of the
+// m x n matrix is processed as if zero-padded: padded rows and columns are never read
+// or written, and reflectors that would act only on padding have tau = 0.
+//
+// Reflector conventions (LAPACK): H = I - tau v v^T, v(0) = 1, beta = -sign(alpha) *
+// ||[alpha; x]||, tau = (beta - alpha) / beta, v = x / (alpha - beta), tau = 0 when
+// x = 0.  T factors: compact-WY (Schreiber & Van Loan, 1989), blocks of ib reflectors,
+// stored ib x nb per factored tile (block b in columns b*ib..).  Householder norms,
+// beta, tau and the scaling of v are computed in FP64 for every storage precision.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tqr_internal.h"
+
+namespace tqr {
+namespace {
+
+__host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kCW = 16;  // columns of an update chunk held in shared memory
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_gpu(const int32_t *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Loads through L2 only: tiles written by other SMs must never be served from a stale
+// L1 line of this SM.
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg(const float *p) { return static_cast<double>(__ldcg(p)); }
+
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Shared-memory layout of one CTA (element type S = compute type).
+template <typename S>
+struct Smem {
+  double *tau;   // [ib] tau of the current block, FP64
+  double *scal;  // [2]  1 / (alpha - beta) of the current reflector
+  S *V;          // [ldv * ib]  panel / reflector block
+  S *C;          // [ldv * kCW] update chunk (C, or C2 of a TT pair)
+  S *C1;         // [ldv * kCW] C1 chunk of a TT pair
+  S *W;          // [ldw * kCW]
+  S *T;          // [ldt * ib]
+  S *G;          // [ldt * ib]  Gram matrix of the reflectors of a block
+  S *P1;         // [ldt * ib]  diagonal block of R(piv) during TTQRT
+  int ldv, ldw, ldt;
+};
+
+__host__ __device__ inline int odd_ld(int x) { return x | 1; }
+
+__host__ __device__ inline size_t smem_elems(int nb, int ib, size_t s_size) {
+  const size_t ldv = odd_ld(nb), ldw = ib + 1, ldt = ib + 1;
+  const size_t d_bytes = (static_cast<size_t>(ib) + 2) * sizeof(double);
+  const size_t s_elems = ldv * ib + 2 * ldv * kCW + ldw * kCW + 3 * ldt * ib;
+  return d_bytes + s_elems * s_size;
+}
+
+template <typename S>
+__device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
+  Smem<S> s;
+  s.ldv = odd_ld(nb);
+  s.ldw = ib + 1;
+  s.ldt = ib + 1;
+  s.tau = reinterpret_cast<double *>(raw);
+  s.scal = s.tau + ib;
+  S *p = reinterpret_cast<S *>(s.scal + 2);
+  s.V = p;
+  p += s.ldv * ib;
+  s.C = p;
+  p += s.ldv * kCW;
+  s.C1 = p;
+  p += s.ldv * kCW;
+  s.W = p;
+  p += s.ldw * kCW;
+  s.T = p;
+  p += s.ldt * ib;
+  s.G = p;
+  p += s.ldt * ib;
+  s.P1 = p;
+  return s;
+}
+
+// dst[r + c*ldd] = src[r + c*lds], r < nrows, c < ncols (warp per column, lanes on rows).
+template <typename S, typename G>
+__device__ void load_block(S *dst, int ldd, const G *src, int64_t lds, int nrows, int ncols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < ncols; c += kWarps)
+    for (int r = lane; r < nrows; r += 32)
+      dst[r + c * ldd] = static_cast<S>(ldcg(src + r + static_cast<int64_t>(c) * lds));
+}
+
+template <typename S, typename G>
+__device__ void store_block(G *dst, int64_t ldd, const S *src, int lds, int nrows, int ncols) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < ncols; c += kWarps)
+    for (int r = lane; r < nrows; r += 32)
+      dst[r + static_cast<int64_t>(c) * ldd] = static_cast<G>(src[r + c * lds]);
+}
+
+// Applies the block reflector of kb reflectors to a chunk of ncols columns:
+//   W = [C1(0:kb, :)] + V^T C          (C1 present for TT pairs: identity part)
+//   W = T^T W  (Q^T, transpose_q = false)   or   W = T W  (Q, transpose_q = true)
+//   C1(0:kb, :) -= W,   C -= V W
+// V is nrows x kb (explicit zeros / unit entries), T upper triangular kb x kb.
+template <typename S>
+__device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols, const S *V,
+                            int ldv, const S *T, int ldt, int kb, S *W, int ldw, bool transpose_q) {
+  const int tid = threadIdx.x;
+  const int a = tid & 31, g = tid >> 5;
+  // W = C1 + V^T C
+  if (a < kb) {
+    S acc[4] = {0, 0, 0, 0};
+    for (int r = 0; r < nrows; ++r) {
+      const S v = V[r + a * ldv];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = g + kWarps * u;
+        if (c < ncols) acc[u] += v * C[r + c * ldc];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = g + kWarps * u;
+      if (c < ncols) W[a + c * ldw] = acc[u] + (C1 ? C1[a + c * ldc1] : S(0));
+    }
+  }
+  __syncthreads();
+  // W = op(T) W
+  S nw[4] = {0, 0, 0, 0};
+  if (a < kb) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = g + kWarps * u;
+      if (c >= ncols) continue;
+      S s = 0;
+      if (!transpose_q) {
+        for (int b = 0; b <= a; ++b) s += T[b + a * ldt] * W[b + c * ldw];
+      } else {
+        for (int b = a; b < kb; ++b) s += T[a + b * ldt] * W[b + c * ldw];
+      }
+      nw[u] = s;
+    }
+  }
+  __syncthreads();
+  if (a < kb) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = g + kWarps * u;
+      if (c < ncols) {
+        W[a + c * ldw] = nw[u];
+        if (C1) C1[a + c * ldc1] -= nw[u];
+      }
+    }
+  }
+  __syncthreads();
+  // C -= V W
+  for (int r = tid; r < nrows; r += kThreads) {
+    S acc[kCW];
+#pragma unroll
+    for (int c = 0; c < kCW; ++c) acc[c] = 0;
+    for (int b = 0; b < kb; ++b) {
+      const S v = V[r + b * ldv];
+#pragma unroll
+      for (int c = 0; c < kCW; ++c) acc[c] += v * W[b + c * ldw];
+    }
+#pragma unroll
+    for (int c = 0; c < kCW; ++c)
+      if (c < ncols) C[r + c * ldc] -= acc[c];
+  }
+  __syncthreads();
+}
+
+// FP64 reflector parameters from alpha and ||x||^2 (LAPACK convention).
+__device__ __forceinline__ void reflector(double alpha, double xx, double *beta, double *tau,
+                                          double *scal) {
+  if (xx == 0.0) {
+    *beta = alpha;
+    *tau = 0.0;
+    *scal = 0.0;
+    return;
+  }
+  const double nrm = sqrt(alpha * alpha + xx);
+  const double b = alpha >= 0.0 ? -nrm : nrm;
+  *beta = b;
+  *tau = (b - alpha) / b;
+  *scal = 1.0 / (alpha - b);
+}
+
+// Builds T (kb x kb, upper) from the Gram matrix G (strict upper part) and tau:
+// T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c).
+template <typename S>
+__device__ void build_t(Smem<S> &s, int kb) {
+  if (threadIdx.x < 32) {
+    const int a = threadIdx.x;
+    for (int c = 0; c < kb; ++c) {
+      const double tc = s.tau[c];
+      S val = 0;
+      if (a < c) {
+        S acc = 0;
+        for (int b = a; b < c; ++b) acc += s.T[a + b * s.ldt] * s.G[b + c * s.ldt];
+        val = static_cast<S>(-tc) * acc;
+      } else if (a == c) {
+        val = static_cast<S>(tc);
+      }
+      __syncwarp();
+      if (a < kb) s.T[a + c * s.ldt] = (a <= c) ? val : S(0);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// Writes the ib x width slice of a T factor for reflectors c0 .. c0+width-1: the kb x kb
+// block from shared memory and zeros elsewhere.
+template <typename S, typename Real>
+__device__ void store_t(Real *Tg, int ib, int c0, int width, const Smem<S> &s, int kb) {
+  for (int idx = threadIdx.x; idx < ib * width; idx += kThreads) {
+    const int c = idx / ib, a = idx - c * ib;
+    S v = 0;
+    if (a < kb && c < kb) v = s.T[a + c * s.ldt];
+    Tg[a + static_cast<int64_t>(c0 + c) * ib] = static_cast<Real>(v);
+  }
+}
+
+template <typename S, typename Real>
+__device__ void load_t(S *dst, int ldt, const Real *Tg, int ib, int c0, int kb) {
+  for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
+    const int c = idx / kb, a = idx - c * kb;
+    dst[a + c * ldt] = static_cast<S>(ldcg(Tg + a + static_cast<int64_t>(c0 + c) * ib));
+  }
+}
+
+struct TileGeom {
+  int64_t m, n;
+  int nb;
+  __device__ int rows(int i) const { return static_cast<int>(lmin(nb, m - int64_t(i) * nb)); }
+  __device__ int cols(int j) const { return static_cast<int>(lmin(nb, n - int64_t(j) * nb)); }
+};
+
+template <typename Real>
+__device__ __forceinline__ Real *tile_ptr(Real *A, int64_t lda, int nb, int i, int j) {
+  return A + static_cast<int64_t>(j) * nb * lda + static_cast<int64_t>(i) * nb;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real *t_ptr(Real *T, int P, int ib, int nb, int i, int k, int which) {
+  return T + (static_cast<int64_t>(k) * P + i) * 2 * ib * nb + static_cast<int64_t>(which) * ib * nb;
+}
+
+// ---------------------------------------------------------------------------------
+// GEQRT(i,k): Householder QR of one tile, blocked by ib (R above, V below the diagonal).
+template <typename Real, typename S>
+__device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
+  const TileGeom geo{p.m, p.n, p.nb};
+  const int nb = p.nb, ib = p.ib;
+  Real *A = static_cast<Real *>(p.A);
+  Real *tile = tile_ptr(A, p.lda, nb, i, k);
+  Real *Tg = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 0);
+  const int mb = geo.rows(i), ncol = geo.cols(k), K = min(mb, ncol);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < nb; c0 += ib) {
+    const int width = min(ib, nb - c0);
+    const int kb = max(0, min(ib, K - c0));
+    if (kb == 0) {
+      store_t(Tg, ib, c0, width, s, 0);
+      continue;
+    }
+    const int rows = mb - c0;
+    Real *blk = tile + c0 + static_cast<int64_t>(c0) * p.lda;
+    load_block(s.V, s.ldv, blk, p.lda, rows, kb);
+    __syncthreads();
+    for (int c = 0; c < kb; ++c) {
+      if (warp == 0) {
+        double xx = 0.0;
+        for (int r = c + 1 + lane; r < rows; r += 32) {
+          const double x = static_cast<double>(s.V[r + c * s.ldv]);
+          xx += x * x;
+        }
+        xx = warp_sum(xx);
+        if (lane == 0) {
+          double beta, tau, scal;
+          reflector(static_cast<double>(s.V[c + c * s.ldv]), xx, &beta, &tau, &scal);
+          s.V[c + c * s.ldv] = static_cast<S>(beta);
+          s.tau[c] = tau;
+          s.scal[0] = scal;
+        }
+      }
+      __syncthreads();
+      const double tau = s.tau[c], scal = s.scal[0];
+      if (tau != 0.0) {
+        for (int r = c + 1 + threadIdx.x; r < rows; r += kThreads)
+          s.V[r + c * s.ldv] = static_cast<S>(static_cast<double>(s.V[r + c * s.ldv]) * scal);
+        __syncthreads();
+        const S t = static_cast<S>(tau);
+        for (int cc = c + 1 + warp; cc < kb; cc += kWarps) {
+          S part = 0;
+          for (int r = c + 1 + lane; r < rows; r += 32) part += s.V[r + c * s.ldv] * s.V[r + cc * s.ldv];
+          const S w = s.V[c + cc * s.ldv] + warp_sum(part);
+          if (lane == 0) s.V[c + cc * s.ldv] -= t * w;
+          for (int r = c + 1 + lane; r < rows; r += 32) s.V[r + cc * s.ldv] -= t * s.V[r + c * s.ldv] * w;
+        }
+      }
+      __syncthreads();
+    }
+    // Gram matrix G(a,c) = v_a . v_c (a < c) of the block's reflectors
+    const int npair = kb * (kb - 1) / 2;
+    for (int pidx = warp; pidx < npair; pidx += kWarps) {
+      int c = 1, base = 0;
+      while (base + c <= pidx) { base += c; ++c; }
+      const int a = pidx - base;
+      S part = 0;
+      for (int r = c + 1 + lane; r < rows; r += 32) part += s.V[r + a * s.ldv] * s.V[r + c * s.ldv];
+      part = warp_sum(part);
+      if (lane == 0) s.G[a + c * s.ldt] = s.V[c + a * s.ldv] + part;
+    }
+    __syncthreads();
+    build_t(s, kb);
+    store_block(blk, p.lda, s.V, s.ldv, rows, kb);
+    store_t(Tg, ib, c0, width, s, kb);
+    __syncthreads();
+    // explicit reflector block: unit diagonal, zeros above
+    for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
+      const int c = idx / kb, r = idx - c * kb;
+      if (r <= c) s.V[r + c * s.ldv] = (r == c) ? S(1) : S(0);
+    }
+    __syncthreads();
+    for (int cs = c0 + kb; cs < ncol; cs += kCW) {
+      const int w = min(kCW, ncol - cs);
+      Real *cblk = tile + c0 + static_cast<int64_t>(cs) * p.lda;
+      load_block(s.C, s.ldv, cblk, p.lda, rows, w);
+      __syncthreads();
+      apply_block(s.C, s.ldv, rows, static_cast<S *>(nullptr), 0, w, s.V, s.ldv, s.T, s.ldt, kb,
+                  s.W, s.ldw, false);
+      store_block(cblk, p.lda, s.C, s.ldv, rows, w);
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// TTQRT(i,piv,k): QR of the upper triangle of tile (piv,k) stacked on the upper
+// triangle of tile (i,k); reflector c acts on row c of (piv,k) and rows 0..c of (i,k),
+// its tail is stored in column c of (i,k)'s upper triangle.
+template <typename Real, typename S>
+__device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int k) {
+  const TileGeom geo{p.m, p.n, p.nb};
+  const int nb = p.nb, ib = p.ib;
+  Real *A = static_cast<Real *>(p.A);
+  Real *t1 = tile_ptr(A, p.lda, nb, piv, k);
+  Real *t2 = tile_ptr(A, p.lda, nb, i, k);
+  Real *Tt = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 1);
+  const int mb = geo.rows(i), K = geo.cols(k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < nb; c0 += ib) {
+    const int width = min(ib, nb - c0);
+    const int kb = max(0, min(ib, K - c0));
+    if (kb == 0) {
+      store_t(Tt, ib, c0, width, s, 0);
+      continue;
+    }
+    const int rb = min(c0 + kb, mb);  // rows of tile i touched by this block
+    // P2 = upper part of tile i, rows 0..rb-1, columns c0..c0+kb-1
+    for (int c = warp; c < kb; c += kWarps)
+      for (int r = lane; r < rb; r += 32)
+        s.V[r + c * s.ldv] =
+            (r <= c0 + c) ? static_cast<S>(ldcg(t2 + r + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
+    // P1 = upper part of the diagonal block of R(piv)
+    for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
+      const int c = idx / kb, r = idx - c * kb;
+      s.P1[r + c * s.ldt] =
+          (r <= c) ? static_cast<S>(ldcg(t1 + (c0 + r) + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
+    }
+    __syncthreads();
+    for (int c = 0; c < kb; ++c) {
+      const int rr = min(c0 + c + 1, mb);
+      if (warp == 0) {
+        double xx = 0.0;
+        for (int r = lane; r < rr; r += 32) {
+          const double x = static_cast<double>(s.V[r + c * s.ldv]);
+          xx += x * x;
+        }
+        xx = warp_sum(xx);
+        if (lane == 0) {
+          double beta, tau, scal;
+          reflector(static_cast<double>(s.P1[c + c * s.ldt]), xx, &beta, &tau, &scal);
+          s.P1[c + c * s.ldt] = static_cast<S>(beta);
+          s.tau[c] = tau;
+          s.scal[0] = scal;
+        }
+      }
+      __syncthreads();
+      const double tau = s.tau[c], scal = s.scal[0];
+      if (tau != 0.0) {
+        for (int r = threadIdx.x; r < rr; r += kThreads)
+          s.V[r + c * s.ldv] = static_cast<S>(static_cast<double>(s.V[r + c * s.ldv]) * scal);
+        __syncthreads();
+        const S t = static_cast<S>(tau);
+        for (int cc = c + 1 + warp; cc < kb; cc += kWarps) {
+          S part = 0;
+          for (int r = lane; r < rr; r += 32) part += s.V[r + c * s.ldv] * s.V[r + cc * s.ldv];
+          const S w = s.P1[c + cc * s.ldt] + warp_sum(part);
+          if (lane == 0) s.P1[c + cc * s.ldt] -= t * w;
+          for (int r = lane; r < rr; r += 32) s.V[r + cc * s.ldv] -= t * s.V[r + c * s.ldv] * w;
+        }
+      }
+      __syncthreads();
+    }
+    const int npair = kb * (kb - 1) / 2;
+    for (int pidx = warp; pidx < npair; pidx += kWarps) {
+      int c = 1, base = 0;
+      while (base + c <= pidx) { base += c; ++c; }
+      const int a = pidx - base;
+      const int ra = min(c0 + a + 1, mb);
+      S part = 0;
+      for (int r = lane; r < ra; r += 32) part += s.V[r + a * s.ldv] * s.V[r + c * s.ldv];
+      part = warp_sum(part);
+      if (lane == 0) s.G[a + c * s.ldt] = part;
+    }
+    __syncthreads();
+    build_t(s, kb);
+    // write back the upper parts only (the lower parts hold GEQRT reflectors)
+    for (int c = warp; c < kb; c += kWarps)
+      for (int r = lane; r < rb; r += 32)
+        if (r <= c0 + c) t2[r + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.V[r + c * s.ldv]);
+    for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
+      const int c = idx / kb, r = idx - c * kb;
+      if (r <= c) t1[(c0 + r) + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.P1[r + c * s.ldt]);
+    }
+    store_t(Tt, ib, c0, width, s, kb);
+    __syncthreads();
+    // trailing columns of the same tile column: [R(piv) rows c0..c0+kb-1 ; tile i rows 0..rb-1]
+    for (int cs = c0 + kb; cs < K; cs += kCW) {
+      const int w = min(kCW, K - cs);
+      Real *c1 = t1 + c0 + static_cast<int64_t>(cs) * p.lda;
+      Real *c2 = t2 + static_cast<int64_t>(cs) * p.lda;
+      load_block(s.C1, s.ldv, c1, p.lda, kb, w);
+      load_block(s.C, s.ldv, c2, p.lda, rb, w);
+      __syncthreads();
+      apply_block(s.C, s.ldv, rb, s.C1, s.ldv, w, s.V, s.ldv, s.T, s.ldt, kb, s.W, s.ldw, false);
+      store_block(c1, p.lda, s.C1, s.ldv, kb, w);
+      store_block(c2, p.lda, s.C, s.ldv, rb, w);
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// UNMQR: C <- Q^T C (or Q C) with the reflectors of GEQRT(i,k).  C is mb x ncols at
+// cptr (leading dimension ldc); it is tile (i,j) of A or tile row i of B.
+template <typename Real, typename S, typename CT>
+__device__ void task_unmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *cptr, int64_t ldc,
+                           int ncols, bool transpose_q) {
+  const TileGeom geo{p.m, p.n, p.nb};
+  const int nb = p.nb, ib = p.ib;
+  const Real *vt = tile_ptr(static_cast<Real *>(p.A), p.lda, nb, i, k);
+  const Real *Tg = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 0);
+  const int mb = geo.rows(i), K = min(mb, geo.cols(k));
+  const int nblk = (K + ib - 1) / ib;
+  for (int cs = 0; cs < ncols; cs += kCW) {
+    const int w = min(kCW, ncols - cs);
+    CT *cblk = cptr + static_cast<int64_t>(cs) * ldc;
+    load_block(s.C, s.ldv, cblk, ldc, mb, w);
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int b = transpose_q ? nblk - 1 - bb : bb;
+      const int c0 = b * ib, kb = min(ib, K - c0), rows = mb - c0;
+      const Real *vb = vt + c0 + static_cast<int64_t>(c0) * p.lda;
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int c = warp; c < kb; c += kWarps)
+        for (int r = lane; r < rows; r += 32)
+          s.V[r + c * s.ldv] = (r > c) ? static_cast<S>(ldcg(vb + r + static_cast<int64_t>(c) * p.lda))
+                                       : (r == c ? S(1) : S(0));
+      load_t(s.T, s.ldt, Tg, ib, c0, kb);
+      __syncthreads();
+      apply_block(s.C + c0, s.ldv, rows, static_cast<S *>(nullptr), 0, w, s.V, s.ldv, s.T, s.ldt, kb,
+                  s.W, s.ldw, transpose_q);
+    }
+    store_block(cblk, ldc, s.C, s.ldv, mb, w);
+    __syncthreads();
+  }
+}
+
+// TTMQR: [C1; C2] <- Q^T [C1; C2] (or Q [C1; C2]) with the reflectors of the TTQRT that
+// zeroed tile (i,k).  C1 is the pivot row's tile (nb rows), C2 row i's tile (mb rows).
+template <typename Real, typename S, typename CT>
+__device__ void task_ttmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *c1ptr, CT *c2ptr,
+                           int64_t ldc, int ncols, bool transpose_q) {
+  const TileGeom geo{p.m, p.n, p.nb};
+  const int nb = p.nb, ib = p.ib;
+  const Real *vt = tile_ptr(static_cast<Real *>(p.A), p.lda, nb, i, k);
+  const Real *Tt = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 1);
+  const int mb = geo.rows(i), K = geo.cols(k);
+  const int nblk = (K + ib - 1) / ib;
+  for (int cs = 0; cs < ncols; cs += kCW) {
+    const int w = min(kCW, ncols - cs);
+    CT *b1 = c1ptr + static_cast<int64_t>(cs) * ldc;
+    CT *b2 = c2ptr + static_cast<int64_t>(cs) * ldc;
+    load_block(s.C1, s.ldv, b1, ldc, K, w);
+    load_block(s.C, s.ldv, b2, ldc, mb, w);
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int b = transpose_q ? nblk - 1 - bb : bb;
+      const int c0 = b * ib, kb = min(ib, K - c0), rb = min(c0 + kb, mb);
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (int c = warp; c < kb; c += kWarps)
+        for (int r = lane; r < rb; r += 32)
+          s.V[r + c * s.ldv] =
+              (r <= c0 + c) ? static_cast<S>(ldcg(vt + r + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
+      load_t(s.T, s.ldt, Tt, ib, c0, kb);
+      __syncthreads();
+      apply_block(s.C, s.ldv, rb, s.C1 + c0, s.ldv, w, s.V, s.ldv, s.T, s.ldt, kb, s.W, s.ldw,
+                  transpose_q);
+    }
+    store_block(b1, ldc, s.C1, s.ldv, K, w);
+    store_block(b2, ldc, s.C, s.ldv, mb, w);
+    __syncthreads();
+  }
+}
+
+// Bounded wait until *counter == 0.  Returns false if this CTA must stop.
+__device__ bool wait_ready(const ExecParams &p, int t) {
+  const int32_t *cnt = p.counters + t;
+  if (ld_acquire_gpu(cnt) <= 0) return true;
+  const uint64_t t0 = globaltimer_ns();
+  const uint64_t limit = static_cast<uint64_t>(p.wait_limit_ns);
+  for (uint64_t it = 0;; ++it) {
+    if (ld_acquire_gpu(cnt) <= 0) return true;
+    if (ld_relaxed_gpu(p.status) != 0) return false;
+    if (globaltimer_ns() - t0 > limit || it > (limit >> 4) + 1000000ull) {
+      atomicCAS(p.status, 0, kStatusTimeout | (t << 8));
+      return false;
+    }
+    __nanosleep(64);
+  }
+}
+
+template <typename Real, typename S>
+__global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task, s_stop;
+  Smem<S> s = carve<S>(smem_raw, p.nb, p.ib);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(p.next, 1);
+      int stop = t >= p.ntask;
+      if (!stop && !wait_ready(p, t)) stop = 1;
+      s_task = t;
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int t = s_task;
+    const Task task = p.tasks[t];
+    const int nb = p.nb;
+    switch (task.kind) {
+      case kGeqrt:
+        task_geqrt<Real, S>(p, s, task.i, task.k);
+        break;
+      case kTtqrt:
+        task_ttqrt<Real, S>(p, s, task.i, task.piv, task.k);
+        break;
+      case kUnmqr: {
+        Real *A = static_cast<Real *>(p.A);
+        const int ncols = static_cast<int>(lmin(nb, p.n - int64_t(task.j) * nb));
+        task_unmqr<Real, S, Real>(p, s, task.i, task.k, tile_ptr(A, p.lda, nb, task.i, task.j), p.lda,
+                                  ncols, false);
+        break;
+      }
+      case kTtmqr: {
+        Real *A = static_cast<Real *>(p.A);
+        const int ncols = static_cast<int>(lmin(nb, p.n - int64_t(task.j) * nb));
+        task_ttmqr<Real, S, Real>(p, s, task.i, task.k, tile_ptr(A, p.lda, nb, task.piv, task.j),
+                                  tile_ptr(A, p.lda, nb, task.i, task.j), p.lda, ncols, false);
+        break;
+      }
+      case kUnmqrB:
+        task_unmqr<Real, S, double>(p, s, task.i, task.k, p.B + static_cast<int64_t>(task.i) * nb, p.ldb,
+                                    static_cast<int>(p.nrhs), p.trans != 0);
+        break;
+      case kTtmqrB:
+        task_ttmqr<Real, S, double>(p, s, task.i, task.k, p.B + static_cast<int64_t>(task.piv) * nb,
+                                    p.B + static_cast<int64_t>(task.i) * nb, p.ldb,
+                                    static_cast<int>(p.nrhs), p.trans != 0);
+        break;
+      default:
+        break;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      for (int e = p.succ_ptr[t]; e < p.succ_ptr[t + 1]; ++e) atomicSub(p.counters + p.succ_idx[e], 1);
+    }
+  }
+}
+
+template <typename Real, typename S>
+int launch_typed(const ExecParams &p, void *stream, size_t smem) {
+  auto kern = executor_kernel<Real, S>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return static_cast<int>(e);
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  if (per_sm < 1) per_sm = 1;
+  int grid = nsm * per_sm;
+  if (grid > p.ntask) grid = p.ntask;
+  if (grid < 1) grid = 1;
+  kern<<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(p);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace
+
+size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q) {
+  const size_t ssz = (real_is_double || apply_q) ? sizeof(double) : sizeof(float);
+  const size_t bytes = smem_elems(nb, ib, ssz);
+  return bytes <= 227 * 1024 ? bytes : 0;
+}
+
+int launch_executor(const ExecParams &p, bool real_is_double, void *stream) {
+  const bool apply_q = p.B != nullptr;
+  const size_t smem = executor_smem_bytes(p.nb, p.ib, real_is_double, apply_q);
+  if (real_is_double) return launch_typed<double, double>(p, stream, smem);
+  if (apply_q) return launch_typed<float, double>(p, stream, smem);
+  return launch_typed<float, float>(p, stream, smem);
+}
+
+}  // namespace tqr

@@ -1,0 +1,170 @@
+// Tile task graph of the TT tiled QR (Section 3.1.1, Algorithm "elimTR"; dependencies
+// Eq. ttdeps and ttdeps2) and its executor order.
+//
+// The graph is the sequential column-by-column program - for every panel k: GEQRT(i,k)
+// and UNMQR(i,k,j) for all rows i >= k, then TTQRT(i,piv,k) and TTMQR(i,piv,k,j) for
+// each elimination of column k in list order - with a dependency wherever two kernels
+// touch the same tile region and one of them writes it.  Splitting each panel tile into
+// its strictly-lower part (GEQRT reflectors, read by UNMQR) and its upper part (R and
+// later the TTQRT reflectors) lets UNMQR overlap TTQRT as Section 3.1.1 states.
+#include <algorithm>
+#include <numeric>
+
+#include "tqr_internal.h"
+
+namespace tqr {
+
+GraphBuilder::GraphBuilder(int nregions)
+    : last_writer(nregions, -1), readers(nregions) {}
+
+int GraphBuilder::add(const Task &t, int w, const int *reads, int nr, const int *writes,
+                      int nw) {
+  const int id = static_cast<int>(tasks.size());
+  std::vector<int32_t> pr;
+  for (int a = 0; a < nr; ++a) {
+    const int r = reads[a];
+    if (last_writer[r] >= 0) pr.push_back(last_writer[r]);
+  }
+  for (int a = 0; a < nw; ++a) {
+    const int r = writes[a];
+    if (last_writer[r] >= 0) pr.push_back(last_writer[r]);
+    for (int32_t x : readers[r]) pr.push_back(x);
+  }
+  std::sort(pr.begin(), pr.end());
+  pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+  int64_t start = 0;
+  for (int32_t x : pr) start = std::max(start, finish[x]);
+  for (int a = 0; a < nr; ++a) readers[reads[a]].push_back(id);
+  for (int a = 0; a < nw; ++a) {
+    last_writer[writes[a]] = id;
+    readers[writes[a]].clear();
+  }
+  tasks.push_back(t);
+  weight.push_back(w);
+  finish.push_back(start + w);
+  preds.push_back(std::move(pr));
+  return id;
+}
+
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k) {
+  std::vector<int> geqrt_ids;
+  for (int i = k; i < p; ++i) {
+    const int rw[2] = {region_L(q, i, k), region_U(q, i, k)};
+    geqrt_ids.push_back(b.add(Task{kGeqrt, i, -1, (int16_t)k, -1}, kWGeqrt, nullptr, 0, rw, 2));
+    for (int j = k + 1; j < q; ++j) {
+      const int rd[1] = {region_L(q, i, k)};
+      const int wr[2] = {region_L(q, i, j), region_U(q, i, j)};
+      b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)j}, kWUnmqr, rd, 1, wr, 2);
+    }
+  }
+  return geqrt_ids;
+}
+
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col) {
+  for (const Elim &e : col) {
+    const int wr[2] = {region_U(q, e.piv, k), region_U(q, e.i, k)};
+    b.add(Task{kTtqrt, e.i, e.piv, (int16_t)k, -1}, kWTtqrt, nullptr, 0, wr, 2);
+    for (int j = k + 1; j < q; ++j) {
+      const int rd[1] = {region_U(q, e.i, k)};
+      const int w4[4] = {region_L(q, e.piv, j), region_U(q, e.piv, j), region_L(q, e.i, j),
+                         region_U(q, e.i, j)};
+      b.add(Task{kTtmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, kWTtmqr, rd, 1, w4, 4);
+    }
+  }
+}
+
+void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge) {
+  const int n = static_cast<int>(b.tasks.size());
+  // successors in program order
+  std::vector<std::vector<int32_t>> succ(n);
+  for (int t = 0; t < n; ++t)
+    for (int32_t x : b.preds[t]) succ[x].push_back(t);
+  // longest path to a sink, including the task itself (program order is topological)
+  std::vector<int64_t> bottom(n, 0);
+  for (int t = n - 1; t >= 0; --t) {
+    int64_t best = 0;
+    for (int32_t s : succ[t]) best = std::max(best, bottom[s]);
+    bottom[t] = best + b.weight[t];
+  }
+  // executor order: earliest start with unbounded processors, then the longer
+  // remaining path first, then program order.  Earliest start strictly increases
+  // along every edge, so this order is topological.
+  std::vector<int32_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+    const int64_t sa = b.finish[a] - b.weight[a], sc = b.finish[c] - b.weight[c];
+    if (sa != sc) return sa < sc;
+    if (bottom[a] != bottom[c]) return bottom[a] > bottom[c];
+    return a < c;
+  });
+  std::vector<int32_t> pos(n);
+  for (int r = 0; r < n; ++r) pos[order[r]] = r;
+
+  g.tasks.resize(n);
+  g.weight.resize(n);
+  g.indeg.assign(n, 0);
+  g.succ_ptr.assign(n + 1, 0);
+  g.succ_idx.clear();
+  g.critical_path = 0;
+  for (int c = 0; c < 4; ++c) g.counts[c] = 0;
+  for (int r = 0; r < n; ++r) {
+    const int t = order[r];
+    g.tasks[r] = b.tasks[t];
+    g.weight[r] = b.weight[t];
+    g.indeg[r] = static_cast<int32_t>(b.preds[t].size());
+    g.critical_path = std::max<int64_t>(g.critical_path, b.finish[t]);
+    const int kind = b.tasks[t].kind;
+    if (kind >= kGeqrt && kind <= kTtmqr) g.counts[kind]++;
+  }
+  int64_t edge = 0;
+  for (int r = 0; r < n; ++r) {
+    const int t = order[r];
+    std::vector<int32_t> s;
+    for (int32_t x : succ[t]) s.push_back(pos[x]);
+    std::sort(s.begin(), s.end());
+    for (int32_t x : s) {
+      // test hook: leave out one release so that its successor can never start
+      if (edge++ == drop_edge) continue;
+      g.succ_idx.push_back(x);
+    }
+    g.succ_ptr[r + 1] = static_cast<int32_t>(g.succ_idx.size());
+  }
+}
+
+void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge) {
+  GraphBuilder b(p * q * 2);
+  const int kmax = std::min(p, q);
+  std::vector<std::vector<Elim>> by_col(kmax);
+  for (const Elim &e : elims) by_col[e.k].push_back(e);
+  for (int k = 0; k < kmax; ++k) {
+    add_panel_tasks(b, p, q, k);
+    add_elim_tasks(b, q, k, by_col[k]);
+  }
+  finalize_graph(b, g, drop_edge);
+}
+
+void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g) {
+  // Regions are the tile rows of the right-hand-side block; the factors are read-only.
+  const int kmax = std::min(p, q);
+  std::vector<std::vector<Elim>> by_col(kmax);
+  for (const Elim &e : elims) by_col[e.k].push_back(e);
+  std::vector<Task> ops;
+  for (int k = 0; k < kmax; ++k) {
+    for (int i = k; i < p; ++i) ops.push_back(Task{kUnmqrB, i, -1, (int16_t)k, -1});
+    for (const Elim &e : by_col[k]) ops.push_back(Task{kTtmqrB, e.i, e.piv, (int16_t)k, -1});
+  }
+  if (reverse) std::reverse(ops.begin(), ops.end());
+  GraphBuilder b(p);
+  for (const Task &t : ops) {
+    if (t.kind == kUnmqrB) {
+      const int wr[1] = {t.i};
+      b.add(t, kWUnmqr, nullptr, 0, wr, 1);
+    } else {
+      const int wr[2] = {t.piv, t.i};
+      b.add(t, kWTtmqr, nullptr, 0, wr, 2);
+    }
+  }
+  finalize_graph(b, g);
+}
+
+}  // namespace tqr

@@ -1,0 +1,167 @@
+// Triangular solve R X = B for the upper-triangular R of a tiled QR (the last step of
+// the least-squares solve x = R^{-1} (Q^T b)(0:n)).
+//
+// Wavefront over row blocks of TB rows: CTAs take tickets in launch order and handle
+// the row blocks bottom-up; block kb waits for every block below it (published through
+// a per-block flag with release/acquire), subtracts R(kb, kk) X(kk), then solves its
+// diagonal block by back substitution (one warp per right-hand side).  A block only
+// waits for blocks whose tickets were taken earlier, so the wavefront cannot deadlock.
+// Waits are bounded like the executor's and report kStatusTimeout.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tqr_internal.h"
+
+namespace tqr {
+namespace {
+
+__host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
+
+constexpr int kTB = 64;        // rows per block
+constexpr int kRHS = 32;       // right-hand sides per pass
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acq(const int32_t *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_rel(int32_t *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const float *p) { return static_cast<double>(__ldcg(p)); }
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A, int64_t lda, double *B,
+                                                        int64_t ldb, int nrhs, int32_t *flags,
+                                                        int32_t *status, int64_t wait_limit_ns) {
+  extern __shared__ double trsm_smem[];
+  double(*Cs)[kRHS + 1] = reinterpret_cast<double(*)[kRHS + 1]>(trsm_smem);
+  double(*Xs)[kRHS + 1] = reinterpret_cast<double(*)[kRHS + 1]>(trsm_smem + kTB * (kRHS + 1));
+  double(*Rs)[kTB + 1] = reinterpret_cast<double(*)[kTB + 1]>(trsm_smem + 2 * kTB * (kRHS + 1));
+  __shared__ int s_kb, s_stop;
+  const int nblk = static_cast<int>((n + kTB - 1) / kTB);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    s_kb = nblk - 1 - atomicAdd(flags, 1);
+    s_stop = 0;
+  }
+  __syncthreads();
+  const int kb = s_kb;
+  if (kb < 0) return;
+  const int64_t r0 = static_cast<int64_t>(kb) * kTB;
+  const int rb = static_cast<int>(lmin(kTB, n - r0));
+  for (int idx = tid; idx < rb * nrhs; idx += kThreads) {
+    const int j = idx / rb, r = idx - j * rb;
+    Cs[r][j] = ld_cg(B + r0 + r + j * ldb);
+  }
+  for (int kk = nblk - 1; kk > kb; --kk) {
+    if (tid == 0) {
+      const uint64_t t0 = gtimer();
+      for (uint64_t it = 0; ld_acq(flags + 1 + kk) == 0; ++it) {
+        if (*(volatile int32_t *)status != 0) { s_stop = 1; break; }
+        if (gtimer() - t0 > static_cast<uint64_t>(wait_limit_ns) ||
+            it > (static_cast<uint64_t>(wait_limit_ns) >> 4) + 1000000ull) {
+          atomicCAS(status, 0, kStatusTimeout | (kk << 8));
+          s_stop = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const int64_t c0 = static_cast<int64_t>(kk) * kTB;
+    const int cb = static_cast<int>(lmin(kTB, n - c0));
+    for (int idx = tid; idx < rb * cb; idx += kThreads) {
+      const int c = idx / rb, r = idx - c * rb;
+      Rs[r][c] = ld_cg(A + (r0 + r) + (c0 + c) * lda);
+    }
+    for (int idx = tid; idx < cb * nrhs; idx += kThreads) {
+      const int j = idx / cb, r = idx - j * cb;
+      Xs[r][j] = ld_cg(B + c0 + r + j * ldb);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rb * nrhs; idx += kThreads) {
+      const int j = idx / rb, r = idx - j * rb;
+      double acc = 0.0;
+      for (int c = 0; c < cb; ++c) acc += Rs[r][c] * Xs[c][j];
+      Cs[r][j] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < rb * rb; idx += kThreads) {
+    const int c = idx / rb, r = idx - c * rb;
+    Rs[r][c] = (r <= c) ? ld_cg(A + (r0 + r) + (r0 + c) * lda) : 0.0;
+  }
+  __syncthreads();
+  // back substitution, one warp per right-hand side; lane owns rows lane and lane+32
+  for (int j = warp; j < nrhs; j += kThreads / 32) {
+    double c_lo = lane < rb ? Cs[lane][j] : 0.0;
+    double c_hi = lane + 32 < rb ? Cs[lane + 32][j] : 0.0;
+    for (int i = rb - 1; i >= 0; --i) {
+      const double ci = __shfl_sync(0xffffffffu, i < 32 ? c_lo : c_hi, i & 31);
+      const double xi = ci / Rs[i][i];
+      if (lane == (i & 31)) {
+        if (i < 32) c_lo = xi; else c_hi = xi;
+      }
+      if (lane < i) c_lo -= Rs[lane][i] * xi;
+      if (lane + 32 < i) c_hi -= Rs[lane + 32][i] * xi;
+    }
+    if (lane < rb) Cs[lane][j] = c_lo;
+    if (lane + 32 < rb) Cs[lane + 32][j] = c_hi;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < rb * nrhs; idx += kThreads) {
+    const int j = idx / rb, r = idx - j * rb;
+    B[r0 + r + j * ldb] = Cs[r][j];
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_rel(flags + 1 + kb, 1);
+  }
+}
+
+}  // namespace
+
+int trsm_flag_count(int64_t n) { return static_cast<int>((n + kTB - 1) / kTB) + 1; }
+
+int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, double *B, int64_t ldb,
+                int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t smem = sizeof(double) * (2 * kTB * (kRHS + 1) + kTB * (kTB + 1));
+  cudaError_t ea = real_is_double
+      ? cudaFuncSetAttribute(trsm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+      : cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (ea != cudaSuccess) return static_cast<int>(ea);
+  const int nblk = static_cast<int>((n + kTB - 1) / kTB);
+  for (int64_t j0 = 0; j0 < nrhs; j0 += kRHS) {
+    const int nr = static_cast<int>(nrhs - j0 < kRHS ? nrhs - j0 : kRHS);
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * (nblk + 1), st);
+    if (e != cudaSuccess) return static_cast<int>(e);
+    if (real_is_double)
+      trsm_kernel<double><<<nblk, kThreads, smem, st>>>(n, static_cast<const double *>(A), lda, B + j0 * ldb, ldb,
+                                                      nr, flags, status, wait_limit_ns);
+    else
+      trsm_kernel<float><<<nblk, kThreads, smem, st>>>(n, static_cast<const float *>(A), lda, B + j0 * ldb, ldb,
+                                                     nr, flags, status, wait_limit_ns);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return static_cast<int>(e);
+  }
+  return 0;
+}
+
+}  // namespace tqr

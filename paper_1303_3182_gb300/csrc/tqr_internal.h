@@ -1,0 +1,125 @@
+// Internal declarations of libtqr shared by the host and device translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace tqr {
+
+// One elimination elim(i, piv, k): tile (i,k) is zeroed by row piv in panel k.
+struct Elim {
+  int k, i, piv;
+};
+
+// Kernel weights in units of nb^3/3 flops (Table "Kernels for tiled QR").
+constexpr int kWGeqrt = 4, kWTtqrt = 2, kWUnmqr = 6, kWTtmqr = 6;
+
+// Elimination list of a tree in canonical order (Section 3.2).  Returns false on an
+// unknown tree.  Host only.
+bool elimination_list(int p, int q, int tree, int bs, std::vector<Elim> &out);
+
+// Task kinds of the tile task graph.
+enum TaskKind : int32_t {
+  kGeqrt = 0,   // GEQRT(i,k)
+  kTtqrt = 1,   // TTQRT(i,piv,k)
+  kUnmqr = 2,   // UNMQR(i,k,j)
+  kTtmqr = 3,   // TTMQR(i,piv,k,j)
+  kUnmqrB = 4,  // UNMQR(i,k) applied to tile row i of a right-hand-side block
+  kTtmqrB = 5,  // TTMQR(i,piv,k) applied to tile rows (piv, i) of a right-hand-side block
+};
+
+// A task as the device executor reads it (16 bytes).
+struct Task {
+  int32_t kind;
+  int32_t i;    // row of the factored / zeroed tile
+  int32_t piv;  // pivot row (TT kernels), else -1
+  int16_t k;    // panel column
+  int16_t j;    // target column of an update, else -1
+};
+
+// The task graph of one factorization or one apply-Q, in executor order.
+struct Graph {
+  std::vector<Task> tasks;           // executor (priority) order, topological
+  std::vector<int32_t> succ_ptr;     // CSR of successors, size tasks+1
+  std::vector<int32_t> succ_idx;
+  std::vector<int32_t> indeg;        // number of predecessors
+  std::vector<int32_t> weight;       // kernel weight per task
+  int64_t critical_path = 0;         // longest weighted path (unbounded processors)
+  int64_t counts[4] = {0, 0, 0, 0};  // GEQRT, TTQRT, UNMQR, TTMQR
+};
+
+// Incremental construction of a task graph in sequential-program order.  Regions are
+// integer ids; a task depends on the last writer of every region it reads or writes
+// and on every reader (since that write) of a region it writes.  finish[] is the
+// earliest finish time with unbounded processors.
+struct GraphBuilder {
+  explicit GraphBuilder(int nregions);
+  int add(const Task &t, int w, const int *reads, int nr, const int *writes, int nw);
+  std::vector<Task> tasks;
+  std::vector<int32_t> weight;
+  std::vector<int64_t> finish;
+  std::vector<std::vector<int32_t>> preds;
+  std::vector<int32_t> last_writer;
+  std::vector<std::vector<int32_t>> readers;
+};
+
+// Tile regions of the factorization graph: each tile (i,j) has a strictly-lower part
+// (GEQRT reflectors) and an upper part (R, then TTQRT reflectors).
+inline int region_L(int q, int i, int j) { return (i * q + j) * 2; }
+inline int region_U(int q, int i, int j) { return (i * q + j) * 2 + 1; }
+// Adds GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k of panel k; returns the task
+// ids of the GEQRTs (index i - k).
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k);
+// Adds TTQRT(i,piv,k) and TTMQR(i,piv,k,j) for the eliminations of panel k, in order.
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col);
+// Orders a built graph for the executor (earliest start, then longest remaining path)
+// and fills the successor CSR.
+void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1);
+
+// Builds the factorization task graph of a p x q tile matrix with the given list
+// (column-by-column program of Algorithm "elimTR"; dependencies from the tile regions
+// each kernel reads and writes, Eq. ttdeps / ttdeps2).
+void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
+                        int64_t drop_edge = -1);
+// Builds the graph that applies Q^T (or Q when reverse) to a right-hand-side block.
+void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g);
+
+void set_error(const std::string &msg);
+
+// ---- device side (factor.cu, solve.cu) -------------------------------------------
+// Status word layout written by the device: code in the low 8 bits, task index above.
+constexpr int kStatusTimeout = 3;
+
+// Arguments of one persistent executor launch.  Pointers are device pointers.
+struct ExecParams {
+  void *A;               // factor storage (double or float), column-major
+  int64_t lda, m, n;
+  int nb, ib, P, Q;      // tile size, inner block, tile grid
+  void *T;               // T workspace (same element type as A)
+  double *B;             // right-hand-side block for apply-Q tasks (else null)
+  int64_t ldb, nrhs;
+  int trans;             // apply-Q: 0 = Q^T, 1 = Q
+  const Task *tasks;
+  const int32_t *succ_ptr, *succ_idx;
+  int32_t *counters;     // per-task remaining predecessors (reset before each run)
+  int32_t *next;         // task ticket
+  int32_t *status;       // 0 or kStatusTimeout | (task << 8)
+  int ntask;
+  int64_t wait_limit_ns;
+};
+
+// Launches the persistent tile-task executor on "stream".  real_is_double selects the
+// factor storage type.  Returns a cudaError_t value (0 = success).
+int launch_executor(const ExecParams &p, bool real_is_double, void *stream);
+// Dynamic shared memory the executor needs (0 if nb/ib do not fit on one SM).
+size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q);
+
+// Wavefront triangular solve R X = B (R upper n x n in A, double or float), X over B.
+// flags: device int32[ceil(n/TB) + 1] scratch (ticket + per-block flags).
+int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, double *B,
+                int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status,
+                int64_t wait_limit_ns, void *stream);
+int trsm_flag_count(int64_t n);
+
+}  // namespace tqr

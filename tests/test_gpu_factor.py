@@ -1,0 +1,208 @@
+"""GPU parity tests of the FP64 / FP32 tiled QR against the CPU oracle, through the C ABI.
+
+Element-wise tolerance (FP64): every stored entry (R, the GEQRT and TTQRT reflectors, the
+T factors) is a sum of at most ~2(m+n) rounded products of O(1) reflector entries and
+entries of A, so GPU and oracle (different summation order) agree to
+|delta| <= c * max(m, n) * u * scale with u = 2^-53; c = 64 covers the accumulation
+of both sides.  scale is the largest magnitude in the compared block.
+FP32 storage (norms and tau still in FP64): the same bound with u = 2^-24, c = 64.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import elimlists as E
+from oracle import householder as H
+from oracle import refine
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1303_3182_gb300 as tqr  # noqa: E402
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1303_3182_gb300 import build
+    build.build()
+    tqr.set_wait_limit_ns(20 * 10 ** 9)
+
+
+def to_dev(a, dtype=torch.float64):
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).to(dtype)
+    return t.cuda().t()  # column-major view, stride (1, m)
+
+
+def to_np(t):
+    return t.double().cpu().numpy()
+
+
+def gpu_t_blocks(Tbuf, P, K, ib, nb, dtype):
+    arr = Tbuf.view(dtype).cpu().double().numpy()
+    return arr.reshape(K, P, 2, nb, ib)  # [k][i][which] -> (nb cols, ib rows) row-major view
+
+
+def compare_factor(A, nb, ib, tree, prec="fp64", bs=2):
+    m, n = A.shape
+    p, q = H.tile_grid(m, n, nb)
+    elims = E.elimination_list(p, q, tqr.TREES[tree] if isinstance(tree, str) else tree, bs=bs)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    if prec != "fp64":
+        A = A.astype(np.float32).astype(np.float64)  # the oracle runs on the rounded input
+    F, Tg, Tt = H.tiled_qr(A, nb, ib, elims)
+    Ad = to_dev(A, dtype)
+    T = tqr.factor(Ad, nb, ib, tree, bs, prec)
+    torch.cuda.synchronize()
+    G = to_np(Ad)
+    u = U64 if prec == "fp64" else U32
+    scale = max(1.0, np.max(np.abs(F[:m, :n])))
+    tol = 64 * max(m, n) * u * scale
+    err = np.max(np.abs(G - F[:m, :n]))
+    assert err <= tol, f"factor mismatch {err} > {tol}"
+    K = min(p, q)
+    Tb = gpu_t_blocks(T, p, K, ib, nb, dtype)
+    worst = 0.0
+    for k in range(K):
+        for i in range(k, p):
+            for which, ref in ((0, Tg[i][k]), (1, Tt[i][k])):
+                if ref is None:
+                    continue
+                got = Tb[k, i, which].T  # ib x nb
+                worst = max(worst, np.max(np.abs(got - ref)))
+    assert worst <= 64 * max(m, n) * u * 4, f"T mismatch {worst}"
+    return Ad, T, F, elims
+
+
+CASES = [
+    # (m, n, nb, ib, tree)
+    (512, 128, 64, 16, "greedy"),       # the 512 x 128 workload (p = 8, q = 2)
+    (1000, 300, 64, 16, "greedy"),      # ragged rows and columns
+    (640, 320, 64, 32, "flat"),
+    (640, 320, 64, 32, "plasma"),
+    (640, 320, 64, 32, "binary"),
+    (640, 320, 64, 32, "fibonacci"),
+    (640, 320, 64, 32, "grasap"),
+    (640, 320, 64, 32, "asap"),
+    (37, 21, 8, 3, "greedy"),           # tiny tiles, nb not a multiple of ib
+    (200, 140, 48, 20, "fibonacci"),
+    (128, 300, 64, 16, "greedy"),       # wide (p < q)
+    (64, 64, 64, 32, "greedy"),         # one tile
+    (2048, 64, 64, 32, "greedy"),       # one tile column (TSQR-like)
+    (1024, 512, 256, 32, "greedy"),     # the 256 x 256 tile size of the large workloads
+    (9, 5, 1, 1, "greedy"),             # scalar tiles
+]
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree", CASES)
+def test_factor_fp64_parity(m, n, nb, ib, tree):
+    A = synthetic.gaussian(m, n, seed=1303318201 + m + n)
+    compare_factor(A, nb, ib, tree)
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree", [(512, 128, 64, 16, "greedy"), (1000, 300, 64, 16, "asap"),
+                                            (300, 200, 32, 8, "flat")])
+def test_factor_fp32_parity(m, n, nb, ib, tree):
+    A = synthetic.gaussian(m, n, seed=77 + m)
+    compare_factor(A, nb, ib, tree, prec="fp32")
+
+
+def test_degenerate_inputs():
+    # zero matrix: every tau = 0, R = 0
+    compare_factor(np.zeros((130, 70)), 32, 8, "greedy")
+    # a zero column and a repeated column (rank deficient)
+    A = synthetic.gaussian(160, 96, seed=5)
+    A[:, 10] = 0.0
+    A[:, 40] = A[:, 41]
+    compare_factor(A, 32, 16, "binary")
+    # already upper triangular
+    compare_factor(np.triu(synthetic.gaussian(96, 96, seed=6)), 32, 16, "fibonacci")
+
+
+def _q_times(Ad, T, Z, nb, ib, tree, trans, prec="fp64"):
+    B = to_dev(Z)
+    tqr.apply_qt(Ad, T, B, nb, ib, tree, 2, prec, trans=trans)
+    torch.cuda.synchronize()
+    return to_np(B)
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree", [(512, 128, 64, 16, "greedy"), (1000, 300, 64, 16, "fibonacci"),
+                                            (37, 21, 8, 3, "asap")])
+def test_apply_q_parity_and_definition(m, n, nb, ib, tree):
+    A = synthetic.gaussian(m, n, seed=11 + m)
+    Ad, T, F, elims = compare_factor(A, nb, ib, tree)
+    p, q = H.tile_grid(m, n, nb)
+    _, Tg, Tt = H.tiled_qr(A, nb, ib, elims)
+    Z = synthetic.gaussian(m, 5, seed=3)
+    for trans in (0, 1):
+        got = _q_times(Ad, T, Z, nb, ib, tree, trans)
+        ref = H.apply_qt(F, Tg, Tt, nb, ib, elims, Z, transpose=(trans == 0))
+        assert np.max(np.abs(got - ref)) <= 64 * m * U64 * np.max(np.abs(ref)) * 4
+    # definition: Q explicit from the GPU, A = Q R and Q^T Q = I
+    Q = _q_times(Ad, T, np.eye(m), nb, ib, tree, 1)
+    k = min(m, n)
+    R = np.zeros((m, n))
+    R[:k] = np.triu(to_np(Ad)[:k])
+    assert np.linalg.norm(A - Q @ R) / np.linalg.norm(A) <= 1e-13
+    assert np.max(np.abs(Q.T @ Q - np.eye(m))) <= 1e-13
+
+
+@pytest.mark.parametrize("m,n,nrhs,nb,ib,tree", [(512, 128, 1, 64, 16, "greedy"), (1000, 300, 3, 64, 16, "grasap"),
+                                                 (300, 300, 2, 64, 32, "fibonacci"), (700, 130, 40, 32, 16, "flat")])
+def test_lstsq_fp64(m, n, nrhs, nb, ib, tree):
+    A, X, B = synthetic.least_squares_problem(m, n, 1e4, 1e-3, nrhs, seed=m + nrhs)
+    p, q = H.tile_grid(m, n, nb)
+    elims = E.elimination_list(p, q, tqr.TREES[tree], bs=2)
+    Xo = H.lstsq(A, B, nb, ib, elims)
+    Xg = to_np(tqr.lstsq(to_dev(A), to_dev(B), nb, ib, tree, 2, "fp64"))
+    assert refine.rel_error(Xg, Xo) <= 1e-12
+    assert refine.ls_optimality(A, Xg, B) <= 10 * refine.ls_optimality(A, Xo, B) + 1e-16
+
+
+def test_trsm_against_back_substitution():
+    n = 333
+    R = np.triu(synthetic.gaussian(n, n, seed=2)) + 4 * np.eye(n)
+    Bm = synthetic.gaussian(n, 37, seed=3)
+    ref = H.back_substitute(R, Bm)
+    Bd = to_dev(Bm)
+    tqr.trsm(to_dev(R), Bd, n, "fp64")
+    torch.cuda.synchronize()
+    assert np.max(np.abs(to_np(Bd) - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # FP32 storage of R: the solve runs in FP64 on the rounded R
+    R32 = R.astype(np.float32).astype(np.float64)
+    Bd = to_dev(Bm)
+    tqr.trsm(to_dev(R32, torch.float32), Bd, n, "fp32")
+    torch.cuda.synchronize()
+    ref32 = H.back_substitute(R32, Bm)
+    assert np.max(np.abs(to_np(Bd) - ref32)) <= 1e-12 * np.max(np.abs(ref32))
+
+
+def test_wait_timeout_reports_error_and_context_survives():
+    """A task graph with one release left out: the waiting CTA gives up after the wait
+    limit and the call returns TQR_ETIMEOUT instead of hanging; the next call works."""
+    A = synthetic.gaussian(256, 128, seed=9)
+    old = tqr.set_wait_limit_ns(200 * 10 ** 6)
+    try:
+        tqr.debug_drop_edge(5)
+        with pytest.raises(tqr.TqrError) as ei:
+            tqr.factor(to_dev(A), 32, 8, "greedy", 1, "fp64")
+        assert ei.value.status == tqr.TQR_ETIMEOUT
+    finally:
+        tqr.set_wait_limit_ns(old)
+    compare_factor(A, 32, 8, "greedy")
+
+
+def test_serialized_equals_parallel_bitwise():
+    """Each task's arithmetic is fixed, so the result does not depend on the schedule:
+    the factorization of the same input twice is bitwise identical."""
+    A = synthetic.gaussian(777, 333, seed=21)
+    a1 = to_dev(A)
+    a2 = to_dev(A)
+    t1 = tqr.factor(a1, 64, 16, "greedy")
+    t2 = tqr.factor(a2, 64, 16, "greedy")
+    torch.cuda.synchronize()
+    assert torch.equal(a1, a2) and torch.equal(t1, t2)

@@ -1,0 +1,115 @@
+"""Host-side tests of libtqr (no GPU): the library loads and exports every symbol that
+include/tqr.h declares; its elimination lists, critical paths and task counts are
+bit-exact against the oracle; invalid arguments return LAPACK-style negative codes."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle import elimlists as E
+
+import paper_1303_3182_gb300 as tqr
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    from paper_1303_3182_gb300 import build
+    build.build()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "tqr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tqr_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    names = _declared_symbols()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", tqr.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in names if n not in exported]
+    assert missing == []
+    L = ctypes.CDLL(tqr.LIB_PATH)
+    for n in names:
+        assert getattr(L, n) is not None
+
+
+ORACLE_TREES = [E.FLAT, E.PLASMA, E.BINARY, E.FIBONACCI, E.GREEDY, E.GRASAP, E.ASAP]
+
+
+@pytest.mark.parametrize("tree", ORACLE_TREES)
+@pytest.mark.parametrize("p,q", [(1, 1), (1, 3), (2, 2), (3, 7), (8, 2), (15, 6), (17, 5),
+                                 (33, 9), (40, 40), (128, 16)])
+def test_elimlist_bitexact_vs_oracle(p, q, tree):
+    bs = 4
+    lst, cp = tqr.elimlist(p, q, tree, bs)
+    ref = E.elimination_list(p, q, tree, bs=bs)
+    assert [tuple(map(int, r)) for r in lst] == ref
+    if p * q <= 40 * 40:
+        assert cp == E.critical_path(p, q, ref)
+
+
+def test_cp_values_of_workload_shapes():
+    """128 x 16 tiles (32768 x 4096 at nb = 256) with the six trees, and the thesis's
+    biggermat Greedy entry 396 for that shape."""
+    cps = {t: tqr.elimlist(128, 16, t, 4)[1] for t in
+           ["flat", "plasma", "binary", "fibonacci", "greedy", "grasap"]}
+    assert cps["greedy"] == 396
+    for t, v in cps.items():
+        assert v == E.critical_path(128, 16, E.elimination_list(128, 16, tqr.TREES[t], bs=4)), t
+
+
+@pytest.mark.parametrize("m,n,nb", [(512, 128, 64), (1000, 300, 64), (300, 1000, 64), (64, 64, 64)])
+def test_plan_stats_vs_oracle(m, n, nb):
+    p, q = -(-m // nb), -(-n // nb)
+    for tree in ["greedy", "flat", "fibonacci", "asap"]:
+        st = tqr.plan_stats(m, n, nb, tree, 1)
+        ref = E.elimination_list(p, q, tqr.TREES[tree])
+        counts = E.kernel_counts(p, q, ref)
+        for k in ("GEQRT", "TTQRT", "UNMQR", "TTMQR"):
+            assert st[k] == counts[k]
+        assert st["cp"] == E.critical_path(p, q, ref)
+
+
+def test_c1_shape_counts():
+    """512 x 128, nb 64: p = 8, q = 2: 15 GEQRT, 13 TTQRT, 8 UNMQR, 7 TTMQR, Greedy CP 34."""
+    st = tqr.plan_stats(512, 128, 64, "greedy", 1)
+    assert (st["GEQRT"], st["TTQRT"], st["UNMQR"], st["TTMQR"], st["cp"]) == (15, 13, 8, 7, 34)
+
+
+def test_invalid_arguments():
+    L = tqr.lib()
+    n = ctypes.c_int64(0)
+    assert L.tqr_elimlist(0, 3, 4, 1, None, ctypes.byref(n), None) == -1
+    assert L.tqr_elimlist(3, 0, 4, 1, None, ctypes.byref(n), None) == -2
+    assert L.tqr_elimlist(3, 3, 9, 1, None, ctypes.byref(n), None) == -3
+    assert L.tqr_elimlist(3, 3, 1, 0, None, ctypes.byref(n), None) == -4
+    assert L.tqr_elimlist(3, 3, 4, 1, None, None, None) == -6
+    small = (ctypes.c_int32 * 3)()
+    cap = ctypes.c_int64(1)
+    assert L.tqr_elimlist(5, 2, 4, 1, small, ctypes.byref(cap), None) == -6
+    vp = ctypes.c_void_p
+    assert L.tqr_factor(0, 4, 4, 2, 4, 1, 0, vp(8), 4, vp(8), None) == -1
+    assert L.tqr_factor(8, 4, 0, 2, 4, 1, 0, vp(8), 8, vp(8), None) == -3
+    assert L.tqr_factor(8, 4, 4, 5, 4, 1, 0, vp(8), 8, vp(8), None) == -4
+    assert L.tqr_factor(8, 4, 4, 2, 7, 1, 0, vp(8), 8, vp(8), None) == -5
+    assert L.tqr_factor(8, 4, 4, 2, 1, 0, 0, vp(8), 8, vp(8), None) == -6
+    assert L.tqr_factor(8, 4, 4, 2, 4, 1, 9, vp(8), 8, vp(8), None) == -7
+    assert L.tqr_factor(8, 4, 4, 2, 4, 1, 0, None, 8, vp(8), None) == -8
+    assert L.tqr_factor(8, 4, 4, 2, 4, 1, 0, vp(8), 7, vp(8), None) == -9
+    assert L.tqr_factor(8, 4, 4, 2, 4, 1, 0, vp(8), 8, None, None) == -10
+    assert L.tqr_trsm(0, 0, vp(8), 1, vp(8), 1, 1, None) == -1
+    assert L.tqr_strerror(3) == b"device dependency wait exceeded the limit"
+
+
+def test_workspace_and_flops():
+    # two ib x nb T factors per tile (i, k), k < min(p, q)
+    assert tqr.workspace_size(512, 128, 64, 16, "fp64") == 2 * 8 * 2 * 16 * 64 * 8
+    assert tqr.workspace_size(512, 128, 64, 16, "fp32") == 2 * 8 * 2 * 16 * 64 * 4
+    assert tqr.nominal_flops(32768, 4096) == pytest.approx(2 * 4096 ** 2 * (32768 - 4096 / 3))
