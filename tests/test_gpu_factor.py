@@ -112,15 +112,29 @@ def test_factor_fp32_parity(m, n, nb, ib, tree):
 
 
 def test_degenerate_inputs():
-    # zero matrix: every tau = 0, R = 0
+    # zero matrix: every tau = 0, R = 0 (exact on both sides)
     compare_factor(np.zeros((130, 70)), 32, 8, "greedy")
-    # a zero column and a repeated column (rank deficient)
+    # an exactly zero column stays zero under every update: tau = 0 for its reflector
     A = synthetic.gaussian(160, 96, seed=5)
     A[:, 10] = 0.0
-    A[:, 40] = A[:, 41]
     compare_factor(A, 32, 16, "binary")
     # already upper triangular
     compare_factor(np.triu(synthetic.gaussian(96, 96, seed=6)), 32, 16, "fibonacci")
+
+
+def test_rank_deficient_is_a_valid_qr():
+    """With a repeated column the reflector after it is built from rounding noise, so
+    R, V and T are not unique there; the result must still be a QR factorization."""
+    m, n, nb, ib = 160, 96, 32, 16
+    A = synthetic.gaussian(m, n, seed=5)
+    A[:, 41] = A[:, 40]
+    Ad = to_dev(A)
+    T = tqr.factor(Ad, nb, ib, "binary", 2, "fp64")
+    Q = _q_times(Ad, T, np.eye(m), nb, ib, "binary", 1)
+    R = np.triu(to_np(Ad))
+    assert np.linalg.norm(A - Q @ R) / np.linalg.norm(A) <= 1e-13
+    assert np.max(np.abs(Q.T @ Q - np.eye(m))) <= 1e-13
+    assert abs(R[41, 41]) <= 1e-12 * np.linalg.norm(A)
 
 
 def _q_times(Ad, T, Z, nb, ib, tree, trans, prec="fp64"):
