@@ -196,10 +196,15 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
   return TQR_OK;
 }
 
+bool is_tensor_prec(int prec) { return prec == TQR_BF16 || prec == TQR_FP16 || prec == TQR_BF16X3; }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec) {
   if (m < 1) return -1;
   if (n < 1) return -2;
   if (nb < 1 || nb > 256) return -3;
+  if (is_tensor_prec(prec) && nb != kMixedNB) return -3;
   if (ib < 1 || ib > nb || ib > 32) return -4;
   if (tree < TQR_FLAT || tree > TQR_ASAP) return -5;
   if (tree == TQR_PLASMA && bs < 1) return -6;
@@ -258,6 +263,7 @@ int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T
   const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
   const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
   *T_bytes = static_cast<size_t>(2 * P * K) * ib * nb * esz;
+  if (is_tensor_prec(prec)) *T_bytes = align_up(*T_bytes, 1024) + static_cast<size_t>(2 * P * K) * mixed_slot_bytes();
   return TQR_OK;
 }
 
@@ -268,9 +274,8 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
   if (!A) return -8;
   if (lda < m) return -9;
   if (!T) return -10;
-  if (prec != TQR_FP64 && prec != TQR_FP32) return TQR_EUNSUPPORTED;
   const bool dbl = prec == TQR_FP64;
-  if (executor_smem_bytes(nb, ib, dbl, false) == 0) {
+  if (!is_tensor_prec(prec) && executor_smem_bytes(nb, ib, dbl, false) == 0) {
     g_last_error = "nb/ib too large for one SM's shared memory";
     return TQR_EUNSUPPORTED;
   }
@@ -289,6 +294,13 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
     prm.Q = Q;
     prm.T = T;
     prm.B = nullptr;
+    if (is_tensor_prec(prec)) {
+      const int64_t K = std::min(P, Q);
+      prm.mixed = 1;
+      prm.ops = static_cast<char *>(T) + align_up(static_cast<size_t>(2 * P * K) * ib * nb * sizeof(float), 1024);
+      prm.nprod = prec == TQR_BF16X3 ? 3 : 1;
+      prm.fmt = prec == TQR_FP16 ? 0 : 1;
+    }
     return run_plan(plan, prm, dbl, static_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc &) {
     return TQR_ENOMEM;

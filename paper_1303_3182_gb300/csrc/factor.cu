@@ -547,6 +547,14 @@ __device__ void task_ttmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *c1
   }
 }
 
+}  // namespace
+}  // namespace tqr
+
+#include "mixed_tasks.cuh"
+
+namespace tqr {
+namespace {
+
 // Bounded wait until *counter == 0.  Returns false if this CTA must stop.
 __device__ bool wait_ready(const ExecParams &p, int t) {
   const int32_t *cnt = p.counters + t;
@@ -564,11 +572,30 @@ __device__ bool wait_ready(const ExecParams &p, int t) {
   }
 }
 
-template <typename Real, typename S>
+template <typename Real, typename S, bool kMixed>
 __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task, s_stop;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
   Smem<S> s = carve<S>(smem_raw, p.nb, p.ib);
+  MixedState ms{};
+  if (kMixed) {
+    if (threadIdx.x == 0) {
+      umma::mbar_init(&s_bar[0], 1);
+      umma::mbar_init(&s_bar[1], 1);
+      umma::mbar_init_fence();
+    }
+    if (threadIdx.x < 32) umma::tmem_alloc(&s_tmem, 512);
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    ms.bar_ld = &s_bar[0];
+    ms.bar_mma = &s_bar[1];
+    ms.tmem = s_tmem;
+    ms.ld_phase = 0;
+    ms.mma_phase = 0;
+  }
   for (;;) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(p.next, 1);
@@ -585,11 +612,23 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     switch (task.kind) {
       case kGeqrt:
         task_geqrt<Real, S>(p, s, task.i, task.k);
+        if (kMixed) {
+          __syncthreads();
+          prep_geqrt_ops(p, smem_raw, task.i, task.k);
+        }
         break;
       case kTtqrt:
         task_ttqrt<Real, S>(p, s, task.i, task.piv, task.k);
+        if (kMixed) {
+          __syncthreads();
+          prep_ttqrt_ops(p, smem_raw, task.i, task.k);
+        }
         break;
       case kUnmqr: {
+        if (kMixed) {
+          task_unmqr_umma(p, smem_raw, ms, task.i, task.k, task.j);
+          break;
+        }
         Real *A = static_cast<Real *>(p.A);
         const int ncols = static_cast<int>(lmin(nb, p.n - int64_t(task.j) * nb));
         task_unmqr<Real, S, Real>(p, s, task.i, task.k, tile_ptr(A, p.lda, nb, task.i, task.j), p.lda,
@@ -597,6 +636,10 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
         break;
       }
       case kTtmqr: {
+        if (kMixed) {
+          task_ttmqr_umma(p, smem_raw, ms, task.i, task.piv, task.k, task.j);
+          break;
+        }
         Real *A = static_cast<Real *>(p.A);
         const int ncols = static_cast<int>(lmin(nb, p.n - int64_t(task.j) * nb));
         task_ttmqr<Real, S, Real>(p, s, task.i, task.k, tile_ptr(A, p.lda, nb, task.piv, task.j),
@@ -622,11 +665,16 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
       for (int e = p.succ_ptr[t]; e < p.succ_ptr[t + 1]; ++e) atomicSub(p.counters + p.succ_idx[e], 1);
     }
   }
+  if (kMixed) {
+    umma::fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) umma::tmem_dealloc(s_tmem, 512);
+  }
 }
 
-template <typename Real, typename S>
+template <typename Real, typename S, bool kMixed>
 int launch_typed(const ExecParams &p, void *stream, size_t smem) {
-  auto kern = executor_kernel<Real, S>;
+  auto kern = executor_kernel<Real, S, kMixed>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
@@ -651,12 +699,18 @@ size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q) {
   return bytes <= 227 * 1024 ? bytes : 0;
 }
 
+size_t mixed_slot_bytes() { return kSlotBytes; }
+
+size_t mixed_executor_smem_bytes() { return mixed_smem_bytes(); }
+
 int launch_executor(const ExecParams &p, bool real_is_double, void *stream) {
   const bool apply_q = p.B != nullptr;
+  if (p.mixed && !apply_q && !real_is_double)
+    return launch_typed<float, float, true>(p, stream, mixed_smem_bytes());
   const size_t smem = executor_smem_bytes(p.nb, p.ib, real_is_double, apply_q);
-  if (real_is_double) return launch_typed<double, double>(p, stream, smem);
-  if (apply_q) return launch_typed<float, double>(p, stream, smem);
-  return launch_typed<float, float>(p, stream, smem);
+  if (real_is_double) return launch_typed<double, double, false>(p, stream, smem);
+  if (apply_q) return launch_typed<float, double, false>(p, stream, smem);
+  return launch_typed<float, float, false>(p, stream, smem);
 }
 
 }  // namespace tqr

@@ -107,6 +107,11 @@ struct ExecParams {
   int32_t *status;       // 0 or kStatusTimeout | (task << 8)
   int ntask;
   int64_t wait_limit_ns;
+  // tensor-core (mixed) mode: split operand images, products per multiply, 16-bit format
+  void *ops;             // 2 * P * min(P,Q) slots of 6 operand images (else null)
+  int nprod;             // 3 = split bf16 x3, 1 = one product
+  int fmt;               // 1 = bf16, 0 = fp16
+  int mixed;             // 1: GEQRT/TTQRT prepare images, UNMQR/TTMQR run on tcgen05
 };
 
 // Launches the persistent tile-task executor on "stream".  real_is_double selects the
@@ -114,6 +119,11 @@ struct ExecParams {
 int launch_executor(const ExecParams &p, bool real_is_double, void *stream);
 // Dynamic shared memory the executor needs (0 if nb/ib do not fit on one SM).
 size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q);
+// Tile size, bytes per factored tile of operand images, and shared memory of the
+// tensor-core (mixed) executor.
+constexpr int kMixedNB = 128;
+size_t mixed_slot_bytes();
+size_t mixed_executor_smem_bytes();
 
 // Wavefront triangular solve R X = B (R upper n x n in A, double or float), X over B.
 // flags: device int32[ceil(n/TB) + 1] scratch (ticket + per-block flags).
