@@ -223,7 +223,10 @@ def test_serialized_equals_parallel_bitwise():
     A = synthetic.gaussian(777, 333, seed=21)
     a1 = to_dev(A)
     a2 = to_dev(A)
-    t1 = tqr.factor(a1, 64, 16, "greedy")
-    t2 = tqr.factor(a2, 64, 16, "greedy")
+    ws = tqr.workspace_size(777, 333, 64, 16, "fp64")
+    t1 = torch.zeros(ws, dtype=torch.uint8, device="cuda")  # unwritten slots compare equal
+    t2 = torch.zeros(ws, dtype=torch.uint8, device="cuda")
+    tqr.factor(a1, 64, 16, "greedy", T=t1)
+    tqr.factor(a2, 64, 16, "greedy", T=t2)
     torch.cuda.synchronize()
     assert torch.equal(a1, a2) and torch.equal(t1, t2)

@@ -44,7 +44,10 @@ def to_np(t):
 
 def factor_mixed(A, prec, tree="greedy", ib=32):
     Ad = to_dev(A, torch.float32)
-    T = tqr.factor(Ad, 128, ib, tree, 2, prec)
+    m, n = A.shape
+    # zero-filled so that slots no task writes (tiles above the diagonal) compare equal
+    T = torch.zeros(tqr.workspace_size(m, n, 128, ib, prec), dtype=torch.uint8, device="cuda")
+    tqr.factor(Ad, 128, ib, tree, 2, prec, T=T)
     torch.cuda.synchronize()
     return Ad, T
 
