@@ -149,6 +149,16 @@ int tqr_sync_status(void *stream);
 int tqr_set_timing(int on);
 int tqr_kernel_time(int kind, double *ms_total, int64_t *launches, int reset);
 
+/* Per-task execution trace (a Gantt chart of the persistent executor).  With tracing on,
+ * each executor launch records for every task the globaltimer (ns) when a CTA claimed
+ * it, when its dependencies were met, when it finished, and the SM it ran on.
+ * tqr_trace_fetch copies the last traced launch: 8 int64 per task in executor order =
+ * {kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR, 4/5 apply-Q), i, piv, k | j << 16, claim,
+ * start, end, sm}.  With out == NULL it returns the task count; otherwise the count
+ * copied, -1 if cap is too small or nothing was traced, -2 on a CUDA error. */
+int tqr_set_trace(int on);
+int64_t tqr_trace_fetch(int64_t *out, int64_t cap);
+
 const char *tqr_strerror(int status);
 const char *tqr_last_error(void);      /* detail of the last TQR_ECUDA / internal error */
 void tqr_finalize(void);               /* free every cached plan                         */

@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
             "tqr_plan_stats": (i32, [i64, i64, i32, i32, i32, c_i64p]),
             "tqr_debug_drop_edge": (None, [i64]),
             "tqr_set_timing": (i32, [i32]),
+            "tqr_set_trace": (i32, [i32]),
+            "tqr_trace_fetch": (i64, [c_i64p, i64]),
             "tqr_kernel_time": (i32, [i32, ctypes.POINTER(ctypes.c_double), c_i64p, i32]),
         }
         for name, (res, args) in sig.items():
@@ -170,6 +172,23 @@ def kernel_time(kind, reset: bool = True):
     k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
     _check("tqr_kernel_time", lib().tqr_kernel_time(k, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
     return ms.value, n.value
+
+
+def set_trace(on: bool) -> bool:
+    """Record per-task globaltimer stamps in every executor launch (tqr_set_trace)."""
+    return bool(lib().tqr_set_trace(1 if on else 0))
+
+
+def trace_fetch():
+    """The last traced launch as an (ntask, 8) int64 array: kind, i, piv, k | j << 16,
+    claim, start, end (ns), sm."""
+    L = lib()
+    n = L.tqr_trace_fetch(None, 0)
+    out = np.zeros((max(n, 1), 8), dtype=np.int64)
+    got = L.tqr_trace_fetch(out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n)
+    if got < 0:
+        raise TqrError("tqr_trace_fetch", int(-got), "no trace")
+    return out[:got]
 
 
 def debug_drop_edge(e: int) -> None:

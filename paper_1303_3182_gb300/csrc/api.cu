@@ -24,6 +24,11 @@ thread_local std::string g_last_error;
 int64_t g_wait_limit_ns = 20LL * 1000 * 1000 * 1000;
 int g_sync = 1;
 int g_timing = 0;
+int g_trace = 0;
+// device trace of the last traced executor run and the task table it refers to
+int64_t *g_trace_buf = nullptr;
+size_t g_trace_cap = 0;
+std::vector<Task> g_trace_tasks;
 // per kernel kind: accumulated device milliseconds and launch count (tqr_kernel_time)
 double g_kernel_ms[4] = {0, 0, 0, 0};
 int64_t g_kernel_launches[4] = {0, 0, 0, 0};
@@ -188,6 +193,20 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
   prm.status = plan->d_state + 1;
   prm.ntask = static_cast<int>(n);
   prm.wait_limit_ns = g_wait_limit_ns;
+  prm.trace = nullptr;
+  if (g_trace) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_trace_cap < n) {
+      cudaFree(g_trace_buf);
+      g_trace_buf = nullptr;
+      g_trace_cap = 0;
+      if (cudaMalloc(&g_trace_buf, n * 4 * sizeof(int64_t)) == cudaSuccess) g_trace_cap = n;
+    }
+    if (g_trace_buf) {
+      prm.trace = g_trace_buf;
+      g_trace_tasks = plan->g.tasks;
+    }
+  }
   LaunchTimer timer(prm.B ? 1 : 0, st);
   const int rc = launch_executor(prm, dbl, st);
   timer.stop(st);
@@ -487,6 +506,10 @@ void tqr_finalize(void) {
   g_plans.clear();
   for (auto &kv : g_scratch) cudaFree(kv.second.flags);
   g_scratch.clear();
+  cudaFree(g_trace_buf);
+  g_trace_buf = nullptr;
+  g_trace_cap = 0;
+  g_trace_tasks.clear();
 }
 
 int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6]) {
@@ -522,6 +545,36 @@ int tqr_kernel_time(int kind, double *ms_total, int64_t *launches, int reset) {
     g_kernel_launches[kind] = 0;
   }
   return TQR_OK;
+}
+
+int tqr_set_trace(int on) {
+  const int old = g_trace;
+  g_trace = on ? 1 : 0;
+  return old;
+}
+
+int64_t tqr_trace_fetch(int64_t *out, int64_t cap) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int64_t n = static_cast<int64_t>(g_trace_tasks.size());
+  if (!out) return n;
+  if (cap < n || !g_trace_buf) return -1;
+  std::vector<int64_t> stamps(static_cast<size_t>(n) * 4);
+  if (cudaMemcpy(stamps.data(), g_trace_buf, stamps.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return -2;
+  for (int64_t t = 0; t < n; ++t) {
+    const Task &k = g_trace_tasks[t];
+    int64_t *o = out + 8 * t;
+    o[0] = k.kind;
+    o[1] = k.i;
+    o[2] = k.piv;
+    o[3] = static_cast<int64_t>(k.k) | (static_cast<int64_t>(k.j) << 16);
+    o[4] = stamps[4 * t + 0];
+    o[5] = stamps[4 * t + 1];
+    o[6] = stamps[4 * t + 2];
+    o[7] = stamps[4 * t + 3];
+  }
+  return n;
 }
 
 void tqr_debug_drop_edge(int64_t e) {

@@ -600,7 +600,15 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(p.next, 1);
       int stop = t >= p.ntask;
+      const uint64_t t_claim = p.trace ? globaltimer_ns() : 0;
       if (!stop && !wait_ready(p, t)) stop = 1;
+      if (p.trace && !stop) {
+        uint32_t sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        p.trace[4 * static_cast<int64_t>(t) + 0] = static_cast<int64_t>(t_claim);
+        p.trace[4 * static_cast<int64_t>(t) + 1] = static_cast<int64_t>(globaltimer_ns());
+        p.trace[4 * static_cast<int64_t>(t) + 3] = sm;
+      }
       s_task = t;
       s_stop = stop;
     }
@@ -661,6 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (p.trace) p.trace[4 * static_cast<int64_t>(t) + 2] = static_cast<int64_t>(globaltimer_ns());
       __threadfence();
       for (int e = p.succ_ptr[t]; e < p.succ_ptr[t + 1]; ++e) atomicSub(p.counters + p.succ_idx[e], 1);
     }

@@ -112,6 +112,7 @@ struct ExecParams {
   int nprod;             // 3 = split bf16 x3, 1 = one product
   int fmt;               // 1 = bf16, 0 = fp16
   int mixed;             // 1: GEQRT/TTQRT prepare images, UNMQR/TTMQR run on tcgen05
+  int64_t *trace;        // optional: per task {claim, start, end, sm} globaltimer stamps
 };
 
 // Launches the persistent tile-task executor on "stream".  real_is_double selects the
