@@ -151,10 +151,13 @@ int tqr_kernel_time(int kind, double *ms_total, int64_t *launches, int reset);
 
 /* Per-task execution trace (a Gantt chart of the persistent executor).  With tracing on,
  * each executor launch records for every task the globaltimer (ns) when a CTA claimed
- * it, when its dependencies were met, when it finished, and the SM it ran on.
- * tqr_trace_fetch copies the last traced launch: 8 int64 per task in executor order =
+ * it, when its dependencies were met, when it finished, the SM it ran on, and the time
+ * (ns) spent in up to four phases of the kernel (panels: factorization loops, T build,
+ * trailing update, operand images; tensor-core updates: operand conversion, first
+ * product, W conversion, second product and epilogue).
+ * tqr_trace_fetch copies the last traced launch: 12 int64 per task in executor order =
  * {kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR, 4/5 apply-Q), i, piv, k | j << 16, claim,
- * start, end, sm}.  With out == NULL it returns the task count; otherwise the count
+ * start, end, sm, phase0, phase1, phase2, phase3}.  With out == NULL it returns the task count; otherwise the count
  * copied, -1 if cap is too small or nothing was traced, -2 on a CUDA error. */
 int tqr_set_trace(int on);
 int64_t tqr_trace_fetch(int64_t *out, int64_t cap);

@@ -180,11 +180,11 @@ def set_trace(on: bool) -> bool:
 
 
 def trace_fetch():
-    """The last traced launch as an (ntask, 8) int64 array: kind, i, piv, k | j << 16,
-    claim, start, end (ns), sm."""
+    """The last traced launch as an (ntask, 12) int64 array: kind, i, piv, k | j << 16,
+    claim, start, end (ns), sm, and four phase durations (ns)."""
     L = lib()
     n = L.tqr_trace_fetch(None, 0)
-    out = np.zeros((max(n, 1), 8), dtype=np.int64)
+    out = np.zeros((max(n, 1), 12), dtype=np.int64)
     got = L.tqr_trace_fetch(out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n)
     if got < 0:
         raise TqrError("tqr_trace_fetch", int(-got), "no trace")

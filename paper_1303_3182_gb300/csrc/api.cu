@@ -200,7 +200,7 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
       cudaFree(g_trace_buf);
       g_trace_buf = nullptr;
       g_trace_cap = 0;
-      if (cudaMalloc(&g_trace_buf, n * 4 * sizeof(int64_t)) == cudaSuccess) g_trace_cap = n;
+      if (cudaMalloc(&g_trace_buf, n * 8 * sizeof(int64_t)) == cudaSuccess) g_trace_cap = n;
     }
     if (g_trace_buf) {
       prm.trace = g_trace_buf;
@@ -398,10 +398,17 @@ int tqr_lstsq_workspace_size(int64_t m, int64_t n, int64_t nrhs, int nb, int ib,
   if (!bytes) return -7;
   size_t tb = 0;
   if ((rc = tqr_workspace_size(m, n, nb, ib, prec, &tb)) != 0) return rc;
-  const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
-  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
-  *bytes = align(static_cast<size_t>(m) * n * esz) + align(tb) +
-           align(static_cast<size_t>(m) * std::max<int64_t>(nrhs, 1) * sizeof(double));
+  const size_t nr = static_cast<size_t>(std::max<int64_t>(nrhs, 1));
+  if (prec == TQR_FP64) {
+    *bytes = align_up(static_cast<size_t>(m) * n * sizeof(double), 256) + align_up(tb, 256) +
+             align_up(static_cast<size_t>(m) * nr * sizeof(double), 256);
+  } else {
+    const size_t ldf = align_up(static_cast<size_t>(m), 32);
+    const size_t nr64 = std::min<size_t>(nr, 64);
+    *bytes = align_up(ldf * n * sizeof(float), 1024) + align_up(tb, 1024) +
+             align_up(static_cast<size_t>(m) * nr * sizeof(double), 1024) +
+             align_up(lsqr_work_doubles(m, n, static_cast<int>(nr64)) * sizeof(double), 1024);
+  }
   return TQR_OK;
 }
 
@@ -417,39 +424,79 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
   if (lda < m) return -10;
   if (!B || ldb < m) return -11;
   if (!X || ldx < n) return -13;
-  (void)tol;
-  (void)max_iter;
   if (iters) *iters = 0;
   if (nrhs == 0) return TQR_OK;
-  if (prec != TQR_FP64) return TQR_EUNSUPPORTED;
   size_t need = 0;
   if ((rc = tqr_lstsq_workspace_size(m, n, nrhs, nb, ib, prec, &need)) != 0) return rc;
   if (!workspace || ws_bytes < need) return -18;
-  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   char *ws = static_cast<char *>(workspace);
-  double *Aw = reinterpret_cast<double *>(ws);
   size_t tb = 0;
   tqr_workspace_size(m, n, nb, ib, prec, &tb);
-  void *Tw = ws + align(static_cast<size_t>(m) * n * sizeof(double));
-  double *Bw = reinterpret_cast<double *>(static_cast<char *>(Tw) + align(tb));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpy2DAsync(Aw, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
-                                    cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(Bw, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
+  if (prec == TQR_FP64) {
+    double *Aw = reinterpret_cast<double *>(ws);
+    void *Tw = ws + align_up(static_cast<size_t>(m) * n * sizeof(double), 256);
+    double *Bw = reinterpret_cast<double *>(static_cast<char *>(Tw) + align_up(tb, 256));
+    cudaError_t e = cudaMemcpy2DAsync(Aw, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
+                                      cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Bw, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
+                            cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-in");
+    if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Aw, m, Tw, stream)) != 0) return rc;
+    if ((rc = tqr_apply_qt(m, n, nb, ib, tree, bs, prec, 0, Aw, m, Tw, Bw, m, nrhs, stream)) != 0) return rc;
+    if ((rc = tqr_trsm(n, prec, Aw, m, Bw, m, nrhs, stream)) != 0) return rc;
+    e = cudaMemcpy2DAsync(X, ldx * sizeof(double), Bw, m * sizeof(double), n * sizeof(double), nrhs,
                           cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-out");
+    if (g_sync) {
+      e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "lstsq");
+    }
+    return TQR_OK;
+  }
+  // low-precision factorization of an FP32 copy, then FP64 LSQR refinement
+  const int64_t ldf = static_cast<int64_t>(align_up(static_cast<size_t>(m), 32));
+  float *Af = reinterpret_cast<float *>(ws);
+  char *p = ws + align_up(static_cast<size_t>(ldf) * n * sizeof(float), 1024);
+  void *Tw = p;
+  p += align_up(tb, 1024);
+  double *Bw = reinterpret_cast<double *>(p);
+  p += align_up(static_cast<size_t>(m) * nrhs * sizeof(double), 1024);
+  double *lw = reinterpret_cast<double *>(p);
+  int rcv = convert_to_f32(A, lda, Af, ldf, m, n, stream);
+  if (rcv) return cuda_fail(static_cast<cudaError_t>(rcv), "lstsq convert");
+  if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Af, ldf, Tw, stream)) != 0) return rc;
+  cudaError_t e = cudaMemcpy2DAsync(Bw, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
+                                    cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-in");
-  if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Aw, m, Tw, stream)) != 0) return rc;
-  if ((rc = tqr_apply_qt(m, n, nb, ib, tree, bs, prec, 0, Aw, m, Tw, Bw, m, nrhs, stream)) != 0) return rc;
-  if ((rc = tqr_trsm(n, prec, Aw, m, Bw, m, nrhs, stream)) != 0) return rc;
+  if ((rc = tqr_apply_qt(m, n, nb, ib, tree, bs, prec, 0, Af, ldf, Tw, Bw, m, nrhs, stream)) != 0) return rc;
+  if ((rc = tqr_trsm(n, prec, Af, ldf, Bw, m, nrhs, stream)) != 0) return rc;
   e = cudaMemcpy2DAsync(X, ldx * sizeof(double), Bw, m * sizeof(double), n * sizeof(double), nrhs,
                         cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-out");
-  if (g_sync) {
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "lstsq");
+  Scratch *s = nullptr;
+  if ((rc = get_scratch(trsm_flag_count(n), &s)) != 0) return rc;
+  int32_t *status = s->flags + s->cap;
+  e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "lstsq reset");
+  int worst_iters = 0;
+  bool converged = true;
+  LaunchTimer timer(3, st);
+  for (int64_t r0 = 0; r0 < nrhs; r0 += 64) {
+    const int nr = static_cast<int>(std::min<int64_t>(64, nrhs - r0));
+    int it = 0;
+    const int lrc = lsqr_refine(m, n, nr, A, lda, Af, ldf, B + r0 * ldb, ldb, X + r0 * ldx, ldx,
+                                tol > 0 ? tol : 1e-14, max_iter > 0 ? max_iter : 100, &it, lw, s->flags, status,
+                                g_wait_limit_ns, stream);
+    if (lrc > 0) return cuda_fail(static_cast<cudaError_t>(lrc), "lstsq refinement");
+    if (lrc < 0) converged = false;
+    worst_iters = std::max(worst_iters, it);
   }
-  return TQR_OK;
+  timer.stop(st);
+  if (iters) *iters = worst_iters;
+  if ((rc = read_status(status, st)) != 0) return rc;
+  return converged ? TQR_OK : TQR_ENOCONV;
 }
 
 double tqr_nominal_flops(int64_t m, int64_t n) {
@@ -558,21 +605,18 @@ int64_t tqr_trace_fetch(int64_t *out, int64_t cap) {
   const int64_t n = static_cast<int64_t>(g_trace_tasks.size());
   if (!out) return n;
   if (cap < n || !g_trace_buf) return -1;
-  std::vector<int64_t> stamps(static_cast<size_t>(n) * 4);
+  std::vector<int64_t> stamps(static_cast<size_t>(n) * 8);
   if (cudaMemcpy(stamps.data(), g_trace_buf, stamps.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) !=
       cudaSuccess)
     return -2;
   for (int64_t t = 0; t < n; ++t) {
     const Task &k = g_trace_tasks[t];
-    int64_t *o = out + 8 * t;
+    int64_t *o = out + 12 * t;
     o[0] = k.kind;
     o[1] = k.i;
     o[2] = k.piv;
     o[3] = static_cast<int64_t>(k.k) | (static_cast<int64_t>(k.j) << 16);
-    o[4] = stamps[4 * t + 0];
-    o[5] = stamps[4 * t + 1];
-    o[6] = stamps[4 * t + 2];
-    o[7] = stamps[4 * t + 3];
+    for (int q = 0; q < 8; ++q) o[4 + q] = stamps[8 * t + q];
   }
   return n;
 }

@@ -56,6 +56,17 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int32_t *p) {
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg(const float *p) { return static_cast<double>(__ldcg(p)); }
 
+// Optional phase accounting of one task for the execution trace: ph[0] holds the last
+// timestamp, ph[1..4] accumulate the time spent in up to four phases (thread 0 only).
+__device__ __forceinline__ void phase_mark(uint64_t *ph, int slot) {
+  if (ph && threadIdx.x == 0) {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    ph[1 + slot] += t - ph[0];
+    ph[0] = t;
+  }
+}
+
 template <typename S>
 __device__ __forceinline__ S warp_sum(S v) {
 #pragma unroll
@@ -76,6 +87,7 @@ struct Smem {
   S *G;          // [ldt * ib]  Gram matrix of the reflectors of a block
   S *P1;         // [ldt * ib]  diagonal block of R(piv) during TTQRT
   int ldv, ldw, ldt;
+  uint64_t *ph;  // phase clock of the execution trace, or null
 };
 
 __host__ __device__ inline int odd_ld(int x) { return x | 1; }
@@ -334,6 +346,7 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
       }
       __syncthreads();
     }
+    phase_mark(s.ph, 0);
     // Gram matrix G(a,c) = v_a . v_c (a < c) of the block's reflectors
     const int npair = kb * (kb - 1) / 2;
     for (int pidx = warp; pidx < npair; pidx += kWarps) {
@@ -350,6 +363,7 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
     store_block(blk, p.lda, s.V, s.ldv, rows, kb);
     store_t(Tg, ib, c0, width, s, kb);
     __syncthreads();
+    phase_mark(s.ph, 1);
     // explicit reflector block: unit diagonal, zeros above
     for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
       const int c = idx / kb, r = idx - c * kb;
@@ -366,6 +380,7 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
       store_block(cblk, p.lda, s.C, s.ldv, rows, w);
       __syncthreads();
     }
+    phase_mark(s.ph, 2);
   }
 }
 
@@ -437,6 +452,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
       }
       __syncthreads();
     }
+    phase_mark(s.ph, 0);
     const int npair = kb * (kb - 1) / 2;
     for (int pidx = warp; pidx < npair; pidx += kWarps) {
       int c = 1, base = 0;
@@ -460,6 +476,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
     }
     store_t(Tt, ib, c0, width, s, kb);
     __syncthreads();
+    phase_mark(s.ph, 1);
     // trailing columns of the same tile column: [R(piv) rows c0..c0+kb-1 ; tile i rows 0..rb-1]
     for (int cs = c0 + kb; cs < K; cs += kCW) {
       const int w = min(kCW, K - cs);
@@ -473,6 +490,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
       store_block(c2, p.lda, s.C, s.ldv, rb, w);
       __syncthreads();
     }
+    phase_mark(s.ph, 2);
   }
 }
 
@@ -578,8 +596,11 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   __shared__ int s_task, s_stop;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
+  __shared__ uint64_t s_ph[5];
   Smem<S> s = carve<S>(smem_raw, p.nb, p.ib);
+  s.ph = p.trace ? s_ph : nullptr;
   MixedState ms{};
+  ms.ph = s.ph;
   if (kMixed) {
     if (threadIdx.x == 0) {
       umma::mbar_init(&s_bar[0], 1);
@@ -605,9 +626,12 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
       if (p.trace && !stop) {
         uint32_t sm;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
-        p.trace[4 * static_cast<int64_t>(t) + 0] = static_cast<int64_t>(t_claim);
-        p.trace[4 * static_cast<int64_t>(t) + 1] = static_cast<int64_t>(globaltimer_ns());
-        p.trace[4 * static_cast<int64_t>(t) + 3] = sm;
+        const uint64_t now = globaltimer_ns();
+        p.trace[8 * static_cast<int64_t>(t) + 0] = static_cast<int64_t>(t_claim);
+        p.trace[8 * static_cast<int64_t>(t) + 1] = static_cast<int64_t>(now);
+        p.trace[8 * static_cast<int64_t>(t) + 3] = sm;
+        s_ph[0] = now;
+        s_ph[1] = s_ph[2] = s_ph[3] = s_ph[4] = 0;
       }
       s_task = t;
       s_stop = stop;
@@ -622,14 +646,18 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
         task_geqrt<Real, S>(p, s, task.i, task.k);
         if (kMixed) {
           __syncthreads();
+          phase_mark(s.ph, 2);
           prep_geqrt_ops(p, smem_raw, task.i, task.k);
+          phase_mark(s.ph, 3);
         }
         break;
       case kTtqrt:
         task_ttqrt<Real, S>(p, s, task.i, task.piv, task.k);
         if (kMixed) {
           __syncthreads();
+          phase_mark(s.ph, 2);
           prep_ttqrt_ops(p, smem_raw, task.i, task.k);
+          phase_mark(s.ph, 3);
         }
         break;
       case kUnmqr: {
@@ -669,7 +697,10 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (p.trace) p.trace[4 * static_cast<int64_t>(t) + 2] = static_cast<int64_t>(globaltimer_ns());
+      if (p.trace) {
+        p.trace[8 * static_cast<int64_t>(t) + 2] = static_cast<int64_t>(globaltimer_ns());
+        for (int q = 0; q < 4; ++q) p.trace[8 * static_cast<int64_t>(t) + 4 + q] = static_cast<int64_t>(s_ph[1 + q]);
+      }
       __threadfence();
       for (int e = p.succ_ptr[t]; e < p.succ_ptr[t + 1]; ++e) atomicSub(p.counters + p.succ_idx[e], 1);
     }

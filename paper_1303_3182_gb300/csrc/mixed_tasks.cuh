@@ -40,6 +40,7 @@ struct MixedState {
   uint64_t *bar_ld, *bar_mma;
   uint32_t tmem;
   uint32_t ld_phase, mma_phase;
+  uint64_t *ph;  // phase clock of the execution trace, or null
 };
 
 __device__ __forceinline__ unsigned char *ops_slot(const ExecParams &p, int i, int k, int which) {
@@ -370,6 +371,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   c_transposed_image(bufA, C, p.lda, mb, ncols, p.fmt, lo);
   umma::fence_proxy_async();
   sync_all_tc();
+  phase_mark(ms.ph, 0);
   if (threadIdx.x == 0) {
     wait_or_flag(p, ms.bar_ld, ms.ld_phase);
     umma::fence_after();
@@ -380,9 +382,11 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
+  phase_mark(ms.ph, 1);
   w_image_from_tmem(bufA, ms.tmem, p.fmt, lo);
   umma::fence_proxy_async();
   sync_all_tc();
+  phase_mark(ms.ph, 2);
   if (threadIdx.x == 0) {
     issue_gemm(ms.tmem + 128, bufZ, bufA, p.nprod, p.fmt, 0);
     umma::commit(ms.bar_mma);
@@ -392,6 +396,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   umma::fence_after();
   subtract_from_tmem(C, p.lda, mb, ncols, ms.tmem + 128);
   sync_all_tc();
+  phase_mark(ms.ph, 3);
 }
 
 __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int piv, int k,
@@ -428,6 +433,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   }
   umma::fence_proxy_async();
   sync_all_tc();
+  phase_mark(ms.ph, 0);
   if (threadIdx.x == 0) {
     wait_or_flag(p, ms.bar_ld, ms.ld_phase);
     umma::fence_after();
@@ -438,9 +444,11 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
+  phase_mark(ms.ph, 1);
   w_image_from_tmem(bufA, ms.tmem, p.fmt, lo);
   umma::fence_proxy_async();
   sync_all_tc();
+  phase_mark(ms.ph, 2);
   if (threadIdx.x == 0) {
     umma::mbar_expect_tx(ms.bar_ld, nimg * kImg);
     umma::bulk_g2s(bufB, slot + 4 * kImg, nimg * kImg, ms.bar_ld);
@@ -457,6 +465,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   subtract_from_tmem(C2, p.lda, mb, ncols, ms.tmem + 128);
   subtract_from_tmem(C1, p.lda, kMNB, ncols, ms.tmem + 256);
   sync_all_tc();
+  phase_mark(ms.ph, 3);
 }
 
 }  // namespace

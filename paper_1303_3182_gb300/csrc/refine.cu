@@ -1,0 +1,342 @@
+// FP64 refinement of a least-squares solution computed from a low-precision tiled QR.
+//
+// The tensor-core factorization gives R with a backward error far above FP64 rounding,
+// so x0 = R^{-1} (Q^T b)(0:n) is only a few digits accurate.  The refinement solves
+// min || A dx - r0 ||, r0 = b - A x0, with LSQR (Paige & Saunders, ACM TOMS 8(1), 1982)
+// right-preconditioned by the computed R: y = R dx, operator A R^{-1}.  A products,
+// residuals, the Krylov vectors and every scalar recurrence are FP64; the triangular
+// solves read the low-precision R (FP32) and compute in FP64.  All scalar state lives in
+// device memory, so an iteration is a fixed sequence of launches without host syncs.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "tqr_internal.h"
+
+namespace tqr {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.
+__device__ double block_sum(double v) {
+  __shared__ double part[kT / 32];
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < kT / 32 ? part[threadIdx.x] : 0.0;
+    s = warp_sum_d(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+__global__ void f64_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n) {
+  const int64_t total = m * n;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t j = idx / m, i = idx - j * m;
+    F[i + j * ldf] = static_cast<float>(A[i + j * lda]);
+  }
+}
+
+// Y(:, r) = sy(r) * Y(:, r) + A X(:, r)  for r < nrhs, rows [row0, row0 + 256) of this CTA,
+// columns [c0, c1) of A; partial sums are added atomically.  sy(r) is applied by the CTAs
+// of the first column chunk only.  ssq(r) += ||Y(:, r)||^2 is NOT formed here.
+__global__ void gemv_n(int64_t m, int64_t n, const double *A, int64_t lda, const double *X, int64_t ldx,
+                       double *Y, int64_t ldy, int nrhs, int64_t chunk) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x;
+  const int64_t c0 = blockIdx.y * chunk, c1 = c0 + chunk < n ? c0 + chunk : n;
+  if (i >= m) return;
+  for (int r = 0; r < nrhs; ++r) {
+    const double *x = X + r * ldx;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t j = c0;
+    for (; j + 4 <= c1; j += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(A[i + (j + u) * lda], x[j + u], acc[u]);
+    }
+    for (; j < c1; ++j) acc[0] = fma(A[i + j * lda], x[j], acc[0]);
+    atomicAdd(Y + i + r * ldy, (acc[0] + acc[1]) + (acc[2] + acc[3]));
+  }
+}
+
+// Y(j, r) = sum_i A(i, j) X(i, r) * scale(r): one warp per column j.
+__global__ void gemv_t(int64_t m, int64_t n, const double *A, int64_t lda, const double *X, int64_t ldx,
+                       double *Y, int64_t ldy, int nrhs, const double *scale) {
+  const int warp = (blockIdx.x * kT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double *col = A + warp * lda;
+  for (int r = 0; r < nrhs; ++r) {
+    const double *x = X + r * ldx;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t i = lane;
+    for (; i + 96 < m; i += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(col[i + 32 * u], x[i + 32 * u], acc[u]);
+    }
+    for (; i < m; i += 32) acc[0] = fma(col[i], x[i], acc[0]);
+    const double s = warp_sum_d((acc[0] + acc[1]) + (acc[2] + acc[3]));
+    if (lane == 0) Y[warp + r * ldy] = s * (scale ? scale[r] : 1.0);
+  }
+}
+
+// LSQR scalar state of one right-hand side (double-buffered by iteration parity).
+struct LsqrScalars {
+  double alpha, beta, rhobar, phibar, anorm2, conv;
+};
+
+// Residual start: U = B - A X0 (U pre-filled with B), then per rhs beta = ||U||.
+__global__ void colnorm(int64_t rows, const double *U, int64_t ldu, double *out, int nrhs) {
+  const int r = blockIdx.y;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < rows;
+       i += static_cast<int64_t>(gridDim.x) * kT) {
+    const double v = U[i + r * ldu];
+    s += v * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(out + r, s);
+}
+
+// v(:, r) = z(:, r) - beta(r) * vold(:, r) when vold given, else z; per-rhs ||v||^2.
+__global__ void axpy_norm(int64_t n, double *Z, int64_t ldz, const double *Vold, int64_t ldv, const double *beta,
+                          double *ssq, int nrhs) {
+  const int r = blockIdx.y;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kT) {
+    double z = Z[i + r * ldz];
+    if (Vold) z -= beta[r] * Vold[i + r * ldv];
+    Z[i + r * ldz] = z;
+    s += z * z;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(ssq + r, s);
+}
+
+
+// One fused scalar + vector step after alpha_new^2 (ssq_a) and beta_new (stored) are known:
+//   alpha = sqrt(ssq_a); v = z / alpha; rho = hypot(rhobar, beta); c = rhobar/rho;
+//   s = beta/rho; theta = s*alpha; rhobar' = -c*alpha; phi = c*phibar; phibar' = s*phibar;
+//   y += (phi/rho) w;  w = v - (theta/rho) w
+__global__ void lsqr_step(int64_t n, double *Z, int64_t ldz, double *V, double *W, double *Y, int64_t ld,
+                          const double *ssq_a, const double *beta_new, const LsqrScalars *in, LsqrScalars *outs,
+                          int nrhs, double tol) {
+  const int r = blockIdx.y;
+  const LsqrScalars st = in[r];
+  const double alpha = sqrt(ssq_a[r]);
+  const double beta = beta_new[r];
+  const double rho = hypot(st.rhobar, beta);
+  const double c = st.rhobar / rho, s = beta / rho;
+  const double theta = s * alpha;
+  const double phi = c * st.phibar;
+  const double inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  const double f_y = phi / rho, f_w = theta / rho;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kT) {
+    const double v = Z[i + r * ldz] * inv_alpha;
+    const double w = W[i + r * ld];
+    V[i + r * ld] = v;
+    Y[i + r * ld] += f_y * w;
+    W[i + r * ld] = v - f_w * w;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    LsqrScalars o;
+    o.alpha = alpha;
+    o.beta = beta;
+    o.rhobar = -c * alpha;
+    o.phibar = s * st.phibar;
+    o.anorm2 = st.anorm2 + alpha * alpha + beta * beta;
+    // ||(A M)^T r|| / (||A M|| ||r||) estimate: alpha |c| / ||A M||
+    o.conv = alpha * fabs(c) / sqrt(o.anorm2);
+    outs[r] = o;
+  }
+}
+
+// Start of LSQR: beta = ||u||, alpha = ||z|| known; v = z/alpha, w = v, y = 0.
+__global__ void lsqr_init(int64_t n, double *Z, int64_t ldz, double *V, double *W, double *Y, int64_t ld,
+                          const double *ssq_a, const double *ssq_b, LsqrScalars *outs, int nrhs) {
+  const int r = blockIdx.y;
+  const double alpha = sqrt(ssq_a[r]), beta = sqrt(ssq_b[r]);
+  const double inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kT) {
+    const double v = Z[i + r * ldz] * inv_alpha;
+    V[i + r * ld] = v;
+    W[i + r * ld] = v;
+    Y[i + r * ld] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    LsqrScalars o;
+    o.alpha = alpha;
+    o.beta = beta;
+    o.rhobar = alpha;
+    o.phibar = beta;
+    o.anorm2 = alpha * alpha;
+    o.conv = beta > 0.0 ? 1.0 : 0.0;
+    outs[r] = o;
+  }
+}
+
+// U = U * (-alpha / beta_old) ... prepares u' accumulation: U_new = A t - alpha * u,
+// with u = U_old / beta_old: scale U_old in place by -alpha/beta_old before the atomics.
+__global__ void scale_u(int64_t m, double *U, int64_t ldu, const LsqrScalars *st, int nrhs) {
+  const int r = blockIdx.y;
+  const double f = st[r].beta > 0.0 ? -st[r].alpha / st[r].beta : 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < m;
+       i += static_cast<int64_t>(gridDim.x) * kT)
+    U[i + r * ldu] *= f;
+}
+
+// inv[r] = 1 / sqrt(ssq[r]); out_beta[r] = sqrt(ssq[r])
+__global__ void finish_norm(const double *ssq, double *inv, double *out_beta, int nrhs) {
+  const int r = threadIdx.x;
+  if (r < nrhs) {
+    const double b = sqrt(ssq[r]);
+    inv[r] = b > 0.0 ? 1.0 / b : 0.0;
+    out_beta[r] = b;
+  }
+}
+
+__global__ void add_into(int64_t n, double *X, int64_t ldx, const double *D, int64_t ldd, int nrhs) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kT)
+    X[i + r * ldx] += D[i + r * ldd];
+}
+
+// D(:, r) = f * S(:, r)
+__global__ void copy_scaled(int64_t n, double *D, int64_t ldd, const double *S, int64_t lds, double f, int nrhs) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kT)
+    D[i + r * ldd] = f * S[i + r * lds];
+}
+
+dim3 vgrid(int64_t len, int nrhs) {
+  int64_t b = (len + kT - 1) / kT;
+  if (b > 1024) b = 1024;
+  return dim3(static_cast<unsigned>(b), static_cast<unsigned>(nrhs));
+}
+
+}  // namespace
+
+size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
+  // U (m) and V, W, Y, Z, Tt (n) per right-hand side, four scalar arrays, two state sets
+  return static_cast<size_t>(nrhs) * (m + 5 * n) + 4 * static_cast<size_t>(nrhs) +
+         2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8;
+}
+
+int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream) {
+  f64_to_f32<<<1216, kT, 0, static_cast<cudaStream_t>(stream)>>>(A, lda, F, ldf, m, n);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, const float *R, int64_t ldr,
+                const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter, int *iters_out,
+                double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double *U = work;
+  double *V = U + static_cast<size_t>(m) * nrhs;
+  double *W = V + static_cast<size_t>(n) * nrhs;
+  double *Y = W + static_cast<size_t>(n) * nrhs;
+  double *Z = Y + static_cast<size_t>(n) * nrhs;
+  double *Tt = Z + static_cast<size_t>(n) * nrhs;
+  double *ssq_a = Tt + static_cast<size_t>(n) * nrhs;
+  double *ssq_b = ssq_a + nrhs;
+  double *inv_b = ssq_b + nrhs;
+  double *betas = inv_b + nrhs;
+  LsqrScalars *sc = reinterpret_cast<LsqrScalars *>(betas + nrhs);  // [2][nrhs]
+  const int64_t chunk = 512;
+  const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
+  const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
+  cudaError_t e = cudaSuccess;
+  int rc = 0;
+#define TQR_CK(x)                                       \
+  do {                                                  \
+    e = (x);                                            \
+    if (e != cudaSuccess) return static_cast<int>(e);   \
+  } while (0)
+#define TQR_CKL()                                       \
+  do {                                                  \
+    e = cudaGetLastError();                             \
+    if (e != cudaSuccess) return static_cast<int>(e);   \
+  } while (0)
+  // u = r0 = B - A X0, beta = ||u||
+  TQR_CK(cudaMemcpy2DAsync(U, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
+                           cudaMemcpyDeviceToDevice, st));
+  copy_scaled<<<vgrid(n, nrhs), kT, 0, st>>>(n, Tt, n, X, ldx, -1.0, nrhs);
+  TQR_CKL();
+  gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
+  TQR_CKL();
+  TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
+  colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);
+  TQR_CKL();
+  finish_norm<<<1, 64, 0, st>>>(ssq_b, inv_b, betas, nrhs);
+  TQR_CKL();
+  // alpha v = R^{-T} A^T u
+  gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
+  TQR_CKL();
+  if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0) return rc;
+  axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, ssq_a, nrhs);
+  TQR_CKL();
+  lsqr_init<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, ssq_b, sc, nrhs);
+  TQR_CKL();
+  std::vector<LsqrScalars> host(nrhs);
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    LsqrScalars *cur = sc + (it & 1) * nrhs, *nxt = sc + ((it + 1) & 1) * nrhs;
+    // t = R^{-1} v
+    TQR_CK(cudaMemcpyAsync(Tt, V, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+    if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0) return rc;
+    // u' = A t - alpha u  (U holds beta * u)
+    scale_u<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, cur, nrhs);
+    TQR_CKL();
+    gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
+    TQR_CKL();
+    TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
+    colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);
+    TQR_CKL();
+    finish_norm<<<1, 64, 0, st>>>(ssq_b, inv_b, betas, nrhs);
+    TQR_CKL();
+    // z = R^{-T} A^T u - beta v
+    gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
+    TQR_CKL();
+    if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0) return rc;
+    axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, n, betas, ssq_a, nrhs);
+    TQR_CKL();
+    lsqr_step<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, betas, cur, nxt, nrhs, tol);
+    TQR_CKL();
+    TQR_CK(cudaMemcpyAsync(host.data(), nxt, sizeof(LsqrScalars) * nrhs, cudaMemcpyDeviceToHost, st));
+    TQR_CK(cudaStreamSynchronize(st));
+    double worst = 0.0;
+    for (int r = 0; r < nrhs; ++r) worst = fmax(worst, host[r].conv);
+    if (!(worst > tol)) {
+      ++it;
+      break;
+    }
+  }
+  // x = x0 + R^{-1} y
+  TQR_CK(cudaMemcpyAsync(Tt, Y, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+  if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0) return rc;
+  add_into<<<vgrid(n, nrhs), kT, 0, st>>>(n, X, ldx, Tt, n, nrhs);
+  TQR_CKL();
+  if (iters_out) *iters_out = it;
+#undef TQR_CK
+#undef TQR_CKL
+  return (it >= max_iter) ? -1 : 0;
+}
+
+}  // namespace tqr

@@ -41,7 +41,9 @@ __device__ __forceinline__ void st_rel(int32_t *p, int v) {
 __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_cg(const float *p) { return static_cast<double>(__ldcg(p)); }
 
-template <typename Real>
+// kLowerT = false: solve R X = B (backward, blocks bottom-up);
+// kLowerT = true : solve R^T X = B (forward, blocks top-down).
+template <typename Real, bool kLowerT>
 __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A, int64_t lda, double *B,
                                                         int64_t ldb, int nrhs, int32_t *flags,
                                                         int32_t *status, int64_t wait_limit_ns) {
@@ -53,7 +55,8 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
   const int nblk = static_cast<int>((n + kTB - 1) / kTB);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    s_kb = nblk - 1 - atomicAdd(flags, 1);
+    const int ticket = atomicAdd(flags, 1);
+    s_kb = kLowerT ? (ticket < nblk ? ticket : -1) : nblk - 1 - ticket;
     s_stop = 0;
   }
   __syncthreads();
@@ -65,7 +68,8 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
     const int j = idx / rb, r = idx - j * rb;
     Cs[r][j] = ld_cg(B + r0 + r + j * ldb);
   }
-  for (int kk = nblk - 1; kk > kb; --kk) {
+  for (int step = 0; step < (kLowerT ? kb : nblk - 1 - kb); ++step) {
+    const int kk = kLowerT ? step : nblk - 1 - step;
     if (tid == 0) {
       const uint64_t t0 = gtimer();
       for (uint64_t it = 0; ld_acq(flags + 1 + kk) == 0; ++it) {
@@ -86,7 +90,8 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
     const int cb = static_cast<int>(lmin(kTB, n - c0));
     for (int idx = tid; idx < rb * cb; idx += kThreads) {
       const int c = idx / rb, r = idx - c * rb;
-      Rs[r][c] = ld_cg(A + (r0 + r) + (c0 + c) * lda);
+      // block (kb, kk) of R, or of R^T = block (kk, kb) of R transposed
+      Rs[r][c] = kLowerT ? ld_cg(A + (c0 + c) + (r0 + r) * lda) : ld_cg(A + (r0 + r) + (c0 + c) * lda);
     }
     for (int idx = tid; idx < cb * nrhs; idx += kThreads) {
       const int j = idx / cb, r = idx - j * cb;
@@ -103,21 +108,30 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
   }
   for (int idx = tid; idx < rb * rb; idx += kThreads) {
     const int c = idx / rb, r = idx - c * rb;
-    Rs[r][c] = (r <= c) ? ld_cg(A + (r0 + r) + (r0 + c) * lda) : 0.0;
+    if (kLowerT)
+      Rs[r][c] = (c <= r) ? ld_cg(A + (r0 + c) + (r0 + r) * lda) : 0.0;
+    else
+      Rs[r][c] = (r <= c) ? ld_cg(A + (r0 + r) + (r0 + c) * lda) : 0.0;
   }
   __syncthreads();
-  // back substitution, one warp per right-hand side; lane owns rows lane and lane+32
+  // substitution, one warp per right-hand side; lane owns rows lane and lane+32
   for (int j = warp; j < nrhs; j += kThreads / 32) {
     double c_lo = lane < rb ? Cs[lane][j] : 0.0;
     double c_hi = lane + 32 < rb ? Cs[lane + 32][j] : 0.0;
-    for (int i = rb - 1; i >= 0; --i) {
+    for (int step = 0; step < rb; ++step) {
+      const int i = kLowerT ? step : rb - 1 - step;
       const double ci = __shfl_sync(0xffffffffu, i < 32 ? c_lo : c_hi, i & 31);
       const double xi = ci / Rs[i][i];
       if (lane == (i & 31)) {
         if (i < 32) c_lo = xi; else c_hi = xi;
       }
-      if (lane < i) c_lo -= Rs[lane][i] * xi;
-      if (lane + 32 < i) c_hi -= Rs[lane + 32][i] * xi;
+      if (kLowerT) {
+        if (lane > i && lane < rb) c_lo -= Rs[lane][i] * xi;
+        if (lane + 32 > i && lane + 32 < rb) c_hi -= Rs[lane + 32][i] * xi;
+      } else {
+        if (lane < i) c_lo -= Rs[lane][i] * xi;
+        if (lane + 32 < i) c_hi -= Rs[lane + 32][i] * xi;
+      }
     }
     if (lane < rb) Cs[lane][j] = c_lo;
     if (lane + 32 < rb) Cs[lane + 32][j] = c_hi;
@@ -135,33 +149,41 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
   }
 }
 
+int trsm_flag_count_impl(int64_t n) { return static_cast<int>((n + kTB - 1) / kTB) + 1; }
+
+template <typename Real, bool kLowerT>
+cudaError_t launch_one(int nblk, size_t smem, cudaStream_t st, int64_t n, const void *A, int64_t lda, double *B,
+                       int64_t ldb, int nr, int32_t *flags, int32_t *status, int64_t wait_limit_ns) {
+  auto kern = trsm_kernel<Real, kLowerT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<nblk, kThreads, smem, st>>>(n, static_cast<const Real *>(A), lda, B, ldb, nr, flags, status, wait_limit_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-int trsm_flag_count(int64_t n) { return static_cast<int>((n + kTB - 1) / kTB) + 1; }
-
 int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, double *B, int64_t ldb,
-                int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream) {
+                int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream,
+                bool lower_transposed) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t smem = sizeof(double) * (2 * kTB * (kRHS + 1) + kTB * (kTB + 1));
-  cudaError_t ea = real_is_double
-      ? cudaFuncSetAttribute(trsm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-      : cudaFuncSetAttribute(trsm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (ea != cudaSuccess) return static_cast<int>(ea);
   const int nblk = static_cast<int>((n + kTB - 1) / kTB);
   for (int64_t j0 = 0; j0 < nrhs; j0 += kRHS) {
     const int nr = static_cast<int>(nrhs - j0 < kRHS ? nrhs - j0 : kRHS);
     cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * (nblk + 1), st);
     if (e != cudaSuccess) return static_cast<int>(e);
     if (real_is_double)
-      trsm_kernel<double><<<nblk, kThreads, smem, st>>>(n, static_cast<const double *>(A), lda, B + j0 * ldb, ldb,
-                                                      nr, flags, status, wait_limit_ns);
+      e = lower_transposed ? launch_one<double, true>(nblk, smem, st, n, A, lda, B + j0 * ldb, ldb, nr, flags, status, wait_limit_ns)
+                           : launch_one<double, false>(nblk, smem, st, n, A, lda, B + j0 * ldb, ldb, nr, flags, status, wait_limit_ns);
     else
-      trsm_kernel<float><<<nblk, kThreads, smem, st>>>(n, static_cast<const float *>(A), lda, B + j0 * ldb, ldb,
-                                                     nr, flags, status, wait_limit_ns);
-    e = cudaGetLastError();
+      e = lower_transposed ? launch_one<float, true>(nblk, smem, st, n, A, lda, B + j0 * ldb, ldb, nr, flags, status, wait_limit_ns)
+                           : launch_one<float, false>(nblk, smem, st, n, A, lda, B + j0 * ldb, ldb, nr, flags, status, wait_limit_ns);
     if (e != cudaSuccess) return static_cast<int>(e);
   }
   return 0;
 }
+
+int trsm_flag_count(int64_t n) { return trsm_flag_count_impl(n); }
 
 }  // namespace tqr

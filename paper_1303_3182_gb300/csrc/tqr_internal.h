@@ -128,9 +128,21 @@ size_t mixed_executor_smem_bytes();
 
 // Wavefront triangular solve R X = B (R upper n x n in A, double or float), X over B.
 // flags: device int32[ceil(n/TB) + 1] scratch (ticket + per-block flags).
+// lower_transposed: solve R^T X = B instead.
 int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, double *B,
                 int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status,
-                int64_t wait_limit_ns, void *stream);
+                int64_t wait_limit_ns, void *stream, bool lower_transposed = false);
 int trsm_flag_count(int64_t n);
+
+// LSQR refinement (refine.cu): X (in: x0, out: refined) for min ||A X - B||, operator
+// A R^{-1} with the FP32 R of a tensor-core factorization.  work: lsqr_work_doubles()
+// doubles; flags: trsm_flag_count(n) int32; status: device status word.
+size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs);
+int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, const float *R, int64_t ldr,
+                const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter,
+                int *iters_out, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
+                void *stream);
+// FP64 -> FP32 copy of an m x n matrix (column-major).
+int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream);
 
 }  // namespace tqr

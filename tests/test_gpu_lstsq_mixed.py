@@ -1,0 +1,55 @@
+"""Least squares with a low-precision tiled QR plus FP64 LSQR refinement, against the
+FP64 oracle (through the C ABI).
+
+Both the refined solution and the oracle's are FP64 least-squares solutions to within
+rounding, so they agree to the LS perturbation bound (Golub & Van Loan, Thm 5.3.1):
+|dx| / |x| <~ c u (kappa + kappa^2 |r| / (|A| |x|)), |A|_2 = 1, u = 2^-53, c = 64; and
+the refined solution's optimality ||A^T r|| / (||A|| ||r||) is within a factor 10 of the
+oracle's, or below the refinement tolerance.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import elimlists as E
+from oracle import householder as H
+from oracle import refine
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1303_3182_gb300 as tqr  # noqa: E402
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1303_3182_gb300 import build
+    build.build()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).cuda().t()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp16", "fp32"])
+@pytest.mark.parametrize("m,n,nrhs,cond,noise", [(1024, 384, 1, 1e4, 1e-3), (900, 256, 3, 1e6, 1e-3),
+                                                 (512, 512, 2, 1e4, 0.0)])
+def test_mixed_lstsq_matches_fp64(m, n, nrhs, cond, noise, prec):
+    A, X, B = synthetic.least_squares_problem(m, n, cond, noise, nrhs, seed=m + n + nrhs)
+    nb, ib = 128, 32
+    p, q = H.tile_grid(m, n, nb)
+    elims = E.elimination_list(p, q, E.GREEDY)
+    Xo = H.lstsq(A, B, nb, ib, elims)
+    Xg, iters = tqr.lstsq(to_dev(A), to_dev(B), nb, ib, "greedy", 1, prec, tol=1e-15, max_iter=300,
+                          return_iters=True)
+    Xg = Xg.cpu().numpy()
+    r = B - A @ Xo
+    bound = 64 * U64 * (cond + cond ** 2 * np.linalg.norm(r) / np.linalg.norm(Xo))
+    err = refine.rel_error(Xg, Xo)
+    assert err <= bound, (err, bound, iters)
+    assert refine.ls_optimality(A, Xg, B) <= max(10 * refine.ls_optimality(A, Xo, B), 1e-15)
+    assert iters >= 1
