@@ -467,14 +467,11 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
   int rcv = convert_to_f32(A, lda, Af, ldf, m, n, stream);
   if (rcv) return cuda_fail(static_cast<cudaError_t>(rcv), "lstsq convert");
   if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Af, ldf, Tw, stream)) != 0) return rc;
-  cudaError_t e = cudaMemcpy2DAsync(Bw, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
-                                    cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-in");
-  if ((rc = tqr_apply_qt(m, n, nb, ib, tree, bs, prec, 0, Af, ldf, Tw, Bw, m, nrhs, stream)) != 0) return rc;
-  if ((rc = tqr_trsm(n, prec, Af, ldf, Bw, m, nrhs, stream)) != 0) return rc;
-  e = cudaMemcpy2DAsync(X, ldx * sizeof(double), Bw, m * sizeof(double), n * sizeof(double), nrhs,
-                        cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-out");
+  // LSQR starts from x0 = 0: with R as preconditioner a few extra iterations cost less
+  // than forming x0 = R^{-1} (Q^T b)(0:n) by a pass over all reflectors
+  (void)Bw;
+  cudaError_t e = cudaMemset2DAsync(X, ldx * sizeof(double), 0, n * sizeof(double), nrhs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "lstsq init");
   Scratch *s = nullptr;
   if ((rc = get_scratch(trsm_flag_count(n), &s)) != 0) return rc;
   int32_t *status = s->flags + s->cap;

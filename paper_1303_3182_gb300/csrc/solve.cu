@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
       Rs[r][c] = (r <= c) ? ld_cg(A + (r0 + r) + (r0 + c) * lda) : 0.0;
   }
   __syncthreads();
+  // reciprocals of the diagonal, formed in parallel once (an FP64 division is slow)
+  __shared__ double s_rinv[kTB];
+  if (tid < rb) s_rinv[tid] = 1.0 / Rs[tid][tid];
+  __syncthreads();
   // substitution, one warp per right-hand side; lane owns rows lane and lane+32
   for (int j = warp; j < nrhs; j += kThreads / 32) {
     double c_lo = lane < rb ? Cs[lane][j] : 0.0;
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) trsm_kernel(int64_t n, const Real *A
     for (int step = 0; step < rb; ++step) {
       const int i = kLowerT ? step : rb - 1 - step;
       const double ci = __shfl_sync(0xffffffffu, i < 32 ? c_lo : c_hi, i & 31);
-      const double xi = ci / Rs[i][i];
+      const double xi = ci * s_rinv[i];
       if (lane == (i & 31)) {
         if (i < 32) c_lo = xi; else c_hi = xi;
       }
