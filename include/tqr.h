@@ -114,9 +114,10 @@ int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t
 /* Least squares min ||A X - B||_2 (m >= n, A of full column rank), all operands double.
  *   prec == TQR_FP64 : X = R^{-1} (Q^T B)(0:n) from an FP64 tiled QR.
  *   otherwise        : the tiled QR runs in "prec" on a float copy of A; X is then
- *                      refined in FP64 (residuals r = B - A X and A^T r in FP64) by
- *                      LSQR (Paige & Saunders, 1982) right-preconditioned with the
- *                      low-precision R, until ||A^T r|| <= tol ||A|| ||r|| or max_iter.
+ *                      computed in FP64 (A products, residuals, Krylov vectors) by LSQR
+ *                      (Paige & Saunders, 1982) from X = 0, right-preconditioned with
+ *                      the low-precision R, until LSQR's estimate of
+ *                      ||(A R^-1)^T r|| / (||A R^-1|| ||r||) <= tol or max_iter.
  *   A, B    : device, not modified.  X : device n x nrhs, ldx >= n.
  *   iters   : out (may be NULL), refinement iterations used (max over right-hand sides).
  *   workspace / ws_bytes : device scratch of at least tqr_lstsq_workspace_size() bytes.
