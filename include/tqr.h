@@ -117,7 +117,8 @@ int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t
  *                      computed in FP64 (A products, residuals, Krylov vectors) by LSQR
  *                      (Paige & Saunders, 1982) from X = 0, right-preconditioned with
  *                      the low-precision R, until LSQR's estimate of
- *                      ||(A R^-1)^T r|| / (||A R^-1|| ||r||) <= tol or max_iter.
+ *                      ||(A R^-1)^T r|| / ||r||, which bounds ||A^T r|| / (||R|| ||r||),
+ *                      is <= tol, or max_iter iterations.
  *   A, B    : device, not modified.  X : device n x nrhs, ldx >= n.
  *   iters   : out (may be NULL), refinement iterations used (max over right-hand sides).
  *   workspace / ws_bytes : device scratch of at least tqr_lstsq_workspace_size() bytes.

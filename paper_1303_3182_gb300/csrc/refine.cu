@@ -159,8 +159,10 @@ __global__ void lsqr_step(int64_t n, double *Z, int64_t ldz, double *V, double *
     o.rhobar = -c * alpha;
     o.phibar = s * st.phibar;
     o.anorm2 = st.anorm2 + alpha * alpha + beta * beta;
-    // ||(A M)^T r|| / (||A M|| ||r||) estimate: alpha |c| / ||A M||
-    o.conv = alpha * fabs(c) / sqrt(o.anorm2);
+    // ||(A M)^T r|| / ||r|| = alpha |c| (Paige & Saunders); since A^T r = R^T (A M)^T r
+    // and ||R|| ~ ||A||, this bounds ||A^T r|| / (||A|| ||r||) of the unpreconditioned
+    // problem, the quantity the FP64 target is stated for
+    o.conv = alpha * fabs(c);
     outs[r] = o;
   }
 }
