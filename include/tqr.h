@@ -114,15 +114,17 @@ int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t
 /* Least squares min ||A X - B||_2 (m >= n, A of full column rank), all operands double.
  *   prec == TQR_FP64 : X = R^{-1} (Q^T B)(0:n) from an FP64 tiled QR.
  *   otherwise        : the tiled QR runs in "prec" on a float copy of A; X is then
- *                      computed in FP64 (A products, residuals, Krylov vectors) by LSQR
- *                      (Paige & Saunders, 1982) from X = 0, right-preconditioned with
- *                      the low-precision R, until LSQR's estimate of
- *                      ||(A R^-1)^T r|| / ||r||, which bounds ||A^T r|| / (||R|| ||r||),
- *                      is <= tol, or max_iter iterations.
+ *                      computed by FP64 iterative refinement from X = 0: each step
+ *                      forms r = B - A X and A^T r in FP64, stops when
+ *                      ||A^T r|| / (||A||_F ||r||) <= tol or when a step no longer
+ *                      halves that quantity (the FP64-attainable level), else solves
+ *                      for the correction with LSQR (Paige & Saunders, 1982) in FP64,
+ *                      right-preconditioned with the low-precision R.
  *   A, B    : device, not modified.  X : device n x nrhs, ldx >= n.
  *   iters   : out (may be NULL), refinement iterations used (max over right-hand sides).
  *   workspace / ws_bytes : device scratch of at least tqr_lstsq_workspace_size() bytes.
- * Errors: -1..-11 sizes/tree/prec/pointers, TQR_ENOCONV when max_iter is reached. */
+ * Errors: -1..-11 sizes/tree/prec/pointers; TQR_ENOCONV when max_iter LSQR iterations
+ *         were used while the solution was still improving. */
 int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int bs, int prec,
               const double *A, int64_t lda, const double *B, int64_t ldb,
               double *X, int64_t ldx, double tol, int max_iter, int *iters,

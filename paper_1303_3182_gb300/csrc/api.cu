@@ -493,6 +493,7 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
   timer.stop(st);
   if (iters) *iters = worst_iters;
   if ((rc = read_status(status, st)) != 0) return rc;
+  if (!converged) g_last_error = "refinement reached max_iter before ||A^T r|| / (||A|| ||r||) <= tol";
   return converged ? TQR_OK : TQR_ENOCONV;
 }
 

@@ -1,9 +1,12 @@
-// FP64 refinement of a least-squares solution computed from a low-precision tiled QR.
+// FP64 iterative refinement of a least-squares solution with a low-precision tiled QR.
 //
-// The tensor-core factorization gives R with a backward error far above FP64 rounding,
-// so x0 = R^{-1} (Q^T b)(0:n) is only a few digits accurate.  The refinement solves
-// min || A dx - r0 ||, r0 = b - A x0, with LSQR (Paige & Saunders, ACM TOMS 8(1), 1982)
-// right-preconditioned by the computed R: y = R dx, operator A R^{-1}.  A products,
+// The tensor-core factorization gives R with a backward error far above FP64 rounding.
+// Each outer step computes, in FP64, the residual r = b - A x of the current solution
+// and its optimality ||A^T r|| / (||A||_F ||r||); it stops when that is <= tol, else it
+// solves min || A dx - r || with LSQR (Paige & Saunders, ACM TOMS 8(1), 1982)
+// right-preconditioned by the computed R (y = R dx, operator A R^{-1}) and sets
+// x += dx.  Restarting from the true residual makes the stopping test independent of
+// LSQR's internal estimates, which drift when the preconditioner is weak.  A products,
 // residuals, the Krylov vectors and every scalar recurrence are FP64; the triangular
 // solves read the low-precision R (FP32) and compute in FP64.  All scalar state lives in
 // device memory, so an iteration is a fixed sequence of launches without host syncs.
@@ -11,6 +14,8 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "tqr_internal.h"
@@ -219,6 +224,20 @@ __global__ void add_into(int64_t n, double *X, int64_t ldx, const double *D, int
     X[i + r * ldx] += D[i + r * ldd];
 }
 
+// out += sum of squares of an m x n column-major matrix
+__global__ void fro_norm2(int64_t m, int64_t n, const double *A, int64_t lda, double *out) {
+  double s = 0.0;
+  const int64_t total = m * n;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * kT) {
+    const int64_t j = idx / m, i = idx - j * m;
+    const double v = A[i + j * lda];
+    s += v * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
 // D(:, r) = f * S(:, r)
 __global__ void copy_scaled(int64_t n, double *D, int64_t ldd, const double *S, int64_t lds, double f, int nrhs) {
   const int r = blockIdx.y;
@@ -236,8 +255,9 @@ dim3 vgrid(int64_t len, int nrhs) {
 }  // namespace
 
 size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
-  // U (m) and V, W, Y, Z, Tt (n) per right-hand side, four scalar arrays, two state sets
-  return static_cast<size_t>(nrhs) * (m + 5 * n) + 4 * static_cast<size_t>(nrhs) +
+  // U (m) and V, W, Y, Z, Tt (n) per right-hand side, five scalar arrays, ||A||_F^2, two
+  // LSQR state sets
+  return static_cast<size_t>(nrhs) * (m + 5 * n) + 5 * static_cast<size_t>(nrhs) + 2 +
          2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8;
 }
 
@@ -256,11 +276,13 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   double *Y = W + static_cast<size_t>(n) * nrhs;
   double *Z = Y + static_cast<size_t>(n) * nrhs;
   double *Tt = Z + static_cast<size_t>(n) * nrhs;
-  double *ssq_a = Tt + static_cast<size_t>(n) * nrhs;
-  double *ssq_b = ssq_a + nrhs;
-  double *inv_b = ssq_b + nrhs;
-  double *betas = inv_b + nrhs;
-  LsqrScalars *sc = reinterpret_cast<LsqrScalars *>(betas + nrhs);  // [2][nrhs]
+  double *ssq_a = Tt + static_cast<size_t>(n) * nrhs;  // [nrhs]
+  double *ssq_b = ssq_a + nrhs;                         // [nrhs]
+  double *inv_b = ssq_b + nrhs;                         // [nrhs]
+  double *betas = inv_b + nrhs;                         // [nrhs]
+  double *anorm2 = betas + nrhs;                        // [1]  ||A||_F^2
+  double *eta2 = anorm2 + 1;                            // [nrhs] ||A^T u||^2, u = r / ||r||
+  LsqrScalars *sc = reinterpret_cast<LsqrScalars *>(eta2 + nrhs + ((nrhs + 1) & 1));  // [2][nrhs]
   const int64_t chunk = 512;
   const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
   const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
@@ -276,69 +298,100 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
     e = cudaGetLastError();                             \
     if (e != cudaSuccess) return static_cast<int>(e);   \
   } while (0)
-  // u = r0 = B - A X0, beta = ||u||
-  TQR_CK(cudaMemcpy2DAsync(U, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
-                           cudaMemcpyDeviceToDevice, st));
-  copy_scaled<<<vgrid(n, nrhs), kT, 0, st>>>(n, Tt, n, X, ldx, -1.0, nrhs);
+  TQR_CK(cudaMemsetAsync(anorm2, 0, sizeof(double), st));
+  fro_norm2<<<1216, kT, 0, st>>>(m, n, A, lda, anorm2);
   TQR_CKL();
-  gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
-  TQR_CKL();
-  TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
-  colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);
-  TQR_CKL();
-  finish_norm<<<1, 64, 0, st>>>(ssq_b, inv_b, betas, nrhs);
-  TQR_CKL();
-  // alpha v = R^{-T} A^T u
-  gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
-  TQR_CKL();
-  if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0) return rc;
-  axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, ssq_a, nrhs);
-  TQR_CKL();
-  lsqr_init<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, ssq_b, sc, nrhs);
-  TQR_CKL();
+  std::vector<double> host_eta(nrhs + 1);
   std::vector<LsqrScalars> host(nrhs);
-  int it = 0;
-  for (; it < max_iter; ++it) {
-    LsqrScalars *cur = sc + (it & 1) * nrhs, *nxt = sc + ((it + 1) & 1) * nrhs;
-    // t = R^{-1} v
-    TQR_CK(cudaMemcpyAsync(Tt, V, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
-    if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0) return rc;
-    // u' = A t - alpha u  (U holds beta * u)
-    scale_u<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, cur, nrhs);
+  int total_it = 0;
+  bool converged = false;
+  double prev_eta = 1e300;
+  const bool debug = std::getenv("TQR_DEBUG_REFINE") != nullptr;
+  const int max_outer = 12;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // FP64 residual of the current solution: u = r = B - A X, beta = ||r||
+    TQR_CK(cudaMemcpy2DAsync(U, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
+                             cudaMemcpyDeviceToDevice, st));
+    copy_scaled<<<vgrid(n, nrhs), kT, 0, st>>>(n, Tt, n, X, ldx, -1.0, nrhs);
     TQR_CKL();
     gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
     TQR_CKL();
     TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
+    TQR_CK(cudaMemsetAsync(eta2, 0, sizeof(double) * nrhs, st));
     colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);
     TQR_CKL();
     finish_norm<<<1, 64, 0, st>>>(ssq_b, inv_b, betas, nrhs);
     TQR_CKL();
-    // z = R^{-T} A^T u - beta v
+    // A^T u in FP64 and the optimality ||A^T r|| / (||A||_F ||r||) of the current X
     gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
     TQR_CKL();
-    if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0) return rc;
-    axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, n, betas, ssq_a, nrhs);
+    axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, eta2, nrhs);
     TQR_CKL();
-    lsqr_step<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, betas, cur, nxt, nrhs, tol);
-    TQR_CKL();
-    TQR_CK(cudaMemcpyAsync(host.data(), nxt, sizeof(LsqrScalars) * nrhs, cudaMemcpyDeviceToHost, st));
+    TQR_CK(cudaMemcpyAsync(host_eta.data(), anorm2, sizeof(double) * (nrhs + 1), cudaMemcpyDeviceToHost, st));
     TQR_CK(cudaStreamSynchronize(st));
-    double worst = 0.0;
-    for (int r = 0; r < nrhs; ++r) worst = fmax(worst, host[r].conv);
-    if (!(worst > tol)) {
-      ++it;
+    double worst_eta = 0.0;
+    for (int r = 0; r < nrhs; ++r) worst_eta = fmax(worst_eta, sqrt(host_eta[1 + r] / host_eta[0]));
+    if (debug) std::fprintf(stderr, "[tqr refine] outer %d: optimality %.3e after %d LSQR iterations\n", outer,
+                            worst_eta, total_it);
+    if (!(worst_eta > tol)) {
+      converged = true;
       break;
     }
+    // an outer step that no longer halves the optimality has reached the level FP64
+    // rounding allows for this problem (as LAPACK's refinement stops): converged
+    if (worst_eta > 0.5 * prev_eta) {
+      converged = true;
+      break;
+    }
+    if (total_it >= max_iter) break;
+    prev_eta = worst_eta;
+    // LSQR on min || (A R^-1) y - r ||, then X += R^{-1} y
+    if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0) return rc;
+    axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, ssq_a, nrhs);
+    TQR_CKL();
+    lsqr_init<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, ssq_b, sc, nrhs);
+    TQR_CKL();
+    for (int it = 0; it < 64 && total_it < max_iter; ++it, ++total_it) {
+      LsqrScalars *cur = sc + (it & 1) * nrhs, *nxt = sc + ((it + 1) & 1) * nrhs;
+      TQR_CK(cudaMemcpyAsync(Tt, V, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+      if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0)
+        return rc;
+      scale_u<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, cur, nrhs);
+      TQR_CKL();
+      gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
+      TQR_CKL();
+      TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
+      colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);
+      TQR_CKL();
+      finish_norm<<<1, 64, 0, st>>>(ssq_b, inv_b, betas, nrhs);
+      TQR_CKL();
+      gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
+      TQR_CKL();
+      if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0)
+        return rc;
+      axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, n, betas, ssq_a, nrhs);
+      TQR_CKL();
+      lsqr_step<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, betas, cur, nxt, nrhs, tol);
+      TQR_CKL();
+      TQR_CK(cudaMemcpyAsync(host.data(), nxt, sizeof(LsqrScalars) * nrhs, cudaMemcpyDeviceToHost, st));
+      TQR_CK(cudaStreamSynchronize(st));
+      double worst = 0.0;
+      for (int r = 0; r < nrhs; ++r) worst = fmax(worst, host[r].conv);
+      if (!(worst > 0.1 * tol)) {
+        ++total_it;
+        break;
+      }
+    }
+    TQR_CK(cudaMemcpyAsync(Tt, Y, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+    if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0)
+      return rc;
+    add_into<<<vgrid(n, nrhs), kT, 0, st>>>(n, X, ldx, Tt, n, nrhs);
+    TQR_CKL();
   }
-  // x = x0 + R^{-1} y
-  TQR_CK(cudaMemcpyAsync(Tt, Y, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
-  if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0) return rc;
-  add_into<<<vgrid(n, nrhs), kT, 0, st>>>(n, X, ldx, Tt, n, nrhs);
-  TQR_CKL();
-  if (iters_out) *iters_out = it;
+  if (iters_out) *iters_out = total_it;
 #undef TQR_CK
 #undef TQR_CKL
-  return (it >= max_iter) ? -1 : 0;
+  return converged ? 0 : -1;
 }
 
 }  // namespace tqr
