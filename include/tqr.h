@@ -111,6 +111,23 @@ int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int pre
 int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb,
              int64_t nrhs, void *stream);
 
+/* Same solve as tqr_trsm, for callers that may not allocate device memory: code that
+ * runs where cudaMalloc is unavailable or forbidden - under a fixed device-memory budget
+ * owned by another allocator, on a path that must never call into the allocator (it can
+ * synchronize the device), or between operations that must not change the device's
+ * memory map.  This entry point allocates nothing: its scratch (a ticket, one flag per
+ * 64-row block and a status word) lives in a fixed array compiled into the library,
+ * which every GPU that loads the library keeps until the process exits.
+ * (The thesis has no counterpart of this entry point.)
+ *   Limit: n <= 262144 (4096 blocks of 64 rows); larger n returns -1 with a message in
+ *   tqr_last_error().  Arguments, layout and the other errors are those of tqr_trsm.
+ *   The first call on a device looks up the device address of the array (once per
+ *   device, with that device current); make that first call before any stream capture.
+ *   Every call uses the same array and resets the parts that must start at zero, so
+ *   calls that overlap on the GPU (e.g. on two streams at once) race: serialize them. */
+int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb,
+                    int64_t nrhs, void *stream);
+
 /* Least squares min ||A X - B||_2 (m >= n, A of full column rank), all operands double.
  *   prec == TQR_FP64 : X = R^{-1} (Q^T B)(0:n) from an FP64 tiled QR.
  *   otherwise        : the tiled QR runs in "prec" on a float copy of A; X is then

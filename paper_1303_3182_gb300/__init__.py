@@ -53,6 +53,7 @@ def lib() -> ctypes.CDLL:
             "tqr_factor": (i32, [i64, i64, i32, i32, i32, i32, i32, vp, i64, vp, vp]),
             "tqr_apply_qt": (i32, [i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64, i64, vp]),
             "tqr_trsm": (i32, [i64, i32, vp, i64, vp, i64, i64, vp]),
+            "tqr_trsm_static": (i32, [i64, i32, vp, i64, vp, i64, i64, vp]),
             "tqr_lstsq": (i32, [i64, i64, i64, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp, i64,
                                 dbl, i32, ctypes.POINTER(ctypes.c_int), vp, ctypes.c_size_t, vp]),
             "tqr_lstsq_workspace_size": (i32, [i64, i64, i64, i32, i32, i32,
@@ -244,6 +245,15 @@ def trsm(A, B, n: int, prec="fp64", stream=None):
     _check("tqr_trsm", lib().tqr_trsm(n, _prec(prec), ctypes.c_void_p(A.data_ptr()), _ld(A, A.shape[0]),
                                       ctypes.c_void_p(B.data_ptr()), _ld(B, B.shape[0]), B.shape[1],
                                       _stream(stream)))
+    return B
+
+
+def trsm_static(A, B, n: int, prec="fp64", stream=None):
+    """tqr_trsm_static: the same solve as trsm() without any device allocation (scratch in
+    a fixed array inside the library; n <= 262144; calls must not overlap on the GPU)."""
+    _check("tqr_trsm_static", lib().tqr_trsm_static(n, _prec(prec), ctypes.c_void_p(A.data_ptr()),
+                                                    _ld(A, A.shape[0]), ctypes.c_void_p(B.data_ptr()),
+                                                    _ld(B, B.shape[0]), B.shape[1], _stream(stream)))
     return B
 
 

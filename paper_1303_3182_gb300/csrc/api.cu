@@ -235,6 +235,8 @@ int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec
 }  // namespace
 
 void set_error(const std::string &msg) { g_last_error = msg; }
+int64_t wait_limit_ns() { return g_wait_limit_ns; }
+bool sync_enabled() { return g_sync != 0; }
 
 }  // namespace tqr
 

@@ -10,7 +10,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <string>
 
+#include "../../include/tqr.h"
 #include "tqr_internal.h"
 
 namespace tqr {
@@ -190,4 +193,84 @@ int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, doub
 
 int trsm_flag_count(int64_t n) { return trsm_flag_count_impl(n); }
 
+// ---------------------------------------------------------------------------------
+// Scratch for tqr_trsm_static: a ticket, one flag per 64-row block and a status word,
+// in a fixed array that exists on every GPU that loads this library (until the process
+// exits).  Its size caps n at kStaticMaxBlocks * 64 rows.
+constexpr int kStaticMaxBlocks = 4096;
+static __device__ __align__(256) int32_t g_trsm_static_scratch[kStaticMaxBlocks + 2];
+
+namespace {
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+int32_t *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device.  The host-side symbol is
+// only a stand-in, so the address is looked up once per device (with that device
+// current) and cached; this lookup is the only set-up the entry point needs.
+int static_scratch(int32_t **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return TQR_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return TQR_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    int32_t *p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_trsm_static_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return TQR_ECUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return TQR_OK;
+}
+}  // namespace
+
 }  // namespace tqr
+
+extern "C" int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb,
+                               int64_t nrhs, void *stream) {
+  using namespace tqr;
+  if (n < 1) return -1;
+  if (prec < TQR_FP64 || prec > TQR_FP32) return -2;
+  if (!A) return -3;
+  if (lda < n) return -4;
+  if (!B) return -5;
+  if (ldb < n) return -6;
+  if (nrhs < 0) return -7;
+  const int64_t nblk = (n + 63) / 64;
+  if (nblk > kStaticMaxBlocks) {
+    set_error("tqr_trsm_static: n exceeds the static scratch limit of " +
+              std::to_string(static_cast<long long>(kStaticMaxBlocks) * 64) + " rows");
+    return -1;
+  }
+  if (nrhs == 0) return TQR_OK;
+  int32_t *scratch = nullptr;
+  int rc = static_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t *status = scratch + kStaticMaxBlocks + 1;
+  // the array keeps the previous call's contents: the status word starts at zero, and
+  // launch_trsm zeroes the ticket and flags before every pass
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) {
+    set_error(std::string("tqr_trsm_static: ") + cudaGetErrorString(e));
+    return TQR_ECUDA;
+  }
+  rc = launch_trsm(n, A, lda, prec == TQR_FP64, B, ldb, nrhs, scratch, status, wait_limit_ns(), stream);
+  if (rc) {
+    set_error(std::string("tqr_trsm_static: ") + cudaGetErrorString(static_cast<cudaError_t>(rc)));
+    return TQR_ECUDA;
+  }
+  if (!sync_enabled()) return TQR_OK;
+  int32_t h = 0;
+  e = cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error(std::string("tqr_trsm_static: ") + cudaGetErrorString(e));
+    return TQR_ECUDA;
+  }
+  return h != 0 ? TQR_ETIMEOUT : TQR_OK;
+}

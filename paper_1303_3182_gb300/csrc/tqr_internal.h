@@ -86,6 +86,8 @@ void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g);
 
 void set_error(const std::string &msg);
+int64_t wait_limit_ns();   // current device-wait limit (tqr_set_wait_limit_ns)
+bool sync_enabled();       // tqr_set_sync state
 
 // ---- device side (factor.cu, solve.cu) -------------------------------------------
 // Status word layout written by the device: code in the low 8 bits, task index above.
