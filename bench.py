@@ -1,15 +1,21 @@
 #!/usr/bin/env python
-"""Benchmark of the tiled-QR least-squares path on GB300.
+"""Benchmark of the tiled-QR least-squares path on one GB300 (per rank).
 
-One step = one least-squares solve min ||A x - b|| of a 32768 x 4096 matrix through the
-C ABI (tqr_lstsq): elimination list + task graph (cached plan), tiled QR (GEQRT, TTQRT,
-UNMQR, TTMQR in the persistent executor), Q^T b, the triangular solve and, for the
-mixed-precision form, the FP64 refinement.  value = nominal 2 n^2 (m - n/3) flops per
-step / step time, in TFLOP/s.  Inputs are synthetic (seeded), resident in HBM; A is
-1.07 GB (> 129 MB L2), so every step streams it from HBM.
+Workload: min ||A x - b|| for A = U diag(sigma) V^T, 32768 x 4096, cond 1e6 (Haar U, V;
+geometric sigma), x ~ N(0,1), b = A x + 1e-3 N(0,1), seeded; one right-hand side.
 
---impl reference times the CPU oracle (plain numpy FP64, one thread) on a bounded
-sample of the same workload instead.
+One step = one call of the library's least-squares entry point (tqr_lstsq):
+  mixed (headline): FP32 copy of A -> elimination list + task graph (cached plan) ->
+    tiled QR (GEQRT/TTQRT panels with FP64 norms and tau, UNMQR/TTMQR on tcgen05 with
+    split-bf16 x3 products, one persistent kernel) -> FP64 refinement (residuals, A^T r,
+    LSQR preconditioned by R) until the LS optimality ||A^T r|| / (||A||_F ||r||)
+    reaches that of the plain FP64 solve ("equal LS error");
+  fp64 arm: FP64 tiled QR (nb 256, ib 32) -> Q^T b -> triangular solve.
+value = nominal 2 n^2 (m - n/3) flops per step / step time (TFLOP/s).  A is 1.07 GB,
+larger than the 129 MB L2, so every step streams it from HBM.
+
+--impl reference times the CPU oracle (plain numpy FP64, one thread) on a bounded sample
+of the same workload instead.
 """
 from __future__ import annotations
 
@@ -20,13 +26,13 @@ import statistics
 import subprocess
 import sys
 import threading
-import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tiled-QR TFLOP/s, mixed vs plain FP64 at equal LS error; % of tensor peak"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (the FP64 path runs on the FP64 ALUs)
+FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 rate (the FP64 arm runs on the FP64 ALUs)
+BF16_FALLBACK = (1900.0, 1700.0)
 
 
 def parse_args():
@@ -37,15 +43,23 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m", type=int, default=32768)
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--nb", type=int, default=256)
-    ap.add_argument("--ib", type=int, default=32)
+    ap.add_argument("--cond", type=float, default=1e6)
+    ap.add_argument("--prec", default="bf16x3")
     ap.add_argument("--tree", default="greedy")
-    ap.add_argument("--prec", default="fp64")
-    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-m", type=int, default=8192)
     ap.add_argument("--sample-n", type=int, default=1024)
     return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return BF16_FALLBACK[0], BF16_FALLBACK[1], "fallback"
 
 
 # ---------------------------------------------------------------------------------
@@ -55,12 +69,11 @@ def parse_args():
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
+import numpy as np
 import synthetic
 from oracle import elimlists as E, householder as H
 m, n, nb, ib, tree, reps = {m}, {n}, {nb}, {ib}, {tree!r}, {reps}
-import numpy as np
-A = synthetic.gaussian(m, n, synthetic.SEED_BASE + 2)
-b = np.random.default_rng(5).standard_normal((m, 1))
+A, X, B = synthetic.least_squares_problem(m, n, {cond}, 1e-3, 1, synthetic.SEED_BASE + 3)
 p, q = H.tile_grid(m, n, nb)
 TREES = dict(flat=E.FLAT, plasma=E.PLASMA, binary=E.BINARY, fibonacci=E.FIBONACCI, greedy=E.GREEDY,
              grasap=E.GRASAP, asap=E.ASAP)
@@ -68,39 +81,48 @@ times = []
 for r in range(reps):
     t0 = time.perf_counter()
     elims = E.elimination_list(p, q, TREES[tree], bs=4)
-    H.lstsq(A, b, nb, ib, elims)
+    H.lstsq(A, B, nb, ib, elims)
     times.append(time.perf_counter() - t0)
 print(json.dumps(dict(times=times, flops=2.0 * n * n * (m - n / 3.0))))
 """
 
 
-def run_oracle(m, n, nb, ib, tree, reps):
+def run_oracle(m, n, nb, ib, tree, reps, cond):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, m=m, n=n, nb=nb, ib=ib, tree=tree, reps=reps)
+    code = ORACLE_SNIPPET.format(root=ROOT, m=m, n=n, nb=nb, ib=ib, tree=tree, reps=reps, cond=cond)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def cpu_baseline(args):
     ms, ns = min(args.sample_m, args.m), min(args.sample_n, args.n)
-    r = run_oracle(ms, ns, args.nb, args.ib, args.tree, 1)
+    r = run_oracle(ms, ns, 256, 32, args.tree, 1, args.cond)
     t = r["times"][0]
     return {"value": r["flops"] / t / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle FP64 tiled QR least squares of the leading {ms}x{ns} block (same nb={args.nb}, "
-                      f"ib={args.ib}, tree={args.tree}), one BLAS thread, {t:.1f} s; rate = nominal flops / time"}
+            "sample": f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.tree}) of a {ms}x{ns} "
+                      f"matrix of the same kind, one BLAS thread, {t:.1f} s; rate = nominal flops / time"}
+
+
+def workload_config(args):
+    return {"workload": f"least squares {args.m}x{args.n}, cond {args.cond:g}, 1 rhs; mixed tiled QR "
+                        f"({args.prec}, nb 128, ib 32, {args.tree}) + FP64 refinement vs FP64 tiled QR "
+                        f"(nb 256, ib 32)",
+            "m": args.m, "n": args.n, "cond": args.cond, "nrhs": 1, "prec": args.prec, "tree": args.tree,
+            "nb_mixed": 128, "nb_fp64": 256, "ib": 32,
+            "l2": "inputs larger than L2 (A is %.2f GB FP64)" % (args.m * args.n * 8 / 1e9),
+            "parallelism": "independent replicas" if args.gpus > 1 else "single GPU"}
 
 
 def reference_arm(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     ms, ns = min(2048, args.m), min(512, args.n)
-    r = run_oracle(ms, ns, args.nb, args.ib, args.tree, args.warmup + args.steps)
+    r = run_oracle(ms, ns, 256, 32, args.tree, args.warmup + args.steps, args.cond)
     times = r["times"][args.warmup:]
     tot = sum(times)
     value = r["flops"] * len(times) / tot / 1e12
-    sample = (f"oracle FP64 tiled QR least squares of the leading {ms}x{ns} block of the {args.m}x{args.n} "
-              f"workload per step (nb={args.nb}, ib={args.ib}, tree={args.tree}), one BLAS thread")
+    sample = (f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.tree}) of a {ms}x{ns} matrix of "
+              f"the workload's kind per step, one BLAS thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
@@ -109,14 +131,6 @@ def reference_arm(args):
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
-
-
-def workload_config(args):
-    return {"workload": f"least squares {args.m}x{args.n}, 1 rhs, tiled QR nb={args.nb} ib={args.ib} "
-                        f"{args.tree} tree, {args.prec}",
-            "m": args.m, "n": args.n, "nb": args.nb, "ib": args.ib, "tree": args.tree, "prec": args.prec,
-            "nrhs": args.nrhs, "l2": "inputs larger than L2 (A is %.2f GB)" % (args.m * args.n * 8 / 1e9),
-            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
 # ---------------------------------------------------------------------------------
@@ -181,7 +195,6 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------
 
 def main_gpu(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -195,29 +208,44 @@ def main_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0 or world == 1:
-        _build.build()
-    if world > 1:
-        dist.barrier()
+    _build.build()
     tqr.lib()
     dev = torch.device("cuda", local)
-    m, n, nb, ib, nrhs = args.m, args.n, args.nb, args.ib, args.nrhs
-    # inputs: i.i.d. N(0,1) A (seeded per rank: independent replicas), b = A x + 1e-3 noise
-    seed = synthetic.SEED_BASE + 2 + 1000 * rank
-    A = synthetic.gaussian(m, n, seed)
-    rng = np.random.default_rng(seed + 1)
-    xtrue = rng.standard_normal((n, nrhs))
-    b = A @ xtrue + 1e-3 * rng.standard_normal((m, nrhs))
-    A_host = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()  # (n, m) row-major = A col-major
-    b_host = torch.from_numpy(np.ascontiguousarray(b.T)).pin_memory()
-    Ad = A_host.to(dev).t()
-    bd = b_host.to(dev).t()
-    X = tqr.colmajor(torch.empty((n, nrhs), dtype=torch.float64, device=dev))
-    ws = torch.empty(tqr.lstsq_workspace_size(m, n, nrhs, nb, ib, args.prec), dtype=torch.uint8, device=dev)
+    m, n = args.m, args.n
     stream = torch.cuda.current_stream()
+    # independent replicas: each rank solves its own seeded problem
+    A, xtrue, b = synthetic.least_squares_device(m, n, args.cond, 1e-3, 1, synthetic.SEED_BASE + 3 + 1000 * rank,
+                                                 dev)
+    anorm = float(torch.linalg.norm(A))
+
+    def optimality(X):
+        r = b - A @ X
+        return float(torch.linalg.norm(A.t() @ r) / (anorm * torch.linalg.norm(r)))
+
+    X = tqr.colmajor(torch.empty((n, 1), dtype=torch.float64, device=dev))
+
+    # ---- plain FP64 arm (the same entry point, FP64 tiled QR) ----
+    ws64 = torch.empty(tqr.lstsq_workspace_size(m, n, 1, 256, 32, "fp64"), dtype=torch.uint8, device=dev)
+    tqr.lstsq(A, b, 256, 32, args.tree, 4, "fp64", X=X, workspace=ws64, stream=stream)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.fp64_steps):
+        tqr.lstsq(A, b, 256, 32, args.tree, 4, "fp64", X=X, workspace=ws64, stream=stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = g0.elapsed_time(g1) / args.fp64_steps
+    eta64 = optimality(X)
+    del ws64
+    torch.cuda.empty_cache()
+
+    # ---- mixed arm (headline) ----
+    tol = eta64
+    ws = torch.empty(tqr.lstsq_workspace_size(m, n, 1, 128, 32, args.prec), dtype=torch.uint8, device=dev)
 
     def step():
-        tqr.lstsq(Ad, bd, nb, ib, args.tree, 4, args.prec, X=X, workspace=ws, stream=stream)
+        return tqr.lstsq(A, b, 128, 32, args.tree, 4, args.prec, tol=tol, max_iter=1000, X=X, workspace=ws,
+                         stream=stream, return_iters=True)[1]
 
     tqr.set_timing(True)
     for _ in range(args.warmup):
@@ -225,42 +253,43 @@ def main_gpu(args):
     torch.cuda.synchronize()
     for kind in ("factor", "apply_q", "trsm", "refine"):
         tqr.kernel_time(kind, reset=True)
+    tqr.launch_count(reset=True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            step()
+            iters.append(step())
         e1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
+    launches = tqr.launch_count(reset=True)
     kt = {k: tqr.kernel_time(k, reset=True) for k in ("factor", "apply_q", "trsm", "refine")}
-    launches = sum(v[1] for v in kt.values())
-    # least-squares quality of the last solve (FP64 residual check on the host)
-    Xh = X.cpu().numpy()
-    r = b - A @ Xh
-    ls_opt = float(np.linalg.norm(A.T @ r) / (np.linalg.norm(A) * np.linalg.norm(r)))
+    tqr.set_timing(False)
+    eta_mixed = optimality(X)
 
-    # end to end: host buffers, copies inside the timed region
-    A_e2e = torch.empty((n, m), dtype=torch.float64, device=dev).t()
-    b_e2e = torch.empty((nrhs, m), dtype=torch.float64, device=dev).t()
-    X_host = torch.empty((nrhs, n), dtype=torch.float64).pin_memory()
+    # ---- end to end: host buffers, copies inside the timed region ----
+    A_host = A.t().contiguous().cpu().pin_memory()   # (n, m) row-major == A column-major
+    b_host = b.t().contiguous().cpu().pin_memory()
+    A_dev = torch.empty((n, m), dtype=torch.float64, device=dev)
+    b_dev = torch.empty((1, m), dtype=torch.float64, device=dev)
+    X_host = torch.empty((1, n), dtype=torch.float64).pin_memory()
 
     def step_e2e():
-        A_e2e.t().copy_(A_host, non_blocking=True)
-        b_e2e.t().copy_(b_host, non_blocking=True)
-        tqr.lstsq(A_e2e, b_e2e, nb, ib, args.tree, 4, args.prec, X=X, workspace=ws, stream=stream)
+        A_dev.copy_(A_host, non_blocking=True)
+        b_dev.copy_(b_host, non_blocking=True)
+        tqr.lstsq(A_dev.t(), b_dev.t(), 128, 32, args.tree, 4, args.prec, tol=tol, max_iter=1000, X=X,
+                  workspace=ws, stream=stream)
         X_host.copy_(X.t(), non_blocking=True)
 
     step_e2e()
     torch.cuda.synchronize()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.steps):
         step_e2e()
@@ -277,23 +306,27 @@ def main_gpu(args):
     value = flops * world / (step_ms * 1e-3) / 1e12
     fac_ms, fac_n = kt["factor"]
     fac_avg = fac_ms / max(fac_n, 1)
+    bf16_burst, bf16_sust, peak_src = peaks()
     achieved = flops / (fac_avg * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32+bf16x3",
-        "data": "synthetic", "config": workload_config(args),
+        "vs_baseline": None, "dtype": "f32+bf16x3 (FP64 norms, tau, refinement)" if args.prec == "bf16x3"
+        else args.prec, "data": "synthetic", "config": workload_config(args),
         "e2e": {"value": flops * world / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": m * n * 8 + m * nrhs * 8, "d2h_bytes_per_step": n * nrhs * 8},
+                "h2d_bytes_per_step": m * n * 8 + m * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches,
-        "roofline": {"kernel": "executor_kernel (tiled QR task graph)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (recipe table); "
-                                    "DFMA probe measured 1.19 TFLOP/s",
-                     "avg_launch_ms": fac_avg},
+        "roofline": {"kernel": "executor_kernel<float,float,1> (mixed tiled-QR task graph, one launch per step)",
+                     "bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
+                     "frac": achieved / bf16_sust, "traffic": None,
+                     "peak_source": f"{peak_src} bf16 dense sustained (MEASURED_PEAKS.json)",
+                     "flops_per_launch": flops, "avg_launch_ms": fac_avg},
+        "ls_optimality": {"mixed": eta_mixed, "fp64": eta64, "target": tol},
+        "refinement_iterations": iters,
+        "fp64": {"value": flops / (fp64_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": fp64_ms,
+                 "steps": args.fp64_steps, "frac_of_fp64_peak": flops / (fp64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+        "speedup_vs_fp64": fp64_ms / step_ms,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
-        "ls_optimality": ls_opt,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -169,6 +169,9 @@ int tqr_sync_status(void *stream);
  * them when reset != 0.  Errors: -1 unknown kind. */
 int tqr_set_timing(int on);
 int tqr_kernel_time(int kind, double *ms_total, int64_t *launches, int reset);
+/* Number of CUDA kernels this library has launched in this process (all entry points);
+ * reset != 0 clears the count after reading it. */
+int64_t tqr_launch_count(int reset);
 
 /* Per-task execution trace (a Gantt chart of the persistent executor).  With tracing on,
  * each executor launch records for every task the globaltimer (ns) when a CTA claimed

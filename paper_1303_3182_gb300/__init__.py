@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
             "tqr_debug_drop_edge": (None, [i64]),
             "tqr_set_timing": (i32, [i32]),
             "tqr_set_trace": (i32, [i32]),
+            "tqr_launch_count": (i64, [i32]),
             "tqr_trace_fetch": (i64, [c_i64p, i64]),
             "tqr_kernel_time": (i32, [i32, ctypes.POINTER(ctypes.c_double), c_i64p, i32]),
         }
@@ -173,6 +174,11 @@ def kernel_time(kind, reset: bool = True):
     k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
     _check("tqr_kernel_time", lib().tqr_kernel_time(k, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
     return ms.value, n.value
+
+
+def launch_count(reset: bool = False) -> int:
+    """Kernels launched by the library so far (tqr_launch_count)."""
+    return int(lib().tqr_launch_count(1 if reset else 0))
 
 
 def set_trace(on: bool) -> bool:

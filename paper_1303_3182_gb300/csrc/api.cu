@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -235,6 +236,11 @@ int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec
 }  // namespace
 
 void set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+std::atomic<int64_t> g_launch_count{0};
+}
+void count_launch(int64_t k) { g_launch_count.fetch_add(k, std::memory_order_relaxed); }
 int64_t wait_limit_ns() { return g_wait_limit_ns; }
 bool sync_enabled() { return g_sync != 0; }
 
@@ -619,6 +625,11 @@ int64_t tqr_trace_fetch(int64_t *out, int64_t cap) {
     for (int q = 0; q < 8; ++q) o[4 + q] = stamps[8 * t + q];
   }
   return n;
+}
+
+int64_t tqr_launch_count(int reset) {
+  const int64_t v = reset ? g_launch_count.exchange(0) : g_launch_count.load();
+  return v;
 }
 
 void tqr_debug_drop_edge(int64_t e) {

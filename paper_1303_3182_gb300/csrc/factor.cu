@@ -728,6 +728,7 @@ int launch_typed(const ExecParams &p, void *stream, size_t smem) {
   if (grid > p.ntask) grid = p.ntask;
   if (grid < 1) grid = 1;
   kern<<<grid, kThreads, smem, static_cast<cudaStream_t>(stream)>>>(p);
+  count_launch();
   return static_cast<int>(cudaGetLastError());
 }
 

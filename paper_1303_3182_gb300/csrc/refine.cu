@@ -256,13 +256,15 @@ dim3 vgrid(int64_t len, int nrhs) {
 
 size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
   // U (m) and V, W, Y, Z, Tt (n) per right-hand side, five scalar arrays, ||A||_F^2, two
-  // LSQR state sets
+  // LSQR state sets, and the inverses of R's 64 x 64 diagonal blocks
+  const size_t nblk = static_cast<size_t>((n + 63) / 64);
   return static_cast<size_t>(nrhs) * (m + 5 * n) + 5 * static_cast<size_t>(nrhs) + 2 +
-         2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8;
+         2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8 + nblk * 64 * 64;
 }
 
 int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream) {
   f64_to_f32<<<1216, kT, 0, static_cast<cudaStream_t>(stream)>>>(A, lda, F, ldf, m, n);
+  count_launch();
   return static_cast<int>(cudaGetLastError());
 }
 
@@ -283,6 +285,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   double *anorm2 = betas + nrhs;                        // [1]  ||A||_F^2
   double *eta2 = anorm2 + 1;                            // [nrhs] ||A^T u||^2, u = r / ||r||
   LsqrScalars *sc = reinterpret_cast<LsqrScalars *>(eta2 + nrhs + ((nrhs + 1) & 1));  // [2][nrhs]
+  double *Dinv = reinterpret_cast<double *>(sc + 2 * nrhs) + 4;                 // [nblk][64][64]
   const int64_t chunk = 512;
   const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
   const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
@@ -295,12 +298,18 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   } while (0)
 #define TQR_CKL()                                       \
   do {                                                  \
+    count_launch();                                     \
     e = cudaGetLastError();                             \
     if (e != cudaSuccess) return static_cast<int>(e);   \
   } while (0)
   TQR_CK(cudaMemsetAsync(anorm2, 0, sizeof(double), st));
   fro_norm2<<<1216, kT, 0, st>>>(m, n, A, lda, anorm2);
   TQR_CKL();
+  if ((rc = launch_diag_inverse(n, R, ldr, false, Dinv, stream)) != 0) return rc;
+  // R^{-1} and R^{-T} applied by the blocked solves with the diagonal-block inverses
+  auto solve_r = [&](double *Vec, bool lower_t) -> int {
+    return launch_trsv_blocked(n, R, ldr, false, Dinv, Vec, n, nrhs, flags, status, wait_limit_ns, stream, lower_t);
+  };
   std::vector<double> host_eta(nrhs + 1);
   std::vector<LsqrScalars> host(nrhs);
   int total_it = 0;
@@ -346,7 +355,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
     if (total_it >= max_iter) break;
     prev_eta = worst_eta;
     // LSQR on min || (A R^-1) y - r ||, then X += R^{-1} y
-    if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0) return rc;
+    if ((rc = solve_r(Z, true)) != 0) return rc;
     axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, ssq_a, nrhs);
     TQR_CKL();
     lsqr_init<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, ssq_b, sc, nrhs);
@@ -354,8 +363,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
     for (int it = 0; it < 64 && total_it < max_iter; ++it, ++total_it) {
       LsqrScalars *cur = sc + (it & 1) * nrhs, *nxt = sc + ((it + 1) & 1) * nrhs;
       TQR_CK(cudaMemcpyAsync(Tt, V, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
-      if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0)
-        return rc;
+      if ((rc = solve_r(Tt, false)) != 0) return rc;
       scale_u<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, cur, nrhs);
       TQR_CKL();
       gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
@@ -367,8 +375,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
       TQR_CKL();
       gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
       TQR_CKL();
-      if ((rc = launch_trsm(n, R, ldr, false, Z, n, nrhs, flags, status, wait_limit_ns, stream, true)) != 0)
-        return rc;
+      if ((rc = solve_r(Z, true)) != 0) return rc;
       axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, n, betas, ssq_a, nrhs);
       TQR_CKL();
       lsqr_step<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, W, Y, n, ssq_a, betas, cur, nxt, nrhs, tol);
@@ -383,8 +390,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
       }
     }
     TQR_CK(cudaMemcpyAsync(Tt, Y, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
-    if ((rc = launch_trsm(n, R, ldr, false, Tt, n, nrhs, flags, status, wait_limit_ns, stream, false)) != 0)
-      return rc;
+    if ((rc = solve_r(Tt, false)) != 0) return rc;
     add_into<<<vgrid(n, nrhs), kT, 0, st>>>(n, X, ldx, Tt, n, nrhs);
     TQR_CKL();
   }

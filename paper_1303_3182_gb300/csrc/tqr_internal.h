@@ -86,6 +86,8 @@ void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g);
 
 void set_error(const std::string &msg);
+// Number of kernels this library has launched (tqr_launch_count).
+void count_launch(int64_t k = 1);
 int64_t wait_limit_ns();   // current device-wait limit (tqr_set_wait_limit_ns)
 bool sync_enabled();       // tqr_set_sync state
 
@@ -135,6 +137,12 @@ int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, doub
                 int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status,
                 int64_t wait_limit_ns, void *stream, bool lower_transposed = false);
 int trsm_flag_count(int64_t n);
+// Inverses of the 64 x 64 diagonal blocks of an upper-triangular R (FP64, 64*64 doubles
+// per block), and the blocked solve R X = B or R^T X = B that uses them.
+int launch_diag_inverse(int64_t n, const void *A, int64_t lda, bool real_is_double, double *Dinv, void *stream);
+int launch_trsv_blocked(int64_t n, const void *A, int64_t lda, bool real_is_double, const double *Dinv, double *B,
+                        int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
+                        void *stream, bool lower_transposed);
 
 // LSQR refinement (refine.cu): X (in: x0, out: refined) for min ||A X - B||, operator
 // A R^{-1} with the FP32 R of a tensor-core factorization.  work: lsqr_work_doubles()

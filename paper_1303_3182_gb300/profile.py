@@ -1,0 +1,68 @@
+"""Run and time tqr_factor on a seeded N(0,1) matrix; optionally dump the per-task trace.
+
+    python -m paper_1303_3182_gb300.profile --m 4096 --n 1024 --prec bf16x3 --reps 3 \
+        [--trace trace.json]
+
+Prints one JSON line per repetition (device time of the factorization executor and the
+nominal TFLOP/s).  With --trace, the last repetition records the executor's per-task
+stamps (tqr_set_trace) and writes them as a list of {kind, i, piv, k, j, sm, start_us,
+end_us, phases_us} records - a Gantt chart of the task graph.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main():
+    import torch
+
+    import paper_1303_3182_gb300 as tqr
+    from paper_1303_3182_gb300 import build
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--m", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--prec", default="bf16x3")
+    ap.add_argument("--nb", type=int, default=0, help="0: 128 for tensor-core precisions, 256 for fp64")
+    ap.add_argument("--ib", type=int, default=32)
+    ap.add_argument("--tree", default="greedy")
+    ap.add_argument("--bs", type=int, default=4)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1303318202)
+    ap.add_argument("--trace", default="")
+    a = ap.parse_args()
+    build.build()
+    nb = a.nb or (256 if a.prec == "fp64" else 128)
+    dt = torch.float64 if a.prec == "fp64" else torch.float32
+    g = torch.Generator(device="cuda")
+    g.manual_seed(a.seed)
+    A0 = torch.randn(a.n, a.m, dtype=torch.float64, device="cuda", generator=g).to(dt).t()
+    work = torch.empty_like(A0.t()).t()
+    T = torch.empty(tqr.workspace_size(a.m, a.n, nb, a.ib, a.prec), dtype=torch.uint8, device="cuda")
+    tqr.set_timing(True)
+    for r in range(a.reps):
+        work.copy_(A0)
+        last = r == a.reps - 1
+        if last and a.trace:
+            tqr.set_trace(True)
+        tqr.kernel_time("factor", reset=True)
+        tqr.factor(work, nb, a.ib, a.tree, a.bs, a.prec, T=T)
+        ms, _ = tqr.kernel_time("factor", reset=True)
+        print(json.dumps({"rep": r, "m": a.m, "n": a.n, "nb": nb, "ib": a.ib, "prec": a.prec, "tree": a.tree,
+                          "ms": ms, "tflops": tqr.nominal_flops(a.m, a.n) / (ms * 1e-3) / 1e12}), flush=True)
+    if a.trace:
+        tqr.set_trace(False)
+        tr = tqr.trace_fetch()
+        t0 = int(tr[:, 4].min())
+        names = ["GEQRT", "TTQRT", "UNMQR", "TTMQR", "UNMQR_B", "TTMQR_B"]
+        recs = [{"kind": names[int(r[0])], "i": int(r[1]), "piv": int(r[2]), "k": int(r[3]) & 0xFFFF,
+                 "j": (int(r[3]) >> 16) if (int(r[3]) >> 16) < 32768 else -1, "sm": int(r[7]),
+                 "start_us": (int(r[5]) - t0) / 1e3, "end_us": (int(r[6]) - t0) / 1e3,
+                 "phases_us": [int(x) / 1e3 for x in r[8:12]]} for r in tr]
+        with open(a.trace, "w") as f:
+            json.dump(recs, f)
+
+
+if __name__ == "__main__":
+    main()

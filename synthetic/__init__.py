@@ -60,3 +60,37 @@ def ragged_batch_shapes(count: int, seed: int, m_lo: int = 256, m_hi: int = 8192
     ms = rng.integers(m_lo, m_hi + 1, size=count)
     ns = rng.choice(np.asarray(n_choices), size=count)
     return [(int(m), int(min(n, m))) for m, n in zip(ms, ns)]
+
+
+def conditioned_device(m: int, n: int, cond: float, seed: int, device):
+    """Device-side (torch) version of conditioned() for inputs too large to build on the
+    host: A = U diag(sigma) V^T, U (m x n) and V (n x n) Haar from the QR of seeded
+    Gaussians with Mezzadri's sign correction.  Returned as a column-major float64 CUDA
+    tensor (stride (1, m)).  Deterministic for a given seed and device type."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+
+    def haar(rows, cols):
+        G = torch.randn(rows, cols, dtype=torch.float64, device=device, generator=g)
+        Q, R = torch.linalg.qr(G)
+        d = torch.sign(torch.diagonal(R))
+        d[d == 0] = 1.0
+        return Q * d
+
+    U = haar(m, n)
+    V = haar(n, n)
+    sig = torch.from_numpy(singular_values(n, cond)).to(device)
+    A = (U * sig) @ V.T
+    return A.t().contiguous().t()
+
+
+def least_squares_device(m: int, n: int, cond: float, noise: float, nrhs: int, seed: int, device):
+    """(A, X, B) of least_squares_problem() built on the device (see conditioned_device)."""
+    import torch
+    A = conditioned_device(m, n, cond, seed, device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 7919)
+    X = torch.randn(n, nrhs, dtype=torch.float64, device=device, generator=g)
+    B = A @ X + noise * torch.randn(m, nrhs, dtype=torch.float64, device=device, generator=g)
+    return A, X.t().contiguous().t(), B.t().contiguous().t()
