@@ -48,9 +48,13 @@ typedef enum {
  *   TQR_FP64   : everything in FP64 (matrix in double).
  *   TQR_FP32   : matrix in float; Householder norms and tau in FP64; updates in FP32.
  *   TQR_BF16X3 : matrix in float; norms/tau in FP64; the UNMQR/TTMQR updates on the
- *                tensor cores as split-bf16 x3 products with FP32 accumulation.
+ *                tensor cores as split-bf16 x3 products (x = hi + lo; hi*hi + hi*lo +
+ *                lo*hi, ~2^-16 relative) with FP32 accumulation.
+ *   TQR_BF16X6 : as TQR_BF16X3 with a three-way split and six products (~2^-24, close
+ *                to FP32 updates).
  *   TQR_BF16, TQR_FP16 : as TQR_BF16X3 with one bf16 / fp16 product. */
-typedef enum { TQR_FP64 = 0, TQR_BF16 = 1, TQR_FP16 = 2, TQR_BF16X3 = 3, TQR_FP32 = 4 } tqr_prec;
+typedef enum { TQR_FP64 = 0, TQR_BF16 = 1, TQR_FP16 = 2, TQR_BF16X3 = 3, TQR_FP32 = 4,
+               TQR_BF16X6 = 5 } tqr_prec;
 
 enum {
   TQR_OK = 0,

@@ -23,8 +23,8 @@ LIB_PATH = os.path.join(_PKG, "libtqr.so")
 FLAT, PLASMA, BINARY, FIBONACCI, GREEDY, GRASAP, ASAP = range(7)
 TREES = {"flat": FLAT, "plasma": PLASMA, "binary": BINARY, "fibonacci": FIBONACCI,
          "greedy": GREEDY, "grasap": GRASAP, "asap": ASAP}
-FP64, BF16, FP16, BF16X3, FP32 = 0, 1, 2, 3, 4
-PRECS = {"fp64": FP64, "bf16": BF16, "fp16": FP16, "bf16x3": BF16X3, "fp32": FP32}
+FP64, BF16, FP16, BF16X3, FP32, BF16X6 = 0, 1, 2, 3, 4, 5
+PRECS = {"fp64": FP64, "bf16": BF16, "fp16": FP16, "bf16x3": BF16X3, "fp32": FP32, "bf16x6": BF16X6}
 TQR_ETIMEOUT = 3
 TQR_EUNSUPPORTED = 5
 

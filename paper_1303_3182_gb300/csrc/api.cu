@@ -216,7 +216,12 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
   return TQR_OK;
 }
 
-bool is_tensor_prec(int prec) { return prec == TQR_BF16 || prec == TQR_FP16 || prec == TQR_BF16X3; }
+bool is_tensor_prec(int prec) {
+  return prec == TQR_BF16 || prec == TQR_FP16 || prec == TQR_BF16X3 || prec == TQR_BF16X6;
+}
+
+// 16-bit parts per operand of a tensor-core precision.
+int tensor_parts(int prec) { return prec == TQR_BF16X6 ? 3 : (prec == TQR_BF16X3 ? 2 : 1); }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -228,7 +233,7 @@ int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec
   if (ib < 1 || ib > nb || ib > 32) return -4;
   if (tree < TQR_FLAT || tree > TQR_ASAP) return -5;
   if (tree == TQR_PLASMA && bs < 1) return -6;
-  if (prec < TQR_FP64 || prec > TQR_FP32) return -7;
+  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -7;
   if (ceil_div(m, nb) > 32767 || ceil_div(n, nb) > 32767) return -3;
   return 0;
 }
@@ -290,7 +295,8 @@ int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T
   const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
   const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
   *T_bytes = static_cast<size_t>(2 * P * K) * ib * nb * esz;
-  if (is_tensor_prec(prec)) *T_bytes = align_up(*T_bytes, 1024) + static_cast<size_t>(2 * P * K) * mixed_slot_bytes();
+  if (is_tensor_prec(prec))
+    *T_bytes = align_up(*T_bytes, 1024) + static_cast<size_t>(2 * P * K) * mixed_slot_bytes(tensor_parts(prec));
   return TQR_OK;
 }
 
@@ -325,7 +331,7 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
       const int64_t K = std::min(P, Q);
       prm.mixed = 1;
       prm.ops = static_cast<char *>(T) + align_up(static_cast<size_t>(2 * P * K) * ib * nb * sizeof(float), 1024);
-      prm.nprod = prec == TQR_BF16X3 ? 3 : 1;
+      prm.nparts = tensor_parts(prec);
       prm.fmt = prec == TQR_FP16 ? 0 : 1;
     }
     return run_plan(plan, prm, dbl, static_cast<cudaStream_t>(stream));
@@ -376,7 +382,7 @@ int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int pre
 int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb, int64_t nrhs,
              void *stream) {
   if (n < 1) return -1;
-  if (prec < TQR_FP64 || prec > TQR_FP32) return -2;
+  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -2;
   if (!A) return -3;
   if (lda < n) return -4;
   if (!B) return -5;

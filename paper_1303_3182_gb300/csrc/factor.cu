@@ -740,7 +740,7 @@ size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q) {
   return bytes <= 227 * 1024 ? bytes : 0;
 }
 
-size_t mixed_slot_bytes() { return kSlotBytes; }
+size_t mixed_slot_bytes(int nparts) { return slot_bytes(nparts); }
 
 size_t mixed_executor_smem_bytes() { return mixed_smem_bytes(); }
 

@@ -13,8 +13,13 @@
 // UNMQR(i,k,j) on C (nb x nb):   W^T = C^T V  (tcgen05, TMEM)  ->  C -= Z W
 // TTMQR(i,piv,k,j) on [C1; C2]:  W^T = C1^T + C2^T V2 (TMEM initialised with C1^T)
 //                                C2 -= Z2 W,  C1 -= T^T W
-// Products are bf16 x3 (hi*hi + hi*lo + lo*hi) or a single bf16 / fp16 product, always
-// accumulated in FP32 in tensor memory.  The tensor-core tile is nb = 128.
+// Operands are split into 1, 2 or 3 16-bit parts (x = p0 + p1 + p2, each the rounding of
+// what the previous parts leave) and multiplied as the sum of the part products whose
+// orders add up to less than the part count: one bf16/fp16 product, split-bf16 x3
+// (hi*hi + hi*lo + lo*hi, ~2^-16 relative) or split-bf16 x6 (three parts, ~2^-24),
+// always accumulated in FP32 in tensor memory.  C tiles are read once into TMEM and the
+// second product accumulates onto them with a negated B, so C is read and written once.
+// The tensor-core tile is nb = 128.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -28,13 +33,15 @@ namespace {
 constexpr int kMNB = 128;                       // tile size of the tensor-core path
 constexpr int kMLD = kMNB + 1;                  // padded leading dimension of FP32 smem matrices
 constexpr uint32_t kImg = kMNB * kMNB * 2;      // one 16-bit operand image, bytes
-constexpr uint32_t kSlotBytes = 6 * kImg;       // operand images of one factored tile
-constexpr size_t kMixedSmem = 3 * 2 * kImg + 1024;  // three split operands + alignment
+constexpr size_t kMixedSmem = 6 * kImg + 1024;  // operand buffers (<= 192 KB) + alignment
 
 __host__ __device__ inline size_t mixed_smem_bytes() {
   const size_t prep = 3 * static_cast<size_t>(kMNB) * kMLD * sizeof(float) + 1024;
   return prep > kMixedSmem ? prep : kMixedSmem;
 }
+
+// Operand images of one factored tile: up to three operands (V, Z, T^T) x nparts parts.
+__host__ __device__ inline size_t slot_bytes(int nparts) { return 3 * static_cast<size_t>(nparts) * kImg; }
 
 struct MixedState {
   uint64_t *bar_ld, *bar_mma;
@@ -45,7 +52,7 @@ struct MixedState {
 
 __device__ __forceinline__ unsigned char *ops_slot(const ExecParams &p, int i, int k, int which) {
   return static_cast<unsigned char *>(p.ops) +
-         ((static_cast<size_t>(k) * p.P + i) * 2 + which) * static_cast<size_t>(kSlotBytes);
+         ((static_cast<size_t>(k) * p.P + i) * 2 + which) * slot_bytes(p.nparts);
 }
 
 __device__ __forceinline__ unsigned char *align1024(unsigned char *raw) {
@@ -53,22 +60,67 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *raw) {
   return raw + ((1024u - (a & 1023u)) & 1023u);
 }
 
-// Writes an operand image (hi, and lo when requested) whose element (row, kk) is get().
+// Splits 8 floats into nparts 16-bit parts x = p0 + p1 + p2 (each the rounding of what
+// the previous parts leave), packed 8 to a uint4.
+__device__ __forceinline__ void split8(const float *x, uint4 *parts, int nparts, int fmt) {
+  float rem[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) rem[j] = x[j];
+  for (int q = 0; q < nparts; ++q) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t lo16, hi16;
+      if (fmt == 1) {
+        const __nv_bfloat16 a = __float2bfloat16_rn(rem[2 * j]);
+        const __nv_bfloat16 b = __float2bfloat16_rn(rem[2 * j + 1]);
+        rem[2 * j] -= __bfloat162float(a);
+        rem[2 * j + 1] -= __bfloat162float(b);
+        lo16 = __bfloat16_as_ushort(a);
+        hi16 = __bfloat16_as_ushort(b);
+      } else {
+        const __half a = __float2half_rn(rem[2 * j]);
+        const __half b = __float2half_rn(rem[2 * j + 1]);
+        rem[2 * j] -= __half2float(a);
+        rem[2 * j + 1] -= __half2float(b);
+        lo16 = __half_as_ushort(a);
+        hi16 = __half_as_ushort(b);
+      }
+      w[j] = lo16 | (hi16 << 16);
+    }
+    parts[q] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// One element split into nparts 16-bit parts (raw bits).
+__device__ __forceinline__ void split1(float x, uint16_t *parts, int nparts, int fmt) {
+  float rem = x;
+  for (int q = 0; q < nparts; ++q) {
+    if (fmt == 1) {
+      const __nv_bfloat16 a = __float2bfloat16_rn(rem);
+      rem -= __bfloat162float(a);
+      parts[q] = __bfloat16_as_ushort(a);
+    } else {
+      const __half a = __float2half_rn(rem);
+      rem -= __half2float(a);
+      parts[q] = __half_as_ushort(a);
+    }
+  }
+}
+
+// Writes the nparts images (consecutive, kImg apart) of an operand whose element
+// (row, kk) is get(row, kk).
 template <typename F>
-__device__ void write_image(unsigned char *hi_img, unsigned char *lo_img, F get, int fmt, bool need_lo) {
+__device__ void write_image(unsigned char *img, F get, int fmt, int nparts) {
   for (int ch = threadIdx.x; ch < kMNB * kMNB / 8; ch += kThreads) {
     const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
     const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = get(row, k0 + j);
-    uint4 h, l;
-    if (fmt == 1)
-      umma::split8_bf16(x, h, l);
-    else
-      umma::split8_f16(x, h, l);
-    reinterpret_cast<uint4 *>(hi_img)[ch] = h;
-    if (need_lo) reinterpret_cast<uint4 *>(lo_img)[ch] = l;
+    uint4 parts[3];
+    split8(x, parts, nparts, fmt);
+    for (int q = 0; q < nparts; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
   }
 }
 
@@ -220,9 +272,9 @@ __device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   v_times_tt(Gs, Vs, Ts, [](int r0, int a0, int &b0, int &b1) { b0 = a0; b1 = min(r0 + 4, kMNB); });
   __syncthreads();
   unsigned char *slot = ops_slot(p, i, k, 0);
-  const bool lo = p.nprod == 3;
-  write_image(slot, slot + kImg, [&](int row, int kk) { return Vs[kk + row * kMLD]; }, p.fmt, lo);
-  write_image(slot + 2 * kImg, slot + 3 * kImg, [&](int row, int kk) { return Gs[row + kk * kMLD]; }, p.fmt, lo);
+  const int np = p.nparts;
+  write_image(slot, [&](int row, int kk) { return Vs[kk + row * kMLD]; }, p.fmt, np);
+  write_image(slot + np * kImg, [&](int row, int kk) { return Gs[row + kk * kMLD]; }, p.fmt, np);
   __syncthreads();
 }
 
@@ -251,55 +303,67 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   v_times_tt(Gs, Vs, Ts, [](int r0, int a0, int &b0, int &b1) { b0 = min(a0, r0); b1 = kMNB; });
   __syncthreads();
   unsigned char *slot = ops_slot(p, i, k, 1);
-  const bool lo = p.nprod == 3;
-  write_image(slot, slot + kImg, [&](int row, int kk) { return Vs[kk + row * kMLD]; }, p.fmt, lo);
-  write_image(slot + 2 * kImg, slot + 3 * kImg, [&](int row, int kk) { return Gs[row + kk * kMLD]; }, p.fmt, lo);
-  write_image(slot + 4 * kImg, slot + 5 * kImg, [&](int row, int kk) { return Ts[kk + row * kMLD]; }, p.fmt, lo);
+  const int np = p.nparts;
+  write_image(slot, [&](int row, int kk) { return Vs[kk + row * kMLD]; }, p.fmt, np);
+  write_image(slot + np * kImg, [&](int row, int kk) { return Gs[row + kk * kMLD]; }, p.fmt, np);
+  write_image(slot + 2 * np * kImg, [&](int row, int kk) { return Ts[kk + row * kMLD]; }, p.fmt, np);
   __syncthreads();
 }
 
-// D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) B^T over K = 128, both split images.
+// D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) op(B)^T over K = 128 for split operands:
+// sum of the products A_qa B_qb with qa + qb < nparts (hi*hi; + hi*lo + lo*hi for two
+// parts; + hi*lo2 + mid*mid + lo2*hi for three), smallest terms first.  neg_b negates B.
 __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const unsigned char *bufA, const unsigned char *bufB,
-                                           int nprod, int fmt, uint32_t accumulate_first) {
-  const uint32_t idesc = umma::idesc_f16(128, 128, fmt, 0);
-  const uint32_t a_hi = umma::smem_u32(bufA), a_lo = a_hi + kImg;
-  const uint32_t b_hi = umma::smem_u32(bufB), b_lo = b_hi + kImg;
+                                           int nparts, int fmt, int neg_b, uint32_t accumulate_first) {
+  const uint32_t idesc = umma::idesc_f16(128, 128, fmt, neg_b);
+  const uint32_t a0 = umma::smem_u32(bufA), b0 = umma::smem_u32(bufB);
 #pragma unroll 1
   for (int ks = 0; ks < kMNB / 16; ++ks) {
     const uint32_t off = (ks >> 2) * (kMNB * 128) + (ks & 3) * 32;
-    const uint32_t acc = (ks > 0 || accumulate_first) ? 1u : 0u;
-    if (nprod == 3) {
-      umma::mma_f16(d_tmem, umma::smem_desc(a_lo + off), umma::smem_desc(b_hi + off), idesc, acc);
-      umma::mma_f16(d_tmem, umma::smem_desc(a_hi + off), umma::smem_desc(b_lo + off), idesc, 1u);
-      umma::mma_f16(d_tmem, umma::smem_desc(a_hi + off), umma::smem_desc(b_hi + off), idesc, 1u);
-    } else {
-      umma::mma_f16(d_tmem, umma::smem_desc(a_hi + off), umma::smem_desc(b_hi + off), idesc, acc);
+    uint32_t acc = (ks > 0 || accumulate_first) ? 1u : 0u;
+    for (int s = nparts - 1; s >= 0; --s) {        // s = qa + qb
+      for (int qa = s; qa >= 0; --qa) {
+        const int qb = s - qa;
+        umma::mma_f16(d_tmem, umma::smem_desc(a0 + qa * kImg + off), umma::smem_desc(b0 + qb * kImg + off),
+                      idesc, acc);
+        acc = 1u;
+      }
     }
   }
 }
 
-// Writes C^T (row c, k = r) of a tile as a split image into shared memory.
-__device__ void c_transposed_image(unsigned char *img, const float *C, int64_t ldc, int mb, int ncols, int fmt,
-                                   bool need_lo) {
-  for (int ch = threadIdx.x; ch < kMNB * kMNB / 8; ch += kThreads) {
-    const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
-    const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
-    float x[8];
-    const float *col = C + static_cast<int64_t>(row) * ldc;
+// Loads this thread's row r of a tile (half the columns, by warp group) into registers,
+// stores them into TMEM at column base tcol (lane r), and optionally writes the split
+// image of the tile's transpose (row c, k = r) into img.
+__device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem, uint32_t tcol,
+                                  unsigned char *img, int fmt, int nparts) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = (warp & 3) * 32 + lane;
+  const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
+  for (int g = 0; g < 2; ++g) {
+    const int c0 = (warp >> 2) * 64 + g * 32;
+    float v[32];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (row < ncols && k0 + j < mb) ? __ldcg(col + k0 + j) : 0.f;
-    uint4 h, l;
-    if (fmt == 1)
-      umma::split8_bf16(x, h, l);
-    else
-      umma::split8_f16(x, h, l);
-    reinterpret_cast<uint4 *>(img)[ch] = h;
-    if (need_lo) reinterpret_cast<uint4 *>(img + kImg)[ch] = l;
+    for (int j = 0; j < 32; ++j) {
+      const int c = c0 + j;
+      v[j] = (r < nrows && c < ncols) ? __ldcg(C + r + static_cast<int64_t>(c) * ldc) : 0.f;
+    }
+    umma::tmem_st32(tmem + lane_base + tcol + c0, v);
+    if (img) {
+#pragma unroll 4
+      for (int j = 0; j < 32; ++j) {
+        uint16_t parts[3];
+        split1(v[j], parts, nparts, fmt);
+        const uint32_t off = umma::sw128_offset(c0 + j, r, kMNB);
+        for (int q = 0; q < nparts; ++q) *reinterpret_cast<uint16_t *>(img + q * kImg + off) = parts[q];
+      }
+    }
   }
+  umma::tmem_wait_st();
 }
 
 // W^T (TMEM lane c, column a) -> split image of W as a B operand (row c, k = a).
-__device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, bool need_lo) {
+__device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, int nparts) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = (warp & 3) * 32 + lane;
   const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
@@ -309,20 +373,16 @@ __device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, 
     umma::tmem_ld32(tmem_w + lane_base + a0, v);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      uint4 h, l;
-      if (fmt == 1)
-        umma::split8_bf16(v + 8 * u, h, l);
-      else
-        umma::split8_f16(v + 8 * u, h, l);
+      uint4 parts[3];
+      split8(v + 8 * u, parts, nparts, fmt);
       const uint32_t off = umma::sw128_offset(c, a0 + 8 * u, kMNB);
-      *reinterpret_cast<uint4 *>(img + off) = h;
-      if (need_lo) *reinterpret_cast<uint4 *>(img + kImg + off) = l;
+      for (int q = 0; q < nparts; ++q) *reinterpret_cast<uint4 *>(img + q * kImg + off) = parts[q];
     }
   }
 }
 
-// C(r, c) -= D(r, c) for the accumulator at tmem_d (lane r, column c).
-__device__ void subtract_from_tmem(float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem_d) {
+// Stores the accumulator at tmem_d (lane r, column c) into C(r, c).
+__device__ void tmem_to_tile(float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem_d) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = (warp & 3) * 32 + lane;
   const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
@@ -331,14 +391,9 @@ __device__ void subtract_from_tmem(float *C, int64_t ldc, int nrows, int ncols, 
     float v[32];
     umma::tmem_ld32(tmem_d + lane_base + c0, v);
     if (r < nrows) {
-#pragma unroll 8
-      for (int j = 0; j < 32; ++j) {
-        const int c = c0 + j;
-        if (c < ncols) {
-          float *ptr = C + r + static_cast<int64_t>(c) * ldc;
-          *ptr = __ldcg(ptr) - v[j];
-        }
-      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < ncols) C[r + static_cast<int64_t>(c0 + j) * ldc] = v[j];
     }
   }
 }
@@ -354,69 +409,96 @@ __device__ __forceinline__ void wait_or_flag(const ExecParams &p, uint64_t *bar,
   if (!umma::mbar_wait(bar, parity, 1ull << 26)) atomicCAS(p.status, 0, kStatusTimeout | (0x7fffff << 8));
 }
 
+// Shared-memory operand buffers: X and Y always; a third buffer Zb when the parts of
+// three operands fit (nparts <= 2), which lets the second operand load early.
+struct OperandBufs {
+  unsigned char *X, *Y, *Zb;
+  uint32_t bytes;  // nparts images
+};
+
+__device__ __forceinline__ OperandBufs operand_bufs(unsigned char *raw, int nparts) {
+  unsigned char *base = align1024(raw);
+  OperandBufs b;
+  b.bytes = static_cast<uint32_t>(nparts) * kImg;
+  b.X = base;
+  b.Y = base + b.bytes;
+  b.Zb = nparts <= 2 ? base + 2 * b.bytes : nullptr;
+  return b;
+}
+
+// UNMQR(i,k,j) on tensor cores:  D2 = C (TMEM),  W^T = C^T V,  D2 += Z (-W),  C = D2.
 __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int k, int j) {
   const TileGeom geo{p.m, p.n, kMNB};
-  unsigned char *base = align1024(raw);
-  unsigned char *bufA = base, *bufB = base + 2 * kImg, *bufZ = base + 4 * kImg;
-  const bool lo = p.nprod == 3;
-  const uint32_t nimg = lo ? 2 : 1;
+  const OperandBufs b = operand_bufs(raw, p.nparts);
   const unsigned char *slot = ops_slot(p, i, k, 0);
+  const unsigned char *imgV = slot, *imgZ = slot + b.bytes;
+  unsigned char *bufZ = b.Zb ? b.Zb : b.Y;
   if (threadIdx.x == 0) {
-    umma::mbar_expect_tx(ms.bar_ld, 2 * nimg * kImg);
-    umma::bulk_g2s(bufB, slot, nimg * kImg, ms.bar_ld);
-    umma::bulk_g2s(bufZ, slot + 2 * kImg, nimg * kImg, ms.bar_ld);
+    umma::mbar_expect_tx(ms.bar_ld, b.Zb ? 2 * b.bytes : b.bytes);
+    umma::bulk_g2s(b.Y, imgV, b.bytes, ms.bar_ld);
+    if (b.Zb) umma::bulk_g2s(b.Zb, imgZ, b.bytes, ms.bar_ld);
   }
   float *C = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  c_transposed_image(bufA, C, p.lda, mb, ncols, p.fmt, lo);
+  tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 128, b.X, p.fmt, p.nparts);
   umma::fence_proxy_async();
   sync_all_tc();
   phase_mark(ms.ph, 0);
   if (threadIdx.x == 0) {
     wait_or_flag(p, ms.bar_ld, ms.ld_phase);
     umma::fence_after();
-    issue_gemm(ms.tmem, bufA, bufB, p.nprod, p.fmt, 0);
+    issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 0);
     umma::commit(ms.bar_mma);
   }
   ms.ld_phase ^= 1;
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
+  if (!b.Zb && threadIdx.x == 0) {  // Y is free again: fetch Z into it
+    umma::mbar_expect_tx(ms.bar_ld, b.bytes);
+    umma::bulk_g2s(b.Y, imgZ, b.bytes, ms.bar_ld);
+  }
   phase_mark(ms.ph, 1);
-  w_image_from_tmem(bufA, ms.tmem, p.fmt, lo);
+  w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts);
   umma::fence_proxy_async();
   sync_all_tc();
   phase_mark(ms.ph, 2);
   if (threadIdx.x == 0) {
-    issue_gemm(ms.tmem + 128, bufZ, bufA, p.nprod, p.fmt, 0);
+    if (!b.Zb) {
+      wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+      umma::fence_after();
+    }
+    issue_gemm(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, 1);
     umma::commit(ms.bar_mma);
   }
+  if (!b.Zb) ms.ld_phase ^= 1;
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
-  subtract_from_tmem(C, p.lda, mb, ncols, ms.tmem + 128);
+  tmem_to_tile(C, p.lda, mb, ncols, ms.tmem + 128);
   sync_all_tc();
   phase_mark(ms.ph, 3);
 }
 
+// TTMQR(i,piv,k,j):  D1 = C1^T (TMEM), D2 = C2, D3 = C1;  W^T = D1 + C2^T V2;
+// D2 += Z2 (-W);  D3 += T^T (-W);  C2 = D2, C1 = D3.
 __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int piv, int k,
                                 int j) {
   const TileGeom geo{p.m, p.n, kMNB};
-  unsigned char *base = align1024(raw);
-  unsigned char *bufA = base, *bufB = base + 2 * kImg, *bufZ = base + 4 * kImg;
-  const bool lo = p.nprod == 3;
-  const uint32_t nimg = lo ? 2 : 1;
+  const OperandBufs b = operand_bufs(raw, p.nparts);
   const unsigned char *slot = ops_slot(p, i, k, 1);
+  const unsigned char *imgV = slot, *imgZ = slot + b.bytes, *imgT = slot + 2 * b.bytes;
   if (threadIdx.x == 0) {
-    umma::mbar_expect_tx(ms.bar_ld, 2 * nimg * kImg);
-    umma::bulk_g2s(bufB, slot, nimg * kImg, ms.bar_ld);
-    umma::bulk_g2s(bufZ, slot + 2 * kImg, nimg * kImg, ms.bar_ld);
+    umma::mbar_expect_tx(ms.bar_ld, b.Zb ? 2 * b.bytes : b.bytes);
+    umma::bulk_g2s(b.Y, imgV, b.bytes, ms.bar_ld);
+    if (b.Zb) umma::bulk_g2s(b.Zb, imgZ, b.bytes, ms.bar_ld);
   }
   float *C1 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, piv, j);
   float *C2 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  c_transposed_image(bufA, C2, p.lda, mb, ncols, p.fmt, lo);
-  // TMEM D1 (lane c, column a) = C1(a, c): the identity part of the TT reflectors
+  tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 128, b.X, p.fmt, p.nparts);
+  tile_rows_to_tmem(C1, p.lda, kMNB, ncols, ms.tmem, 256, nullptr, p.fmt, p.nparts);
+  // D1 (lane c, column a) = C1(a, c): the identity part of the TT reflectors
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = (warp & 3) * 32 + lane;
@@ -437,33 +519,57 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   if (threadIdx.x == 0) {
     wait_or_flag(p, ms.bar_ld, ms.ld_phase);
     umma::fence_after();
-    issue_gemm(ms.tmem, bufA, bufB, p.nprod, p.fmt, 1);
+    issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 1);
     umma::commit(ms.bar_mma);
   }
   ms.ld_phase ^= 1;
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
+  if (threadIdx.x == 0) {  // Y is free: the next operand (Z2, or T^T when Z2 is resident)
+    umma::mbar_expect_tx(ms.bar_ld, b.bytes);
+    umma::bulk_g2s(b.Y, b.Zb ? imgT : imgZ, b.bytes, ms.bar_ld);
+  }
   phase_mark(ms.ph, 1);
-  w_image_from_tmem(bufA, ms.tmem, p.fmt, lo);
+  w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts);
   umma::fence_proxy_async();
   sync_all_tc();
   phase_mark(ms.ph, 2);
   if (threadIdx.x == 0) {
-    umma::mbar_expect_tx(ms.bar_ld, nimg * kImg);
-    umma::bulk_g2s(bufB, slot + 4 * kImg, nimg * kImg, ms.bar_ld);
-    issue_gemm(ms.tmem + 128, bufZ, bufA, p.nprod, p.fmt, 0);
-    wait_or_flag(p, ms.bar_ld, ms.ld_phase);
-    umma::fence_after();
-    issue_gemm(ms.tmem + 256, bufB, bufA, p.nprod, p.fmt, 0);
-    umma::commit(ms.bar_mma);
+    if (b.Zb) {
+      issue_gemm(ms.tmem + 128, b.Zb, b.X, p.nparts, p.fmt, 1, 1);   // C2 -= Z2 W
+      wait_or_flag(p, ms.bar_ld, ms.ld_phase);                      // T^T in Y
+      umma::fence_after();
+      issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);    // C1 -= T^T W
+      umma::commit(ms.bar_mma);
+    } else {
+      wait_or_flag(p, ms.bar_ld, ms.ld_phase);                      // Z2 in Y
+      umma::fence_after();
+      issue_gemm(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, 1);
+      umma::commit(ms.bar_mma);
+    }
   }
   ms.ld_phase ^= 1;
+  if (!b.Zb) {
+    // Y held Z2: wait for that product, then bring T^T into Y
+    wait_or_flag(p, ms.bar_mma, ms.mma_phase);
+    ms.mma_phase ^= 1;
+    umma::fence_after();
+    if (threadIdx.x == 0) {
+      umma::mbar_expect_tx(ms.bar_ld, b.bytes);
+      umma::bulk_g2s(b.Y, imgT, b.bytes, ms.bar_ld);
+      wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+      umma::fence_after();
+      issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);
+      umma::commit(ms.bar_mma);
+    }
+    ms.ld_phase ^= 1;
+  }
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
-  subtract_from_tmem(C2, p.lda, mb, ncols, ms.tmem + 128);
-  subtract_from_tmem(C1, p.lda, kMNB, ncols, ms.tmem + 256);
+  tmem_to_tile(C2, p.lda, mb, ncols, ms.tmem + 128);
+  tmem_to_tile(C1, p.lda, kMNB, ncols, ms.tmem + 256);
   sync_all_tc();
   phase_mark(ms.ph, 3);
 }

@@ -113,7 +113,7 @@ struct ExecParams {
   int64_t wait_limit_ns;
   // tensor-core (mixed) mode: split operand images, products per multiply, 16-bit format
   void *ops;             // 2 * P * min(P,Q) slots of 6 operand images (else null)
-  int nprod;             // 3 = split bf16 x3, 1 = one product
+  int nparts;            // 16-bit parts per operand: 1, 2 (split x3) or 3 (split x6)
   int fmt;               // 1 = bf16, 0 = fp16
   int mixed;             // 1: GEQRT/TTQRT prepare images, UNMQR/TTMQR run on tcgen05
   int64_t *trace;        // optional: per task {claim, start, end, sm} globaltimer stamps
@@ -127,7 +127,7 @@ size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q);
 // Tile size, bytes per factored tile of operand images, and shared memory of the
 // tensor-core (mixed) executor.
 constexpr int kMixedNB = 128;
-size_t mixed_slot_bytes();
+size_t mixed_slot_bytes(int nparts);
 size_t mixed_executor_smem_bytes();
 
 // Wavefront triangular solve R X = B (R upper n x n in A, double or float), X over B.

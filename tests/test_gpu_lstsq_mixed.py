@@ -39,7 +39,7 @@ def to_dev(a):
 # (u = 2^-8 for bf16, 2^-11 fp16, ~2^-16 bf16 x3, 2^-24 fp32); harder cases need far
 # more refinement iterations.
 CASES = [(prec, m, n, nrhs, cond, noise)
-         for prec, conds in (("bf16x3", (1e4, 1e6)), ("fp32", (1e4, 1e6)), ("fp16", (1e2, 1e3)),
+         for prec, conds in (("bf16x6", (1e4, 1e6)), ("bf16x3", (1e4, 1e6)), ("fp32", (1e4, 1e6)), ("fp16", (1e2, 1e3)),
                              ("bf16", (1e1, 1e2)))
          for (m, n, nrhs, noise), cond in zip(((1024, 384, 1, 1e-3), (900, 256, 3, 1e-3)), conds)]
 CASES += [("bf16x3", 512, 512, 2, 1e4, 0.0), ("fp16", 512, 512, 2, 1e2, 0.0)]

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_1303_3182_gb300 as tqr  # noqa: E402
 
-U = {"bf16x3": 2.0 ** -16, "bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "fp32": 2.0 ** -24}
+U = {"bf16x6": 2.0 ** -23, "bf16x3": 2.0 ** -16, "bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "fp32": 2.0 ** -24}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -63,7 +63,7 @@ CASES = [(640, 384, "greedy"), (700, 300, "fibonacci"), (512, 512, "flat"), (102
          (300, 700, "greedy")]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16", "fp16"])
 @pytest.mark.parametrize("m,n,tree", CASES)
 def test_mixed_factor_is_a_qr(m, n, tree, prec):
     """R of the tensor-core factorization against the FP64 oracle (|R| up to row signs),
@@ -109,7 +109,7 @@ def test_mixed_t_matches_its_reflectors():
     assert worst <= 1e-4
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3", "bf16"])
 def test_mixed_bitwise_repeatable(prec):
     """Every task's arithmetic is fixed, so two runs give bitwise identical factors."""
     A = synthetic.gaussian(900, 500, seed=4)
@@ -128,3 +128,20 @@ def test_mixed_bf16x3_much_closer_than_bf16():
         Rf[:384] = np.triu(to_np(Ad)[:384])
         errs[prec] = np.linalg.norm(A - Q @ Rf) / np.linalg.norm(A)
     assert errs["bf16x3"] * 64 < errs["bf16"], errs
+
+
+def test_mixed_bf16x6_close_to_fp32():
+    """Three-part split with six products: the factorization's backward error is within a
+    small factor of the FP32 SIMT factorization's and far below split x3's."""
+    A = synthetic.gaussian(768, 384, seed=12).astype(np.float32).astype(np.float64)
+    errs = {}
+    for prec in ("bf16x6", "bf16x3", "fp32"):
+        Ad = to_dev(A, torch.float32)
+        T = tqr.factor(Ad, 128, 32, "greedy", 1, prec)
+        torch.cuda.synchronize()
+        Q = q_explicit(Ad, T, 768, "greedy", prec)
+        Rf = np.zeros((768, 384))
+        Rf[:384] = np.triu(to_np(Ad)[:384])
+        errs[prec] = np.linalg.norm(A - Q @ Rf) / np.linalg.norm(A)
+    assert errs["bf16x6"] < 8 * errs["fp32"] + 1e-7, errs
+    assert errs["bf16x6"] * 16 < errs["bf16x3"], errs
