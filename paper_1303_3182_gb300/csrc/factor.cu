@@ -214,7 +214,12 @@ __device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols
   __syncthreads();
 }
 
-// FP64 reflector parameters from alpha and ||x||^2 (LAPACK convention).
+// FP64 reflector parameters from alpha and ||x||^2 (LAPACK convention):
+// beta = -sign(alpha) sqrt(alpha^2 + ||x||^2), tau = (beta - alpha) / beta,
+// scal = 1 / (alpha - beta).  With p = beta (alpha - beta), one reciprocal d = 1/p gives
+// both 1/beta = (alpha - beta) d and scal = beta d.  1/sqrt and 1/p start from FP32 seeds
+// and take two Newton steps in FP64 (quadratic convergence: 2^-23 -> 2^-46 -> FP64
+// rounding), which is shorter on this GPU's FP64 pipe than sqrt and two divisions.
 __device__ __forceinline__ void reflector(double alpha, double xx, double *beta, double *tau,
                                           double *scal) {
   if (xx == 0.0) {
@@ -223,31 +228,149 @@ __device__ __forceinline__ void reflector(double alpha, double xx, double *beta,
     *scal = 0.0;
     return;
   }
-  const double nrm = sqrt(alpha * alpha + xx);
+  const double s = fma(alpha, alpha, xx);
+  if (!(s > 1e-30 && s < 1e30)) {  // outside the FP32 seed range: plain FP64 operations
+    const double nrm = sqrt(s);
+    const double b = alpha >= 0.0 ? -nrm : nrm;
+    *beta = b;
+    *tau = (b - alpha) / b;
+    *scal = 1.0 / (alpha - b);
+    return;
+  }
+  double r = static_cast<double>(rsqrtf(static_cast<float>(s)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double h = fma(-s * r, r, 1.0);  // 1 - s r^2
+    r = fma(0.5 * r, h, r);
+  }
+  const double nrm = s * r;
   const double b = alpha >= 0.0 ? -nrm : nrm;
+  const double amb = alpha - b;
+  const double pp = b * amb;
+  double d = static_cast<double>(1.0f / static_cast<float>(pp));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) d = fma(d, fma(-pp, d, 1.0), d);
   *beta = b;
-  *tau = (b - alpha) / b;
-  *scal = 1.0 / (alpha - b);
+  *scal = b * d;
+  *tau = fma(-alpha, amb * d, 1.0);
 }
 
-// Builds T (kb x kb, upper) from the Gram matrix G (strict upper part) and tau:
-// T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c).
+// Householder factorization of one panel block (kb columns) held in shared memory.
+//   GEQRT: column c of s.V; head = V(c, c), tail = V(c+1 .. rows-1, c)
+//   TT:    head = P1(c, c) (row c of R(piv)), tail = V(0 .. min(c0+c+1, mb)-1, c)
+// Reflector c updates every later column cc of the block:
+//   w = head(c, cc) + v . tail(cc);  head(c, cc) -= tau w;  tail(cc) -= tau v w,
+// with v = tail(c) * scal.  Warp 0 updates column c+1 first and at once forms the next
+// reflector (FP64 norm and tau) from it; warps 1.. update the remaining columns; column
+// c's tail is scaled in place one step later, when no warp reads it any more.  One
+// block-wide barrier per reflector.  On return the tails hold v, the heads beta, and
+// s.tau the taus.
+template <typename S, bool kTT>
+__device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto head = [&](int c, int cc) -> S & { return kTT ? s.P1[c + cc * s.ldt] : s.V[c + cc * s.ldv]; };
+  auto tlo = [&](int c) { return kTT ? 0 : c + 1; };
+  auto thi = [&](int c) { return kTT ? min(c0 + c + 1, mb) : rows; };
+  auto col = [&](int c) -> S * { return s.V + c * s.ldv; };
+  // the reflector of column c, by one warp, from its current values
+  auto make_reflector = [&](int c) {
+    double xx = 0.0;
+    const S *x = col(c);
+    for (int r = tlo(c) + lane; r < thi(c); r += 32) {
+      const double v = static_cast<double>(x[r]);
+      xx = fma(v, v, xx);
+    }
+    xx = warp_sum(xx);
+    if (lane == 0) {
+      double beta, tau, scal;
+      reflector(static_cast<double>(head(c, c)), xx, &beta, &tau, &scal);
+      head(c, c) = static_cast<S>(beta);
+      s.tau[c] = tau;
+      s.scal[c & 1] = scal;
+    }
+  };
+  auto update = [&](int c, int cc, S t, S sc) {
+    const S *x = col(c);
+    S *y = col(cc);
+    const int lo = tlo(c), hi = thi(c);
+    S part = 0;
+    for (int r = lo + lane; r < hi; r += 32) part += (x[r] * sc) * y[r];
+    const S w = head(c, cc) + warp_sum(part);
+    if (lane == 0) head(c, cc) -= t * w;
+    const S tw = t * w;
+    for (int r = lo + lane; r < hi; r += 32) y[r] -= (x[r] * sc) * tw;
+  };
+  auto scale_tail = [&](int c) {
+    const S sc = static_cast<S>(s.scal[c & 1]);
+    S *x = col(c);
+    for (int r = tlo(c) + lane; r < thi(c); r += 32) x[r] = x[r] * sc;
+  };
+  if (warp == 0) make_reflector(0);
+  __syncthreads();
+  for (int c = 0; c < kb; ++c) {
+    const double tau = s.tau[c];
+    const S t = static_cast<S>(tau);
+    const S sc = static_cast<S>(s.scal[c & 1]);
+    if (warp == 0) {
+      if (c + 1 < kb) {
+        if (tau != 0.0) update(c, c + 1, t, sc);
+        __syncwarp();
+        make_reflector(c + 1);
+      }
+    } else {
+      if (tau != 0.0)
+        for (int cc = c + 1 + warp; cc < kb; cc += kWarps - 1) update(c, cc, t, sc);
+      if (warp == kWarps - 1 && c >= 1) scale_tail(c - 1);
+    }
+    __syncthreads();
+  }
+  if (warp == kWarps - 1) scale_tail(kb - 1);
+  __syncthreads();
+}
+
+// Gram matrix G(a, c) = v_a . v_c (all a, c < kb) of a panel block's reflectors, with the
+// explicit vectors (GEQRT: unit diagonal, zeros above; TT: the stored tails, zeros below).
+template <typename S, bool kTT>
+__device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
+  const int a = threadIdx.x & 31, cg = threadIdx.x >> 5;
+  auto vexp = [&](int r, int c) -> S {
+    if (c >= kb) return S(0);
+    if (kTT) return s.V[r + c * s.ldv];
+    return r > c ? s.V[r + c * s.ldv] : (r == c ? S(1) : S(0));
+  };
+  S acc[4] = {0, 0, 0, 0};
+  for (int r = 0; r < nrows; ++r) {
+    const S va = vexp(r, a);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += va * vexp(r, cg + kWarps * u);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = cg + kWarps * u;
+    if (a < kb && c < kb) s.G[a + c * s.ldt] = acc[u];
+  }
+  __syncthreads();
+}
+
+// Builds T (kb x kb, upper) from the Gram matrix G and tau (Schreiber-Van Loan):
+// T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c).  Columns of T not yet formed
+// are zero, so each step is one fixed-length dot product per lane.
 template <typename S>
 __device__ void build_t(Smem<S> &s, int kb) {
   if (threadIdx.x < 32) {
     const int a = threadIdx.x;
+    for (int b = 0; b < kb; ++b)
+      if (a < kb) s.T[a + b * s.ldt] = 0;
+    __syncwarp();
     for (int c = 0; c < kb; ++c) {
       const double tc = s.tau[c];
-      S val = 0;
-      if (a < c) {
-        S acc = 0;
-        for (int b = a; b < c; ++b) acc += s.T[a + b * s.ldt] * s.G[b + c * s.ldt];
-        val = static_cast<S>(-tc) * acc;
-      } else if (a == c) {
-        val = static_cast<S>(tc);
-      }
+      S acc = 0;
+#pragma unroll
+      for (int b = 0; b < 32; ++b)
+        if (b < c) acc += s.T[a + b * s.ldt] * s.G[b + c * s.ldt];
+      const S val = a < c ? static_cast<S>(-tc) * acc : (a == c ? static_cast<S>(tc) : S(0));
       __syncwarp();
-      if (a < kb) s.T[a + c * s.ldt] = (a <= c) ? val : S(0);
+      if (a < kb) s.T[a + c * s.ldt] = val;
       __syncwarp();
     }
   }
@@ -313,52 +436,9 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
     Real *blk = tile + c0 + static_cast<int64_t>(c0) * p.lda;
     load_block(s.V, s.ldv, blk, p.lda, rows, kb);
     __syncthreads();
-    for (int c = 0; c < kb; ++c) {
-      if (warp == 0) {
-        double xx = 0.0;
-        for (int r = c + 1 + lane; r < rows; r += 32) {
-          const double x = static_cast<double>(s.V[r + c * s.ldv]);
-          xx += x * x;
-        }
-        xx = warp_sum(xx);
-        if (lane == 0) {
-          double beta, tau, scal;
-          reflector(static_cast<double>(s.V[c + c * s.ldv]), xx, &beta, &tau, &scal);
-          s.V[c + c * s.ldv] = static_cast<S>(beta);
-          s.tau[c] = tau;
-          s.scal[0] = scal;
-        }
-      }
-      __syncthreads();
-      const double tau = s.tau[c], scal = s.scal[0];
-      if (tau != 0.0) {
-        for (int r = c + 1 + threadIdx.x; r < rows; r += kThreads)
-          s.V[r + c * s.ldv] = static_cast<S>(static_cast<double>(s.V[r + c * s.ldv]) * scal);
-        __syncthreads();
-        const S t = static_cast<S>(tau);
-        for (int cc = c + 1 + warp; cc < kb; cc += kWarps) {
-          S part = 0;
-          for (int r = c + 1 + lane; r < rows; r += 32) part += s.V[r + c * s.ldv] * s.V[r + cc * s.ldv];
-          const S w = s.V[c + cc * s.ldv] + warp_sum(part);
-          if (lane == 0) s.V[c + cc * s.ldv] -= t * w;
-          for (int r = c + 1 + lane; r < rows; r += 32) s.V[r + cc * s.ldv] -= t * s.V[r + c * s.ldv] * w;
-        }
-      }
-      __syncthreads();
-    }
+    panel_factor<S, false>(s, kb, rows, c0, mb);
     phase_mark(s.ph, 0);
-    // Gram matrix G(a,c) = v_a . v_c (a < c) of the block's reflectors
-    const int npair = kb * (kb - 1) / 2;
-    for (int pidx = warp; pidx < npair; pidx += kWarps) {
-      int c = 1, base = 0;
-      while (base + c <= pidx) { base += c; ++c; }
-      const int a = pidx - base;
-      S part = 0;
-      for (int r = c + 1 + lane; r < rows; r += 32) part += s.V[r + a * s.ldv] * s.V[r + c * s.ldv];
-      part = warp_sum(part);
-      if (lane == 0) s.G[a + c * s.ldt] = s.V[c + a * s.ldv] + part;
-    }
-    __syncthreads();
+    panel_gram<S, false>(s, kb, rows);
     build_t(s, kb);
     store_block(blk, p.lda, s.V, s.ldv, rows, kb);
     store_t(Tg, ib, c0, width, s, kb);
@@ -418,53 +498,9 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
           (r <= c) ? static_cast<S>(ldcg(t1 + (c0 + r) + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
     }
     __syncthreads();
-    for (int c = 0; c < kb; ++c) {
-      const int rr = min(c0 + c + 1, mb);
-      if (warp == 0) {
-        double xx = 0.0;
-        for (int r = lane; r < rr; r += 32) {
-          const double x = static_cast<double>(s.V[r + c * s.ldv]);
-          xx += x * x;
-        }
-        xx = warp_sum(xx);
-        if (lane == 0) {
-          double beta, tau, scal;
-          reflector(static_cast<double>(s.P1[c + c * s.ldt]), xx, &beta, &tau, &scal);
-          s.P1[c + c * s.ldt] = static_cast<S>(beta);
-          s.tau[c] = tau;
-          s.scal[0] = scal;
-        }
-      }
-      __syncthreads();
-      const double tau = s.tau[c], scal = s.scal[0];
-      if (tau != 0.0) {
-        for (int r = threadIdx.x; r < rr; r += kThreads)
-          s.V[r + c * s.ldv] = static_cast<S>(static_cast<double>(s.V[r + c * s.ldv]) * scal);
-        __syncthreads();
-        const S t = static_cast<S>(tau);
-        for (int cc = c + 1 + warp; cc < kb; cc += kWarps) {
-          S part = 0;
-          for (int r = lane; r < rr; r += 32) part += s.V[r + c * s.ldv] * s.V[r + cc * s.ldv];
-          const S w = s.P1[c + cc * s.ldt] + warp_sum(part);
-          if (lane == 0) s.P1[c + cc * s.ldt] -= t * w;
-          for (int r = lane; r < rr; r += 32) s.V[r + cc * s.ldv] -= t * s.V[r + c * s.ldv] * w;
-        }
-      }
-      __syncthreads();
-    }
+    panel_factor<S, true>(s, kb, rb, c0, mb);
     phase_mark(s.ph, 0);
-    const int npair = kb * (kb - 1) / 2;
-    for (int pidx = warp; pidx < npair; pidx += kWarps) {
-      int c = 1, base = 0;
-      while (base + c <= pidx) { base += c; ++c; }
-      const int a = pidx - base;
-      const int ra = min(c0 + a + 1, mb);
-      S part = 0;
-      for (int r = lane; r < ra; r += 32) part += s.V[r + a * s.ldv] * s.V[r + c * s.ldv];
-      part = warp_sum(part);
-      if (lane == 0) s.G[a + c * s.ldt] = part;
-    }
-    __syncthreads();
+    panel_gram<S, true>(s, kb, rb);
     build_t(s, kb);
     // write back the upper parts only (the lower parts hold GEQRT reflectors)
     for (int c = warp; c < kb; c += kWarps)
