@@ -332,6 +332,7 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
       prm.mixed = 1;
       prm.ops = static_cast<char *>(T) + align_up(static_cast<size_t>(2 * P * K) * ib * nb * sizeof(float), 1024);
       prm.nparts = tensor_parts(prec);
+      prm.vec4 = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
       prm.fmt = prec == TQR_FP16 ? 0 : 1;
     }
     return run_plan(plan, prm, dbl, static_cast<cudaStream_t>(stream));

@@ -78,7 +78,7 @@ __device__ __forceinline__ S warp_sum(S v) {
 template <typename S>
 struct Smem {
   double *tau;   // [ib] tau of the current block, FP64
-  double *scal;  // [2]  1 / (alpha - beta) of the current reflector
+  double *scal;  // [ib] 1 / (alpha - beta) of each reflector of the block
   S *V;          // [ldv * ib]  panel / reflector block
   S *C;          // [ldv * kCW] update chunk (C, or C2 of a TT pair)
   S *C1;         // [ldv * kCW] C1 chunk of a TT pair
@@ -94,7 +94,7 @@ __host__ __device__ inline int odd_ld(int x) { return x | 1; }
 
 __host__ __device__ inline size_t smem_elems(int nb, int ib, size_t s_size) {
   const size_t ldv = odd_ld(nb), ldw = ib + 1, ldt = ib + 1;
-  const size_t d_bytes = (static_cast<size_t>(ib) + 2) * sizeof(double);
+  const size_t d_bytes = 2 * static_cast<size_t>(ib) * sizeof(double);
   const size_t s_elems = ldv * ib + 2 * ldv * kCW + ldw * kCW + 3 * ldt * ib;
   return d_bytes + s_elems * s_size;
 }
@@ -107,7 +107,7 @@ __device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
   s.ldt = ib + 1;
   s.tau = reinterpret_cast<double *>(raw);
   s.scal = s.tau + ib;
-  S *p = reinterpret_cast<S *>(s.scal + 2);
+  S *p = reinterpret_cast<S *>(s.scal + ib);
   s.V = p;
   p += s.ldv * ib;
   s.C = p;
@@ -220,6 +220,7 @@ __device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols
 // both 1/beta = (alpha - beta) d and scal = beta d.  1/sqrt and 1/p start from FP32 seeds
 // and take two Newton steps in FP64 (quadratic convergence: 2^-23 -> 2^-46 -> FP64
 // rounding), which is shorter on this GPU's FP64 pipe than sqrt and two divisions.
+template <int kNewton>
 __device__ __forceinline__ void reflector(double alpha, double xx, double *beta, double *tau,
                                           double *scal) {
   if (xx == 0.0) {
@@ -239,7 +240,7 @@ __device__ __forceinline__ void reflector(double alpha, double xx, double *beta,
   }
   double r = static_cast<double>(rsqrtf(static_cast<float>(s)));
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < kNewton; ++it) {
     const double h = fma(-s * r, r, 1.0);  // 1 - s r^2
     r = fma(0.5 * r, h, r);
   }
@@ -249,10 +250,47 @@ __device__ __forceinline__ void reflector(double alpha, double xx, double *beta,
   const double pp = b * amb;
   double d = static_cast<double>(1.0f / static_cast<float>(pp));
 #pragma unroll
-  for (int it = 0; it < 2; ++it) d = fma(d, fma(-pp, d, 1.0), d);
+  for (int it = 0; it < kNewton; ++it) d = fma(d, fma(-pp, d, 1.0), d);
   *beta = b;
   *scal = b * d;
   *tau = fma(-alpha, amb * d, 1.0);
+}
+
+// Sum of squares of FP32 values to FP64 accuracy with FP32 instructions: each square
+// is split exactly (x*x = p + e, e = fma(x, x, -p)) and the parts are accumulated with
+// error-free TwoSum (Knuth) into a (hi, lo) pair; the pair is converted to FP64 once.
+struct DFloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DFloat df_add(DFloat a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b - bb);
+  return DFloat{s, a.lo + err};
+}
+
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+  DFloat r = df_add(a, b.hi);
+  r.lo += b.lo;
+  return r;
+}
+
+__device__ __forceinline__ DFloat df_sq_acc(DFloat acc, float x) {
+  const float p = x * x;
+  const float e = fmaf(x, x, -p);
+  DFloat r = df_add(acc, p);
+  r.lo += e;
+  return r;
+}
+
+__device__ __forceinline__ double df_warp_sum(DFloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DFloat w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, w);
+  }
+  return static_cast<double>(v.hi) + static_cast<double>(v.lo);
 }
 
 // Householder factorization of one panel block (kb columns) held in shared memory.
@@ -274,19 +312,30 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
   auto col = [&](int c) -> S * { return s.V + c * s.ldv; };
   // the reflector of column c, by one warp, from its current values
   auto make_reflector = [&](int c) {
-    double xx = 0.0;
     const S *x = col(c);
-    for (int r = tlo(c) + lane; r < thi(c); r += 32) {
-      const double v = static_cast<double>(x[r]);
-      xx = fma(v, v, xx);
+    double xx;
+    if (sizeof(S) == sizeof(float)) {
+      DFloat acc{0.f, 0.f};
+      for (int r = tlo(c) + lane; r < thi(c); r += 32) acc = df_sq_acc(acc, static_cast<float>(x[r]));
+      xx = df_warp_sum(acc);
+    } else {
+      xx = 0.0;
+      for (int r = tlo(c) + lane; r < thi(c); r += 32) {
+        const double v = static_cast<double>(x[r]);
+        xx = fma(v, v, xx);
+      }
+      xx = warp_sum(xx);
     }
-    xx = warp_sum(xx);
     if (lane == 0) {
       double beta, tau, scal;
-      reflector(static_cast<double>(head(c, c)), xx, &beta, &tau, &scal);
+      // FP32 storage keeps ~2^-24 of these scalars: one Newton step (2^-46) suffices
+      if (sizeof(S) == sizeof(float))
+        reflector<1>(static_cast<double>(head(c, c)), xx, &beta, &tau, &scal);
+      else
+        reflector<2>(static_cast<double>(head(c, c)), xx, &beta, &tau, &scal);
       head(c, c) = static_cast<S>(beta);
       s.tau[c] = tau;
-      s.scal[c & 1] = scal;
+      s.scal[c] = scal;
     }
   };
   auto update = [&](int c, int cc, S t, S sc) {
@@ -301,7 +350,7 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
     for (int r = lo + lane; r < hi; r += 32) y[r] -= (x[r] * sc) * tw;
   };
   auto scale_tail = [&](int c) {
-    const S sc = static_cast<S>(s.scal[c & 1]);
+    const S sc = static_cast<S>(s.scal[c]);
     S *x = col(c);
     for (int r = tlo(c) + lane; r < thi(c); r += 32) x[r] = x[r] * sc;
   };
@@ -310,7 +359,7 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
   for (int c = 0; c < kb; ++c) {
     const double tau = s.tau[c];
     const S t = static_cast<S>(tau);
-    const S sc = static_cast<S>(s.scal[c & 1]);
+    const S sc = static_cast<S>(s.scal[c]);
     if (warp == 0) {
       if (c + 1 < kb) {
         if (tau != 0.0) update(c, c + 1, t, sc);

@@ -124,38 +124,36 @@ __device__ void write_image(unsigned char *img, F get, int fmt, int nparts) {
   }
 }
 
-// G(a, c) = sum_r V(r, a) V(r, c) for a < c over the rows rlo(a0,c0)..rhi, in 4x4 tiles.
+// G(a, c) = sum_r V(r, a) V(r, c) for a < c.  Thread (warp w, lane l) forms rows
+// a = l + 32x (x < 4) of columns c = 16w .. 16w+15: the V(r, a) loads of a warp hit
+// consecutive words, the V(r, c) loads are broadcasts.  range(c_lo, r0, r1) bounds r.
 template <typename RowRange>
 __device__ void gram_upper(float *G, const float *V, RowRange range) {
-  for (int t = threadIdx.x; t < 32 * 32; t += kThreads) {
-    const int ta = t & 31, tc = t >> 5;
-    if (ta > tc) continue;
-    const int a0 = ta * 4, c0 = tc * 4;
-    int r0, r1;
-    range(a0, c0, r0, r1);
-    float acc[4][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cb = warp * 16;
+  int r0, r1;
+  range(cb, r0, r1);
+  float acc[4][16];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 16; ++y) acc[x][y] = 0.f;
+  for (int r = r0; r < r1; ++r) {
+    float va[4], vc[16];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) va[x] = V[r + (lane + 32 * x) * kMLD];
+#pragma unroll
+    for (int y = 0; y < 16; ++y) vc[y] = V[r + (cb + y) * kMLD];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-    for (int r = r0; r < r1; ++r) {
-      float va[4], vc[4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        va[x] = V[r + (a0 + x) * kMLD];
-        vc[x] = V[r + (c0 + x) * kMLD];
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] += va[x] * vc[y];
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y)
-        if (a0 + x < c0 + y) G[(a0 + x) + (c0 + y) * kMLD] = acc[x][y];
+      for (int y = 0; y < 16; ++y) acc[x][y] += va[x] * vc[y];
   }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 16; ++y)
+      if (lane + 32 * x < cb + y) G[(lane + 32 * x) + (cb + y) * kMLD] = acc[x][y];
 }
 
 // T_full from its ib x ib diagonal blocks (already in Ts) and the Gram matrix (Gs).
@@ -204,36 +202,34 @@ __device__ void assemble_t(float *Ts, float *Gs, int ib) {
   }
 }
 
-// Z(r, a) = sum_b V(r, b) T(a, b) (= V T^T), b over [max(a0, blo(r0)), bhi(r0)) in 4x4 tiles.
+// Z(r, a) = sum_b V(r, b) T(a, b) (= V T^T).  Thread (warp w, lane l) forms rows
+// r = l + 32x of columns a = 16w .. 16w+15; bounds(a_lo, b0, b1) limits b.
 template <typename Bounds>
 __device__ void v_times_tt(float *Z, const float *V, const float *Ts, Bounds bounds) {
-  for (int t = threadIdx.x; t < 32 * 32; t += kThreads) {
-    const int tr = t & 31, ta = t >> 5;
-    const int r0 = tr * 4, a0 = ta * 4;
-    int b0, b1;
-    bounds(r0, a0, b0, b1);
-    float acc[4][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ab = warp * 16;
+  int b0, b1;
+  bounds(ab, b0, b1);
+  float acc[4][16];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 16; ++y) acc[x][y] = 0.f;
+  for (int b = b0; b < b1; ++b) {
+    float vr[4], tt[16];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) vr[x] = V[(lane + 32 * x) + b * kMLD];
+#pragma unroll
+    for (int y = 0; y < 16; ++y) tt[y] = Ts[(ab + y) + b * kMLD];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-    for (int b = b0; b < b1; ++b) {
-      float vr[4], ta4[4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        vr[x] = V[(r0 + x) + b * kMLD];
-        ta4[x] = Ts[(a0 + x) + b * kMLD];
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] += vr[x] * ta4[y];
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) Z[(r0 + x) + (a0 + y) * kMLD] = acc[x][y];
+      for (int y = 0; y < 16; ++y) acc[x][y] += vr[x] * tt[y];
   }
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 16; ++y) Z[(lane + 32 * x) + (ab + y) * kMLD] = acc[x][y];
 }
 
 // Loads the ib-blocked T of a factored tile into the block diagonal of Ts (zeros elsewhere).
@@ -265,11 +261,11 @@ __device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   load_t_blocks(Ts, Tg, p.ib);
   __syncthreads();
   // G(a, c) = v_a . v_c over rows r >= c (v_c is zero above its diagonal)
-  gram_upper(Gs, Vs, [](int a0, int c0, int &r0, int &r1) { r0 = c0; r1 = kMNB; });
+  gram_upper(Gs, Vs, [](int c_lo, int &r0, int &r1) { r0 = c_lo; r1 = kMNB; });
   __syncthreads();
   assemble_t(Ts, Gs, p.ib);
   // Z = V T^T: Z(r, a) = sum_{a <= b <= r} V(r, b) T(a, b)
-  v_times_tt(Gs, Vs, Ts, [](int r0, int a0, int &b0, int &b1) { b0 = a0; b1 = min(r0 + 4, kMNB); });
+  v_times_tt(Gs, Vs, Ts, [](int a_lo, int &b0, int &b1) { b0 = a_lo; b1 = kMNB; });
   __syncthreads();
   unsigned char *slot = ops_slot(p, i, k, 0);
   const int np = p.nparts;
@@ -296,11 +292,11 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   load_t_blocks(Ts, Tt, p.ib);
   __syncthreads();
   // G(a, c) = v_a . v_c over rows r <= a (the tails live in the upper triangle)
-  gram_upper(Gs, Vs, [](int a0, int c0, int &r0, int &r1) { r0 = 0; r1 = min(a0 + 4, kMNB); });
+  gram_upper(Gs, Vs, [](int c_lo, int &r0, int &r1) { r0 = 0; r1 = min(c_lo + 16, kMNB); });
   __syncthreads();
   assemble_t(Ts, Gs, p.ib);
   // Z2(r, a) = sum_{b >= max(a, r)} V2(r, b) T(a, b)
-  v_times_tt(Gs, Vs, Ts, [](int r0, int a0, int &b0, int &b1) { b0 = min(a0, r0); b1 = kMNB; });
+  v_times_tt(Gs, Vs, Ts, [](int a_lo, int &b0, int &b1) { b0 = a_lo; b1 = kMNB; });
   __syncthreads();
   unsigned char *slot = ops_slot(p, i, k, 1);
   const int np = p.nparts;
@@ -332,11 +328,9 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const unsigned char 
   }
 }
 
-// Loads this thread's row r of a tile (half the columns, by warp group) into registers,
-// stores them into TMEM at column base tcol (lane r), and optionally writes the split
-// image of the tile's transpose (row c, k = r) into img.
-__device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem, uint32_t tcol,
-                                  unsigned char *img, int fmt, int nparts) {
+// Loads this thread's row r of a tile (half the columns, by warp group) and stores it
+// into TMEM at column base tcol (lane r).
+__device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem, uint32_t tcol) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = (warp & 3) * 32 + lane;
   const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
@@ -349,17 +343,33 @@ __device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int nc
       v[j] = (r < nrows && c < ncols) ? __ldcg(C + r + static_cast<int64_t>(c) * ldc) : 0.f;
     }
     umma::tmem_st32(tmem + lane_base + tcol + c0, v);
-    if (img) {
-#pragma unroll 4
-      for (int j = 0; j < 32; ++j) {
-        uint16_t parts[3];
-        split1(v[j], parts, nparts, fmt);
-        const uint32_t off = umma::sw128_offset(c0 + j, r, kMNB);
-        for (int q = 0; q < nparts; ++q) *reinterpret_cast<uint16_t *>(img + q * kImg + off) = parts[q];
-      }
-    }
   }
   umma::tmem_wait_st();
+}
+
+// Split image of C^T (row c, k = r) in shared memory, one 16-byte chunk (8 rows of one
+// column) per thread step; the rows come as two float4 loads when the tile is 16-byte
+// aligned (vec4), else one by one.
+__device__ void c_transposed_image(unsigned char *img, const float *C, int64_t ldc, int mb, int ncols, int fmt,
+                                   int nparts, bool vec4) {
+  for (int ch = threadIdx.x; ch < kMNB * kMNB / 8; ch += kThreads) {
+    const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
+    const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
+    float x[8];
+    const float *colp = C + static_cast<int64_t>(row) * ldc + k0;
+    if (row < ncols && vec4 && k0 + 8 <= mb) {
+      const float4 a = __ldcg(reinterpret_cast<const float4 *>(colp));
+      const float4 b = __ldcg(reinterpret_cast<const float4 *>(colp + 4));
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+      x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = (row < ncols && k0 + j < mb) ? __ldcg(colp + j) : 0.f;
+    }
+    uint4 parts[3];
+    split8(x, parts, nparts, fmt);
+    for (int q = 0; q < nparts; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
+  }
 }
 
 // W^T (TMEM lane c, column a) -> split image of W as a B operand (row c, k = a).
@@ -440,7 +450,8 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   }
   float *C = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 128, b.X, p.fmt, p.nparts);
+  c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
+  tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 128);
   umma::fence_proxy_async();
   sync_all_tc();
   phase_mark(ms.ph, 0);
@@ -496,8 +507,9 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   float *C1 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, piv, j);
   float *C2 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 128, b.X, p.fmt, p.nparts);
-  tile_rows_to_tmem(C1, p.lda, kMNB, ncols, ms.tmem, 256, nullptr, p.fmt, p.nparts);
+  c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
+  tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 128);
+  tile_rows_to_tmem(C1, p.lda, kMNB, ncols, ms.tmem, 256);
   // D1 (lane c, column a) = C1(a, c): the identity part of the TT reflectors
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -507,8 +519,16 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     for (int g = 0; g < 2; ++g) {
       const int a0 = (warp >> 2) * 64 + g * 32;
       float v[32];
+      if (c < ncols && p.vec4) {
 #pragma unroll
-      for (int u = 0; u < 32; ++u) v[u] = c < ncols ? __ldcg(col + a0 + u) : 0.f;
+        for (int u = 0; u < 8; ++u) {
+          const float4 q4 = __ldcg(reinterpret_cast<const float4 *>(col + a0) + u);
+          v[4 * u] = q4.x; v[4 * u + 1] = q4.y; v[4 * u + 2] = q4.z; v[4 * u + 3] = q4.w;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) v[u] = c < ncols ? __ldcg(col + a0 + u) : 0.f;
+      }
       umma::tmem_st32(ms.tmem + lane_base + a0, v);
     }
     umma::tmem_wait_st();

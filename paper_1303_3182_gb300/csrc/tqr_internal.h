@@ -116,6 +116,7 @@ struct ExecParams {
   int nparts;            // 16-bit parts per operand: 1, 2 (split x3) or 3 (split x6)
   int fmt;               // 1 = bf16, 0 = fp16
   int mixed;             // 1: GEQRT/TTQRT prepare images, UNMQR/TTMQR run on tcgen05
+  int vec4;              // A is 16-byte aligned with lda % 4 == 0 (vector loads allowed)
   int64_t *trace;        // optional: per task {claim, start, end, sm} globaltimer stamps
 };
 
