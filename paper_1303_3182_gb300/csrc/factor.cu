@@ -79,6 +79,8 @@ template <typename S>
 struct Smem {
   double *tau;   // [ib] tau of the current block, FP64
   double *scal;  // [ib] 1 / (alpha - beta) of each reflector of the block
+  S *tau_s;      // [ib] tau in the compute type (read by every warp)
+  S *scal_s;     // [ib] scal in the compute type
   S *V;          // [ldv * ib]  panel / reflector block
   S *C;          // [ldv * kCW] update chunk (C, or C2 of a TT pair)
   S *C1;         // [ldv * kCW] C1 chunk of a TT pair
@@ -95,7 +97,7 @@ __host__ __device__ inline int odd_ld(int x) { return x | 1; }
 __host__ __device__ inline size_t smem_elems(int nb, int ib, size_t s_size) {
   const size_t ldv = odd_ld(nb), ldw = ib + 1, ldt = ib + 1;
   const size_t d_bytes = 2 * static_cast<size_t>(ib) * sizeof(double);
-  const size_t s_elems = ldv * ib + 2 * ldv * kCW + ldw * kCW + 3 * ldt * ib;
+  const size_t s_elems = ldv * ib + 2 * ldv * kCW + ldw * kCW + 3 * ldt * ib + 2 * ib;
   return d_bytes + s_elems * s_size;
 }
 
@@ -121,6 +123,10 @@ __device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
   s.G = p;
   p += s.ldt * ib;
   s.P1 = p;
+  p += s.ldt * ib;
+  s.tau_s = p;
+  p += ib;
+  s.scal_s = p;
   return s;
 }
 
@@ -336,6 +342,8 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
       head(c, c) = static_cast<S>(beta);
       s.tau[c] = tau;
       s.scal[c] = scal;
+      s.tau_s[c] = static_cast<S>(tau);
+      s.scal_s[c] = static_cast<S>(scal);
     }
   };
   auto update = [&](int c, int cc, S t, S sc) {
@@ -350,24 +358,24 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
     for (int r = lo + lane; r < hi; r += 32) y[r] -= (x[r] * sc) * tw;
   };
   auto scale_tail = [&](int c) {
-    const S sc = static_cast<S>(s.scal[c]);
+    const S sc = s.scal_s[c];
     S *x = col(c);
     for (int r = tlo(c) + lane; r < thi(c); r += 32) x[r] = x[r] * sc;
   };
   if (warp == 0) make_reflector(0);
   __syncthreads();
   for (int c = 0; c < kb; ++c) {
-    const double tau = s.tau[c];
-    const S t = static_cast<S>(tau);
-    const S sc = static_cast<S>(s.scal[c]);
+    // only lane 0 of warp 0 touches FP64: the other warps share its FP64 pipe
+    const S t = s.tau_s[c];
+    const S sc = s.scal_s[c];
     if (warp == 0) {
       if (c + 1 < kb) {
-        if (tau != 0.0) update(c, c + 1, t, sc);
+        if (t != S(0)) update(c, c + 1, t, sc);
         __syncwarp();
         make_reflector(c + 1);
       }
     } else {
-      if (tau != 0.0)
+      if (t != S(0))
         for (int cc = c + 1 + warp; cc < kb; cc += kWarps - 1) update(c, cc, t, sc);
       if (warp == kWarps - 1 && c >= 1) scale_tail(c - 1);
     }
@@ -412,12 +420,12 @@ __device__ void build_t(Smem<S> &s, int kb) {
       if (a < kb) s.T[a + b * s.ldt] = 0;
     __syncwarp();
     for (int c = 0; c < kb; ++c) {
-      const double tc = s.tau[c];
+      const S tc = s.tau_s[c];
       S acc = 0;
 #pragma unroll
       for (int b = 0; b < 32; ++b)
         if (b < c) acc += s.T[a + b * s.ldt] * s.G[b + c * s.ldt];
-      const S val = a < c ? static_cast<S>(-tc) * acc : (a == c ? static_cast<S>(tc) : S(0));
+      const S val = a < c ? -tc * acc : (a == c ? tc : S(0));
       __syncwarp();
       if (a < kb) s.T[a + c * s.ldt] = val;
       __syncwarp();

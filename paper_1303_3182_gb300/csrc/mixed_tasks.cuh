@@ -158,46 +158,71 @@ __device__ void gram_upper(float *G, const float *V, RowRange range) {
 
 // T_full from its ib x ib diagonal blocks (already in Ts) and the Gram matrix (Gs).
 // Block column j: X = G(0:c0, blk) T(blk, blk);  T(0:c0, blk) = -T(0:c0, 0:c0) X.
+// Thread (warp w, lane l) forms rows a = l + 32x of the block column's w-th group of
+// columns (w < w_blk / 4 ... one column per warp when w_blk = 32), so loads of a warp are
+// consecutive words or broadcasts.
 __device__ void assemble_t(float *Ts, float *Gs, int ib) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c0 = ib; c0 < kMNB; c0 += ib) {
     const int w = min(ib, kMNB - c0);
-    const int nout = c0 * w;
-    float reg[16];
+    const int nx = (c0 + 31) / 32;  // row groups of 32 above the block
+    // columns of the block column handled by this warp: cc = warp, warp + 8, ...
+    float acc[4][4];
+    // X = G(0:c0, blk) T(blk, blk): X(a, cc) = sum_{b <= cc} G(a, c0+b) T(c0+b, c0+cc)
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const int o = threadIdx.x + s * kThreads;
-      reg[s] = 0.f;
-      if (o < nout) {
-        const int a = o % c0, cc = o / c0;
-        float acc = 0.f;
-        for (int b = 0; b <= cc; ++b) acc += Gs[a + (c0 + b) * kMLD] * Ts[(c0 + b) + (c0 + cc) * kMLD];
-        reg[s] = acc;
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+    for (int b = 0; b < w; ++b) {
+      float g[4], t[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) g[x] = (x < nx) ? Gs[(lane + 32 * x) + (c0 + b) * kMLD] : 0.f;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int cc = warp + 8 * y;
+        t[y] = (cc < w) ? Ts[(c0 + b) + (c0 + cc) * kMLD] : 0.f;
       }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += g[x] * t[y];
     }
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const int o = threadIdx.x + s * kThreads;
-      if (o < nout) Gs[(o % c0) + (c0 + o / c0) * kMLD] = reg[s];
-    }
-    __syncthreads();
+    for (int x = 0; x < 4; ++x)
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const int o = threadIdx.x + s * kThreads;
-      reg[s] = 0.f;
-      if (o < nout) {
-        const int a = o % c0, cc = o / c0;
-        float acc = 0.f;
-        for (int b = a; b < c0; ++b) acc += Ts[a + b * kMLD] * Gs[b + (c0 + cc) * kMLD];
-        reg[s] = -acc;
+      for (int y = 0; y < 4; ++y) {
+        const int a = lane + 32 * x, cc = warp + 8 * y;
+        if (a < c0 && cc < w) Gs[a + (c0 + cc) * kMLD] = acc[x][y];
       }
+    __syncthreads();
+    // T(0:c0, blk) = -T(0:c0, 0:c0) X: T(a, c0+cc) = -sum_{a <= b < c0} T(a, b) X(b, cc)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+    for (int b = 0; b < c0; ++b) {
+      float t[4], xv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) t[x] = (x < nx) ? Ts[(lane + 32 * x) + b * kMLD] : 0.f;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int cc = warp + 8 * y;
+        xv[y] = (cc < w) ? Gs[b + (c0 + cc) * kMLD] : 0.f;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += t[x] * xv[y];
     }
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const int o = threadIdx.x + s * kThreads;
-      if (o < nout) Ts[(o % c0) + (c0 + o / c0) * kMLD] = reg[s];
-    }
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int a = lane + 32 * x, cc = warp + 8 * y;
+        if (a < c0 && cc < w) Ts[a + (c0 + cc) * kMLD] = -acc[x][y];
+      }
     __syncthreads();
   }
 }
