@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tiled-QR TFLOP/s, mixed vs plain FP64 at equal LS error; % of tensor peak"
 FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 rate (the FP64 arm runs on the FP64 ALUs)
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+BATCH_COUNT = 2048
 BF16_FALLBACK = (1900.0, 1700.0)
 
 
@@ -53,6 +56,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-m", type=int, default=8192)
     ap.add_argument("--sample-n", type=int, default=1024)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched measurement (2048 FP32 matrices, one launch)")
+    ap.add_argument("--batch-prec", default="fp32")
+    ap.add_argument("--batch-table", default="", help="JSON tuning table (autotune output) for the batch")
+    ap.add_argument("--batch-reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -63,6 +71,14 @@ def peaks():
         return float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
     except (OSError, KeyError, ValueError):
         return BF16_FALLBACK[0], BF16_FALLBACK[1], "fallback"
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 # ---------------------------------------------------------------------------------
@@ -194,6 +210,95 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------
+# Batched factorization: 2048 FP32 matrices, rows U[256, 8192], columns {32..256}
+# ---------------------------------------------------------------------------------
+
+def batched_measurement(args, hbm_gbs):
+    """One graph-replayed persistent launch over the whole batch vs the same plan
+    without a graph vs one tqr_factor launch per matrix (device time, inputs restored
+    untimed before each launch; the 4.2 GB batch is larger than L2)."""
+    import numpy as np
+    import torch
+
+    import paper_1303_3182_gb300 as tqr
+    import synthetic
+    from paper_1303_3182_gb300.autotune import DeviceBatch, size_classes, time_launch
+
+    prec = args.batch_prec
+    shapes = synthetic.ragged_batch_shapes(BATCH_COUNT, seed=synthetic.SEED_BASE + 4)
+    ms, ns = [m for m, _ in shapes], [n for _, n in shapes]
+    table = None
+    if args.batch_table:
+        with open(args.batch_table) as fh:
+            table = json.load(fh)["table"]
+    params = tqr.batch_params(ms, ns, prec, table)
+    db = DeviceBatch(shapes, synthetic.SEED_BASE + 4,
+                     dtype=torch.float64 if prec == "fp64" else torch.float32)
+    plan = tqr.BatchPlan(db.As, prec, params=params)
+    info = plan.info()
+    graph_ms = time_launch(plan, db.restore, reps=args.batch_reps, use_graph=True)
+    plain_ms = time_launch(plan, db.restore, reps=max(2, args.batch_reps // 2), use_graph=False)
+    # one launch per matrix (the same tuning, the same T buffers)
+    off = tqr.batch_workspace_offsets(ms, ns, prec, params)
+    Ts = [plan.T[int(off[b]):int(off[b + 1])] for b in range(len(shapes))]
+    stream = torch.cuda.current_stream()
+
+    def per_matrix():
+        for b, A in enumerate(db.As):
+            nb, ib, tree, bs = (int(x) for x in params[b])
+            tqr.factor(A, nb, ib, tree, bs, prec, T=Ts[b], stream=stream)
+
+    old = tqr.set_sync(False)
+    db.restore()
+    per_matrix()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    db.restore()
+    e0.record(stream)
+    per_matrix()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tqr.set_sync(old)
+    tqr.lib().tqr_sync_status(None)
+    per_ms = e0.elapsed_time(e1)
+    flops = info["flops"]
+    esz = 8 if prec == "fp64" else 4
+    t_bytes = int(sum(tqr.workspace_size(m, n, int(p[0]), int(p[1]), prec) for (m, n), p in zip(shapes, params)))
+    a_bytes = 2 * esz * sum(m * n for m, n in shapes)
+    byts = a_bytes + t_bytes
+    peak = FP32_ALU_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
+    classes = []
+    for (lo, hi, n), idx in sorted(size_classes(shapes).items()):
+        f_c = sum(tqr.nominal_flops(ms[b], n) for b in idx)
+        b_c = sum(2 * esz * ms[b] * n + tqr.workspace_size(ms[b], n, int(params[b][0]), int(params[b][1]), prec)
+                  for b in idx)
+        ai = f_c / b_c
+        classes.append({"m": [lo, min(hi, max(ms))], "n": n, "matrices": len(idx), "flops": f_c,
+                        "ai_flop_per_byte": ai, "bound_tflops": min(peak, ai * hbm_gbs / 1e3),
+                        "nb": int(params[idx[0]][0]), "ib": int(params[idx[0]][1]),
+                        "tree": int(params[idx[0]][2])})
+    t_bound = max(flops / (peak * 1e12), byts / (hbm_gbs * 1e9)) * 1e3
+    achieved = flops / (graph_ms * 1e-3) / 1e12
+    plan.close()
+    del db
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"batched QR of {BATCH_COUNT} {prec.upper()} matrices, rows uniform in [256, 8192], "
+                    "columns uniform in {32, 64, 128, 256}, N(0,1), seed 1303318204",
+        "metric": "nominal TFLOP/s of one batched launch", "value": achieved, "unit": "TFLOP/s",
+        "ms_graph_launch": graph_ms, "ms_plain_launch": plain_ms, "ms_one_launch_per_matrix": per_ms,
+        "speedup_vs_per_matrix": per_ms / graph_ms, "tasks": info["tasks"], "edges": info["edges"],
+        "resident_ctas": info["slots"], "tuning": "table " + args.batch_table if table else "built-in size classes",
+        "roofline": {"bound": "alu" if flops / (peak * 1e12) > byts / (hbm_gbs * 1e9) else "hbm",
+                     "peak_tflops": peak, "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+                     if prec == "fp32" else "FP64 nominal", "hbm_gbs": hbm_gbs,
+                     "algorithmic_bytes": byts, "flops": flops, "bound_ms": t_bound,
+                     "frac": t_bound / graph_ms, "classes": classes},
+        "l2": "inputs larger than L2 (%.2f GB), restored before every launch" % (a_bytes / 2 / 1e9),
+    }
+
+
+# ---------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------
 
@@ -312,6 +417,10 @@ def main_gpu(args):
             trees[tr] = {"factor_ms": fms, "tflops": tqr.nominal_flops(m, n) / (fms * 1e-3) / 1e12, "cp_units": cp}
         tqr.set_timing(False)
 
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = batched_measurement(args, hbm_peak())
+
     # ---- end to end: host buffers, copies inside the timed region ----
     A_host = A.t().contiguous().cpu().pin_memory()   # (n, m) row-major == A column-major
     b_host = b.t().contiguous().cpu().pin_memory()
@@ -367,6 +476,7 @@ def main_gpu(args):
         "speedup_vs_fp64": fp64_ms / step_ms,
         "also": also,
         "fp64_trees": trees,
+        "batched": batched,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "clocks": clk.summary(),
     }

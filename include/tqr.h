@@ -91,12 +91,96 @@ int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T
  *         lower part of each tile holds its GEQRT reflectors and the upper triangle of
  *         each zeroed tile holds its TTQRT reflectors.
  *   T   : device, tqr_workspace_size() bytes, written.
- *   nb  : tile size, 1..256 for TQR_FP64, a multiple of 32 up to 128 for the tensor-
- *         core precisions; ib: inner block, 1 <= ib <= nb.
+ *   nb  : tile size, 1..256 for TQR_FP64 and TQR_FP32, exactly 128 for the tensor-core
+ *         precisions; ib: inner block, 1 <= ib <= min(nb, 32).
  * Errors: -1..-4 sizes, -5 tree, -6 bs, -7 prec, -8 A NULL, -9 lda < m, -10 T NULL;
  *         TQR_ETIMEOUT, TQR_ECUDA, TQR_ENOMEM, TQR_EUNSUPPORTED. */
 int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
                void *A, int64_t lda, void *T, void *stream);
+
+/* ---- Batched factorization ------------------------------------------------------
+ * Many independent matrices factored by ONE persistent executor launch: the task
+ * graphs of all matrices (each the graph of tqr_factor for its own nb, ib and tree)
+ * are concatenated into one task table.  The thesis factors one matrix at a time
+ * (Chapter 3); batching is this library's own extension of the same task model.
+ * Tuning: each matrix takes (nb, ib, tree, bs) from "params" (4 ints per matrix). */
+
+/* Per-matrix tuning from a size-class table.
+ *   table : nrows rows of 8 int64 {m_lo, m_hi, n_lo, n_hi, nb, ib, tree, bs}; matrix b
+ *           takes the first row with m_lo <= m[b] <= m_hi and n_lo <= n[b] <= n_hi.
+ *           Matrices that no row covers (or table NULL) take the library's built-in
+ *           size-class rule for "prec".
+ *   params: out, 4 * nbatch ints {nb, ib, tree, bs}.
+ * Host only.  Errors: -1 nbatch < 1, -2 a size < 1, -3 a table row that
+ * tqr_factor would reject, -4 params NULL, -7 prec. */
+int tqr_batch_params(int nbatch, const int64_t *m, const int64_t *n, int prec,
+                     const int64_t *table, int nrows, int *params);
+
+/* Offsets of the matrices' T workspaces in one buffer: T of matrix b occupies bytes
+ * [offsets[b], offsets[b] + tqr_workspace_size(m[b], n[b], nb_b, ib_b, prec)) and
+ * offsets[nbatch] is the total; every offset is a multiple of 256.  Host only. */
+int tqr_batch_workspace_size(int nbatch, const int64_t *m, const int64_t *n, int prec,
+                             const int *params, size_t *offsets);
+
+/* An uploaded batched task graph bound to fixed device buffers (opaque). */
+typedef struct tqr_batch_plan tqr_batch_plan;
+
+/* Builds the concatenated task graph of a batch and uploads it to the current device.
+ *   m, n, lda : host arrays of nbatch sizes (lda[b] >= m[b]).
+ *   A, T      : host arrays of nbatch DEVICE pointers: matrix b (column-major, double
+ *               for TQR_FP64, float otherwise) and its T workspace (tqr_workspace_size
+ *               bytes for its nb/ib).  The plan keeps the pointers; the caller keeps the
+ *               buffers alive while the plan is used and owns them.
+ *   params    : 4 * nbatch ints from tqr_batch_params (NULL: built-in rule).  Tensor-
+ *               core precisions need nb = 128 for every matrix.
+ *   prec      : TQR_FP64, TQR_FP32 or a tensor-core precision.
+ * Task order: every matrix's own order (earliest start, then longest remaining path)
+ * is kept; matrices are started longest-critical-path first, each offset by the work
+ * of the matrices before it divided by the resident CTAs, and the tasks of all
+ * matrices are merged by that offset plus their earliest start.  The merged order is
+ * topological, so the ticket claim of the executor cannot deadlock.
+ * Errors: as tqr_factor, with -1/-2 reporting nbatch and the first bad matrix via
+ * tqr_last_error(); TQR_ENOMEM. */
+int tqr_batch_plan_create(int nbatch, const int64_t *m, const int64_t *n, void *const *A,
+                          const int64_t *lda, const int *params, int prec, void *const *T,
+                          tqr_batch_plan **plan);
+
+/* The merged claim order of a batch for "slots" resident CTAs, without building a plan
+ * (host only; for inspection and tests).  Position r of the order is task local[r] (an
+ * index into matrix mat_of[r]'s own executor order, as tqr_factor would run it).
+ *   params : as for tqr_batch_plan_create (NULL: built-in rule).
+ *   ntask  : in = capacity of mat_of / local; out = number of tasks.  Pass mat_of or
+ *            local NULL to query the count only.
+ * Errors: -1 nbatch / sizes, -4 ntask NULL or capacity too small, tqr_factor's status
+ * for a bad matrix, TQR_ENOMEM. */
+int tqr_batch_order(int nbatch, const int64_t *m, const int64_t *n, int prec, const int *params,
+                    int slots, int32_t *mat_of, int32_t *local, int64_t *ntask);
+
+/* Runs a batch plan on "stream": resets the dependency counters, the ticket and the
+ * status word (device-to-device copy and memset) and launches the executor once.
+ * use_graph != 0 replays a CUDA graph of those three operations, captured on the first
+ * such call on a stream owned by the plan.  With synchronization on (tqr_set_sync),
+ * waits for the stream and returns TQR_ETIMEOUT if a dependency wait ran out. */
+int tqr_batch_plan_run(tqr_batch_plan *plan, int use_graph, void *stream);
+
+/* Waits for "stream" and returns the plan's device status: TQR_OK, or TQR_ETIMEOUT if
+ * a dependency wait of its last run ran out (for runs made with synchronization off). */
+int tqr_batch_plan_status(tqr_batch_plan *plan, void *stream);
+
+/* out[0] tasks, out[1] dependency edges, out[2] matrices, out[3] resident CTAs the
+ * order was planned for, out[4] 1 if a CUDA graph was captured, out[5] nominal flops
+ * (sum of 2 n^2 (m - n/3)).  Host only. */
+int tqr_batch_plan_info(const tqr_batch_plan *plan, int64_t out[6]);
+
+/* Frees a plan's device buffers and graph (the caller's A and T are untouched). */
+void tqr_batch_plan_destroy(tqr_batch_plan *plan);
+
+/* One-shot batched factorization: tqr_batch_plan_create + one tqr_batch_plan_run
+ * without a graph + destroy.  The call always synchronizes the stream (the plan's
+ * buffers are freed before it returns). */
+int tqr_factor_batched(int nbatch, const int64_t *m, const int64_t *n, void *const *A,
+                       const int64_t *lda, const int *params, int prec, void *const *T,
+                       void *stream);
 
 /* Apply Q^T (trans = 0) or Q (trans = 1) of a tqr_factor result to B (m x nrhs,
  * column-major, ldb >= m), in place, replaying the UNMQR/TTMQR kernels on B's tile rows

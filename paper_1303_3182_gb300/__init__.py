@@ -72,6 +72,21 @@ def lib() -> ctypes.CDLL:
             "tqr_launch_count": (i64, [i32]),
             "tqr_trace_fetch": (i64, [c_i64p, i64]),
             "tqr_kernel_time": (i32, [i32, ctypes.POINTER(ctypes.c_double), c_i64p, i32]),
+            "tqr_batch_params": (i32, [i32, c_i64p, c_i64p, i32, c_i64p, i32,
+                                       ctypes.POINTER(ctypes.c_int)]),
+            "tqr_batch_workspace_size": (i32, [i32, c_i64p, c_i64p, i32, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+            "tqr_batch_plan_create": (i32, [i32, c_i64p, c_i64p, ctypes.POINTER(vp), c_i64p,
+                                            ctypes.POINTER(ctypes.c_int), i32, ctypes.POINTER(vp),
+                                            ctypes.POINTER(vp)]),
+            "tqr_batch_order": (i32, [i32, c_i64p, c_i64p, i32, ctypes.POINTER(ctypes.c_int), i32,
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), c_i64p]),
+            "tqr_batch_plan_run": (i32, [vp, i32, vp]),
+            "tqr_batch_plan_status": (i32, [vp, vp]),
+            "tqr_batch_plan_info": (i32, [vp, c_i64p]),
+            "tqr_batch_plan_destroy": (None, [vp]),
+            "tqr_factor_batched": (i32, [i32, c_i64p, c_i64p, ctypes.POINTER(vp), c_i64p,
+                                         ctypes.POINTER(ctypes.c_int), i32, ctypes.POINTER(vp), vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -157,6 +172,11 @@ def nominal_flops(m: int, n: int) -> float:
 
 def set_wait_limit_ns(ns: int) -> int:
     return lib().tqr_set_wait_limit_ns(ns)
+
+
+def set_sync(on: bool) -> bool:
+    """Synchronize and check the device status inside every call (default on)."""
+    return bool(lib().tqr_set_sync(1 if on else 0))
 
 
 def set_timing(on: bool) -> bool:
@@ -289,3 +309,148 @@ def lstsq(A, B, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64", tol: 
                                         ctypes.byref(iters), ctypes.c_void_p(workspace.data_ptr()),
                                         workspace.numel(), _stream(stream)))
     return (X, iters.value) if return_iters else X
+
+
+# ---------------------------------------------------------------------------------
+# Batched factorization (many independent matrices, one persistent launch)
+# ---------------------------------------------------------------------------------
+
+def _i64(a):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def batch_params(ms, ns, prec="fp32", table=None):
+    """(nbatch, 4) int32 array of per-matrix (nb, ib, tree, bs): the first row of
+    ``table`` (rows m_lo, m_hi, n_lo, n_hi, nb, ib, tree, bs) covering each matrix, else
+    the library's built-in size classes."""
+    m, mp = _i64(ms)
+    n, np_ = _i64(ns)
+    out = np.zeros((len(m), 4), dtype=np.int32)
+    if table is not None and len(table):
+        t, tp = _i64(np.asarray(table, dtype=np.int64).reshape(-1, 8))
+        nrows = t.shape[0]
+    else:
+        t, tp, nrows = None, None, 0
+    _check("tqr_batch_params", lib().tqr_batch_params(len(m), mp, np_, _prec(prec), tp, nrows,
+                                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    return out
+
+
+def batch_workspace_offsets(ms, ns, prec="fp32", params=None):
+    """Byte offsets (nbatch + 1) of the per-matrix T workspaces in one buffer."""
+    m, mp = _i64(ms)
+    n, np_ = _i64(ns)
+    off = np.zeros(len(m) + 1, dtype=np.uint64)
+    pp = None
+    if params is not None:
+        params = np.ascontiguousarray(np.asarray(params, dtype=np.int32))
+        pp = params.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    _check("tqr_batch_workspace_size",
+           lib().tqr_batch_workspace_size(len(m), mp, np_, _prec(prec), pp,
+                                          off.ctypes.data_as(ctypes.POINTER(ctypes.c_size_t))))
+    return off.astype(np.int64)
+
+
+def batch_order(ms, ns, prec="fp32", params=None, slots: int = 152):
+    """Merged claim order of a batch (host only): arrays (matrix, local task index)."""
+    m, mp = _i64(ms)
+    n, np_ = _i64(ns)
+    pp = None
+    if params is not None:
+        params = np.ascontiguousarray(np.asarray(params, dtype=np.int32))
+        pp = params.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    cnt = ctypes.c_int64(0)
+    L = lib()
+    _check("tqr_batch_order", L.tqr_batch_order(len(m), mp, np_, _prec(prec), pp, slots, None, None,
+                                                ctypes.byref(cnt)))
+    mat = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    loc = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    _check("tqr_batch_order", L.tqr_batch_order(len(m), mp, np_, _prec(prec), pp, slots,
+                                                mat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                loc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                ctypes.byref(cnt)))
+    return mat[:cnt.value], loc[:cnt.value]
+
+
+class BatchPlan:
+    """tqr_batch_plan: the merged task graph of a batch, bound to its A and T buffers.
+    ``As`` is a list of column-major CUDA tensors; ``T`` one uint8 CUDA buffer carved at
+    ``batch_workspace_offsets``.  Keep both alive while the plan is used."""
+
+    def __init__(self, As, prec="fp32", params=None, T=None):
+        import torch
+        self.prec = _prec(prec)
+        dt = _dtype_of(prec)
+        ms = [int(a.shape[0]) for a in As]
+        ns = [int(a.shape[1]) for a in As]
+        for a in As:
+            if a.dtype != dt or not a.is_cuda:
+                raise ValueError("every matrix must be a CUDA tensor of the precision's storage type")
+        self.params = batch_params(ms, ns, prec) if params is None else \
+            np.ascontiguousarray(np.asarray(params, dtype=np.int32).reshape(-1, 4))
+        off = batch_workspace_offsets(ms, ns, prec, self.params)
+        if T is None:
+            T = torch.empty(int(off[-1]), dtype=torch.uint8, device=As[0].device)
+        self.T, self.As = T, list(As)
+        base = T.data_ptr()
+        self._m, mp = _i64(ms)
+        self._n, np_ = _i64(ns)
+        self._lda, lp = _i64([_ld(a, r) for a, r in zip(As, ms)])
+        VP = ctypes.c_void_p * len(As)
+        self._A = VP(*[a.data_ptr() for a in As])
+        self._T = VP(*[base + int(o) for o in off[:-1]])
+        h = ctypes.c_void_p(0)
+        _check("tqr_batch_plan_create",
+               lib().tqr_batch_plan_create(len(As), mp, np_, self._A, lp,
+                                           self.params.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                           self.prec, self._T, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, use_graph: bool = False, stream=None):
+        _check("tqr_batch_plan_run", lib().tqr_batch_plan_run(self._h, 1 if use_graph else 0, _stream(stream)))
+
+    def status(self, stream=None):
+        """Wait for the stream; raise if the last run's device status is an error."""
+        _check("tqr_batch_plan_status", lib().tqr_batch_plan_status(self._h, _stream(stream)))
+
+    def info(self):
+        out = (ctypes.c_int64 * 6)()
+        _check("tqr_batch_plan_info", lib().tqr_batch_plan_info(self._h, out))
+        return {"tasks": out[0], "edges": out[1], "matrices": out[2], "slots": out[3],
+                "graph": bool(out[4]), "flops": float(out[5])}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tqr_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def factor_batched(As, prec="fp32", params=None, T=None, stream=None):
+    """One-shot batched factorization (tqr_factor_batched) of a list of column-major CUDA
+    tensors in place.  Returns (T buffer, byte offsets, params)."""
+    import torch
+    ms = [int(a.shape[0]) for a in As]
+    ns = [int(a.shape[1]) for a in As]
+    params = batch_params(ms, ns, prec) if params is None else \
+        np.ascontiguousarray(np.asarray(params, dtype=np.int32).reshape(-1, 4))
+    off = batch_workspace_offsets(ms, ns, prec, params)
+    if T is None:
+        T = torch.empty(int(off[-1]), dtype=torch.uint8, device=As[0].device)
+    m, mp = _i64(ms)
+    n, np_ = _i64(ns)
+    lda, lp = _i64([_ld(a, r) for a, r in zip(As, ms)])
+    VP = ctypes.c_void_p * len(As)
+    Ap = VP(*[a.data_ptr() for a in As])
+    Tp = VP(*[T.data_ptr() + int(o) for o in off[:-1]])
+    _check("tqr_factor_batched",
+           lib().tqr_factor_batched(len(As), mp, np_, Ap, lp,
+                                    params.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _prec(prec),
+                                    Tp, _stream(stream)))
+    return T, off, params

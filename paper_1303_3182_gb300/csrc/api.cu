@@ -216,6 +216,10 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
   return TQR_OK;
 }
 
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
 bool is_tensor_prec(int prec) {
   return prec == TQR_BF16 || prec == TQR_FP16 || prec == TQR_BF16X3 || prec == TQR_BF16X6;
 }
@@ -238,9 +242,18 @@ int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec
   return 0;
 }
 
-}  // namespace
+size_t ops_offset(int64_t m, int64_t n, int nb, int ib) {
+  const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
+  return align_up(static_cast<size_t>(2 * P * K) * ib * nb * sizeof(float), 1024);
+}
 
-void set_error(const std::string &msg) { g_last_error = msg; }
+size_t factor_workspace_bytes(int64_t m, int64_t n, int nb, int ib, int prec) {
+  const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
+  const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
+  if (!is_tensor_prec(prec)) return static_cast<size_t>(2 * P * K) * ib * nb * esz;
+  return ops_offset(m, n, nb, ib) + static_cast<size_t>(2 * P * K) * mixed_slot_bytes(tensor_parts(prec));
+}
+
 
 namespace {
 std::atomic<int64_t> g_launch_count{0};
@@ -292,11 +305,7 @@ int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T
   const int rc = check_tiles(m, n, nb, ib, TQR_GREEDY, 1, prec);
   if (rc) return rc;
   if (!T_bytes) return -6;
-  const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
-  const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
-  *T_bytes = static_cast<size_t>(2 * P * K) * ib * nb * esz;
-  if (is_tensor_prec(prec))
-    *T_bytes = align_up(*T_bytes, 1024) + static_cast<size_t>(2 * P * K) * mixed_slot_bytes(tensor_parts(prec));
+  *T_bytes = factor_workspace_bytes(m, n, nb, ib, prec);
   return TQR_OK;
 }
 
@@ -328,9 +337,8 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
     prm.T = T;
     prm.B = nullptr;
     if (is_tensor_prec(prec)) {
-      const int64_t K = std::min(P, Q);
       prm.mixed = 1;
-      prm.ops = static_cast<char *>(T) + align_up(static_cast<size_t>(2 * P * K) * ib * nb * sizeof(float), 1024);
+      prm.ops = static_cast<char *>(T) + ops_offset(m, n, nb, ib);
       prm.nparts = tensor_parts(prec);
       prm.vec4 = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0) ? 1 : 0;
       prm.fmt = prec == TQR_FP16 ? 0 : 1;

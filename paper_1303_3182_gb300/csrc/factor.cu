@@ -481,7 +481,6 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
   Real *tile = tile_ptr(A, p.lda, nb, i, k);
   Real *Tg = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 0);
   const int mb = geo.rows(i), ncol = geo.cols(k), K = min(mb, ncol);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c0 = 0; c0 < nb; c0 += ib) {
     const int width = min(ib, nb - c0);
     const int kb = max(0, min(ib, K - c0));
@@ -676,7 +675,7 @@ __device__ bool wait_ready(const ExecParams &p, int t) {
     if (ld_acquire_gpu(cnt) <= 0) return true;
     if (ld_relaxed_gpu(p.status) != 0) return false;
     if (globaltimer_ns() - t0 > limit || it > (limit >> 4) + 1000000ull) {
-      atomicCAS(p.status, 0, kStatusTimeout | (t << 8));
+      atomicCAS(p.status, 0, kStatusTimeout | (min(t, (1 << 23) - 1) << 8));
       return false;
     }
     __nanosleep(64);
@@ -690,10 +689,11 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ uint64_t s_ph[5];
-  Smem<S> s = carve<S>(smem_raw, p.nb, p.ib);
-  s.ph = p.trace ? s_ph : nullptr;
+  __shared__ ExecParams s_q;  // the current task's parameters in a batched launch
+  Smem<S> s0 = carve<S>(smem_raw, p.nb, p.ib);
+  s0.ph = p.trace ? s_ph : nullptr;
   MixedState ms{};
-  ms.ph = s.ph;
+  ms.ph = s0.ph;
   if (kMixed) {
     if (threadIdx.x == 0) {
       umma::mbar_init(&s_bar[0], 1);
@@ -710,6 +710,9 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     ms.ld_phase = 0;
     ms.mma_phase = 0;
   }
+  // task functions read the parameters from shared memory; the claim barrier below
+  // publishes this copy (and each batched task's geometry) to the block
+  if (threadIdx.x == 0) s_q = p;
   for (;;) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(p.next, 1);
@@ -726,6 +729,21 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
         s_ph[0] = now;
         s_ph[1] = s_ph[2] = s_ph[3] = s_ph[4] = 0;
       }
+      // a batched launch carries each task's matrix in a descriptor
+      if (!stop && p.mats) {
+        const BatchMat *d = p.mats + p.mat_of[t];
+        s_q.A = d->A;
+        s_q.lda = d->lda;
+        s_q.m = d->m;
+        s_q.n = d->n;
+        s_q.nb = d->nb;
+        s_q.ib = d->ib;
+        s_q.P = d->P;
+        s_q.Q = d->Q;
+        s_q.T = d->T;
+        s_q.ops = d->ops;
+        s_q.vec4 = d->vec4;
+      }
       s_task = t;
       s_stop = stop;
     }
@@ -733,56 +751,62 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     if (s_stop) break;
     const int t = s_task;
     const Task task = p.tasks[t];
-    const int nb = p.nb;
+    const ExecParams &q = s_q;
+    const int nb = q.nb;
+    Smem<S> s = s0;
+    if (p.mats) {
+      s = carve<S>(smem_raw, nb, q.ib);
+      s.ph = s0.ph;
+    }
     switch (task.kind) {
       case kGeqrt:
-        task_geqrt<Real, S>(p, s, task.i, task.k);
+        task_geqrt<Real, S>(q, s, task.i, task.k);
         if (kMixed) {
           __syncthreads();
           phase_mark(s.ph, 2);
-          prep_geqrt_ops(p, smem_raw, task.i, task.k);
+          prep_geqrt_ops(q, smem_raw, task.i, task.k);
           phase_mark(s.ph, 3);
         }
         break;
       case kTtqrt:
-        task_ttqrt<Real, S>(p, s, task.i, task.piv, task.k);
+        task_ttqrt<Real, S>(q, s, task.i, task.piv, task.k);
         if (kMixed) {
           __syncthreads();
           phase_mark(s.ph, 2);
-          prep_ttqrt_ops(p, smem_raw, task.i, task.k);
+          prep_ttqrt_ops(q, smem_raw, task.i, task.k);
           phase_mark(s.ph, 3);
         }
         break;
       case kUnmqr: {
         if (kMixed) {
-          task_unmqr_umma(p, smem_raw, ms, task.i, task.k, task.j);
+          task_unmqr_umma(q, smem_raw, ms, task.i, task.k, task.j);
           break;
         }
-        Real *A = static_cast<Real *>(p.A);
-        const int ncols = static_cast<int>(lmin(nb, p.n - int64_t(task.j) * nb));
-        task_unmqr<Real, S, Real>(p, s, task.i, task.k, tile_ptr(A, p.lda, nb, task.i, task.j), p.lda,
+        Real *A = static_cast<Real *>(q.A);
+        const int ncols = static_cast<int>(lmin(nb, q.n - int64_t(task.j) * nb));
+        task_unmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.i, task.j), q.lda,
                                   ncols, false);
         break;
       }
       case kTtmqr: {
         if (kMixed) {
-          task_ttmqr_umma(p, smem_raw, ms, task.i, task.piv, task.k, task.j);
+          task_ttmqr_umma(q, smem_raw, ms, task.i, task.piv, task.k, task.j);
           break;
         }
-        Real *A = static_cast<Real *>(p.A);
-        const int ncols = static_cast<int>(lmin(nb, p.n - int64_t(task.j) * nb));
-        task_ttmqr<Real, S, Real>(p, s, task.i, task.k, tile_ptr(A, p.lda, nb, task.piv, task.j),
-                                  tile_ptr(A, p.lda, nb, task.i, task.j), p.lda, ncols, false);
+        Real *A = static_cast<Real *>(q.A);
+        const int ncols = static_cast<int>(lmin(nb, q.n - int64_t(task.j) * nb));
+        task_ttmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.piv, task.j),
+                                  tile_ptr(A, q.lda, nb, task.i, task.j), q.lda, ncols, false);
         break;
       }
       case kUnmqrB:
-        task_unmqr<Real, S, double>(p, s, task.i, task.k, p.B + static_cast<int64_t>(task.i) * nb, p.ldb,
-                                    static_cast<int>(p.nrhs), p.trans != 0);
+        task_unmqr<Real, S, double>(q, s, task.i, task.k, q.B + static_cast<int64_t>(task.i) * nb, q.ldb,
+                                    static_cast<int>(q.nrhs), q.trans != 0);
         break;
       case kTtmqrB:
-        task_ttmqr<Real, S, double>(p, s, task.i, task.k, p.B + static_cast<int64_t>(task.piv) * nb,
-                                    p.B + static_cast<int64_t>(task.i) * nb, p.ldb,
-                                    static_cast<int>(p.nrhs), p.trans != 0);
+        task_ttmqr<Real, S, double>(q, s, task.i, task.k, q.B + static_cast<int64_t>(task.piv) * nb,
+                                    q.B + static_cast<int64_t>(task.i) * nb, q.ldb,
+                                    static_cast<int>(q.nrhs), q.trans != 0);
         break;
       default:
         break;
@@ -836,6 +860,26 @@ size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q) {
 size_t mixed_slot_bytes(int nparts) { return slot_bytes(nparts); }
 
 size_t mixed_executor_smem_bytes() { return mixed_smem_bytes(); }
+
+template <typename Real, typename S, bool kMixed>
+int slots_typed(size_t smem) {
+  auto kern = executor_kernel<Real, S, kMixed>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+      cudaSuccess)
+    return 0;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess) return 0;
+  return nsm * (per_sm < 1 ? 1 : per_sm);
+}
+
+int executor_slots(bool real_is_double, bool mixed, int nb, int ib) {
+  if (mixed && !real_is_double) return slots_typed<float, float, true>(mixed_smem_bytes());
+  const size_t smem = executor_smem_bytes(nb, ib, real_is_double, false);
+  if (real_is_double) return slots_typed<double, double, false>(smem);
+  return slots_typed<float, float, false>(smem);
+}
 
 int launch_executor(const ExecParams &p, bool real_is_double, void *stream) {
   const bool apply_q = p.B != nullptr;

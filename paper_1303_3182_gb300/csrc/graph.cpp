@@ -102,6 +102,8 @@ void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge) {
 
   g.tasks.resize(n);
   g.weight.resize(n);
+  g.start.resize(n);
+  g.bottom.resize(n);
   g.indeg.assign(n, 0);
   g.succ_ptr.assign(n + 1, 0);
   g.succ_idx.clear();
@@ -111,6 +113,8 @@ void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge) {
     const int t = order[r];
     g.tasks[r] = b.tasks[t];
     g.weight[r] = b.weight[t];
+    g.start[r] = b.finish[t] - b.weight[t];
+    g.bottom[r] = bottom[t];
     g.indeg[r] = static_cast<int32_t>(b.preds[t].size());
     g.critical_path = std::max<int64_t>(g.critical_path, b.finish[t]);
     const int kind = b.tasks[t].kind;

@@ -47,6 +47,19 @@ struct Graph {
   std::vector<int32_t> weight;       // kernel weight per task
   int64_t critical_path = 0;         // longest weighted path (unbounded processors)
   int64_t counts[4] = {0, 0, 0, 0};  // GEQRT, TTQRT, UNMQR, TTMQR
+  std::vector<int64_t> start;        // earliest start (unbounded processors), executor order
+  std::vector<int64_t> bottom;       // longest weighted path to a sink, task included
+};
+
+// One matrix of a batched factorization, as the executor reads it.
+struct BatchMat {
+  void *A;
+  int64_t lda, m, n;
+  int nb, ib, P, Q;
+  void *T;
+  void *ops;
+  int vec4;
+  int pad;
 };
 
 // Incremental construction of a task graph in sequential-program order.  Regions are
@@ -118,6 +131,9 @@ struct ExecParams {
   int mixed;             // 1: GEQRT/TTQRT prepare images, UNMQR/TTMQR run on tcgen05
   int vec4;              // A is 16-byte aligned with lda % 4 == 0 (vector loads allowed)
   int64_t *trace;        // optional: per task {claim, start, end, sm} globaltimer stamps
+  // batched factorization: per-task matrix index and per-matrix geometry (else null)
+  const int32_t *mat_of;
+  const BatchMat *mats;
 };
 
 // Launches the persistent tile-task executor on "stream".  real_is_double selects the
@@ -125,6 +141,18 @@ struct ExecParams {
 int launch_executor(const ExecParams &p, bool real_is_double, void *stream);
 // Dynamic shared memory the executor needs (0 if nb/ib do not fit on one SM).
 size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q);
+// Resident factorization CTAs on the current device (SMs x CTAs per SM), 0 on error.
+int executor_slots(bool real_is_double, bool mixed, int nb, int ib);
+
+// Argument checks and workspace layout shared by the single and batched entry points.
+bool is_tensor_prec(int prec);
+int tensor_parts(int prec);  // 16-bit parts per operand of a tensor-core precision
+size_t align_up(size_t x, size_t a);
+// 0 or the negative status of tqr_factor for bad sizes / tree / prec
+int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec);
+// byte offset of the operand images in T (tensor-core precisions)
+size_t ops_offset(int64_t m, int64_t n, int nb, int ib);
+size_t factor_workspace_bytes(int64_t m, int64_t n, int nb, int ib, int prec);
 // Tile size, bytes per factored tile of operand images, and shared memory of the
 // tensor-core (mixed) executor.
 constexpr int kMixedNB = 128;
