@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--batch-prec", default="fp32")
     ap.add_argument("--batch-table", default="", help="JSON tuning table (autotune output) for the batch")
     ap.add_argument("--batch-reps", type=int, default=5)
+    ap.add_argument("--c5", action="store_true",
+                    help="also measure the square 16384^2 solve (cond 1e4, 64 right-hand sides), ~1 min")
+    ap.add_argument("--c5-precs", default="bf16x3,bf16x6")
     return ap.parse_args()
 
 
@@ -213,26 +216,29 @@ class ClockSampler:
 # Batched factorization: 2048 FP32 matrices, rows U[256, 8192], columns {32..256}
 # ---------------------------------------------------------------------------------
 
-def batched_measurement(args, hbm_gbs):
+def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
     """One graph-replayed persistent launch over the whole batch vs the same plan
     without a graph vs one tqr_factor launch per matrix (device time, inputs restored
-    untimed before each launch; the 4.2 GB batch is larger than L2)."""
+    untimed before each launch; the 4.2 GB batch is larger than L2).  With several
+    ranks each takes every world-th matrix and the times are maxima over ranks."""
     import numpy as np
     import torch
 
     import paper_1303_3182_gb300 as tqr
     import synthetic
+    from paper_1303_3182_gb300 import replicas
     from paper_1303_3182_gb300.autotune import DeviceBatch, size_classes, time_launch
 
     prec = args.batch_prec
-    shapes = synthetic.ragged_batch_shapes(BATCH_COUNT, seed=synthetic.SEED_BASE + 4)
+    all_shapes = synthetic.ragged_batch_shapes(BATCH_COUNT, seed=synthetic.SEED_BASE + 4)
+    shapes = [all_shapes[b] for b in replicas.shard(len(all_shapes), rank, world)]
     ms, ns = [m for m, _ in shapes], [n for _, n in shapes]
     table = None
     if args.batch_table:
         with open(args.batch_table) as fh:
             table = json.load(fh)["table"]
     params = tqr.batch_params(ms, ns, prec, table)
-    db = DeviceBatch(shapes, synthetic.SEED_BASE + 4,
+    db = DeviceBatch(shapes, replicas.replica_seed(synthetic.SEED_BASE + 4, rank),
                      dtype=torch.float64 if prec == "fp64" else torch.float32)
     plan = tqr.BatchPlan(db.As, prec, params=params)
     info = plan.info()
@@ -261,23 +267,26 @@ def batched_measurement(args, hbm_gbs):
     tqr.set_sync(old)
     tqr.lib().tqr_sync_status(None)
     per_ms = e0.elapsed_time(e1)
-    flops = info["flops"]
+    graph_ms, plain_ms, per_ms = replicas.max_over_ranks([graph_ms, plain_ms, per_ms], device)
+    flops = sum(tqr.nominal_flops(m, n) for m, n in all_shapes)
     esz = 8 if prec == "fp64" else 4
-    t_bytes = int(sum(tqr.workspace_size(m, n, int(p[0]), int(p[1]), prec) for (m, n), p in zip(shapes, params)))
-    a_bytes = 2 * esz * sum(m * n for m, n in shapes)
+    all_params = tqr.batch_params([m for m, _ in all_shapes], [n for _, n in all_shapes], prec, table)
+    t_bytes = int(sum(tqr.workspace_size(m, n, int(p[0]), int(p[1]), prec) for (m, n), p in zip(all_shapes, all_params)))
+    a_bytes = 2 * esz * sum(m * n for m, n in all_shapes)
     byts = a_bytes + t_bytes
     peak = FP32_ALU_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
     classes = []
-    for (lo, hi, n), idx in sorted(size_classes(shapes).items()):
-        f_c = sum(tqr.nominal_flops(ms[b], n) for b in idx)
-        b_c = sum(2 * esz * ms[b] * n + tqr.workspace_size(ms[b], n, int(params[b][0]), int(params[b][1]), prec)
-                  for b in idx)
+    all_ms = [m for m, _ in all_shapes]
+    for (lo, hi, n), idx in sorted(size_classes(all_shapes).items()):
+        f_c = sum(tqr.nominal_flops(all_ms[b], n) for b in idx)
+        b_c = sum(2 * esz * all_ms[b] * n + tqr.workspace_size(all_ms[b], n, int(all_params[b][0]),
+                                                               int(all_params[b][1]), prec) for b in idx)
         ai = f_c / b_c
-        classes.append({"m": [lo, min(hi, max(ms))], "n": n, "matrices": len(idx), "flops": f_c,
-                        "ai_flop_per_byte": ai, "bound_tflops": min(peak, ai * hbm_gbs / 1e3),
-                        "nb": int(params[idx[0]][0]), "ib": int(params[idx[0]][1]),
-                        "tree": int(params[idx[0]][2])})
-    t_bound = max(flops / (peak * 1e12), byts / (hbm_gbs * 1e9)) * 1e3
+        classes.append({"m": [lo, min(hi, max(all_ms))], "n": n, "matrices": len(idx), "flops": f_c,
+                        "ai_flop_per_byte": ai, "bound_tflops": min(peak * world, ai * hbm_gbs * world / 1e3),
+                        "nb": int(all_params[idx[0]][0]), "ib": int(all_params[idx[0]][1]),
+                        "tree": int(all_params[idx[0]][2])})
+    t_bound = max(flops / (peak * 1e12 * world), byts / (hbm_gbs * 1e9 * world)) * 1e3
     achieved = flops / (graph_ms * 1e-3) / 1e12
     plan.close()
     del db
@@ -289,13 +298,75 @@ def batched_measurement(args, hbm_gbs):
         "ms_graph_launch": graph_ms, "ms_plain_launch": plain_ms, "ms_one_launch_per_matrix": per_ms,
         "speedup_vs_per_matrix": per_ms / graph_ms, "tasks": info["tasks"], "edges": info["edges"],
         "resident_ctas": info["slots"], "tuning": "table " + args.batch_table if table else "built-in size classes",
-        "roofline": {"bound": "alu" if flops / (peak * 1e12) > byts / (hbm_gbs * 1e9) else "hbm",
+        "ranks": world, "scaling": "strong (the 2048 matrices split across ranks)",
+        "roofline": {"bound": "alu" if flops / peak > byts / (hbm_gbs * 1e-3) else "hbm",
                      "peak_tflops": peak, "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
                      if prec == "fp32" else "FP64 nominal", "hbm_gbs": hbm_gbs,
                      "algorithmic_bytes": byts, "flops": flops, "bound_ms": t_bound,
                      "frac": t_bound / graph_ms, "classes": classes},
         "l2": "inputs larger than L2 (%.2f GB), restored before every launch" % (a_bytes / 2 / 1e9),
     }
+
+
+# ---------------------------------------------------------------------------------
+# Square solve: A = U diag(sigma) V^T 16384 x 16384, cond 1e4, 64 right-hand sides N(0,1)
+# ---------------------------------------------------------------------------------
+
+def c5_measurement(args, n=16384, nrhs=64, cond=1e4):
+    """FP64 tiled QR solve (nb 256) vs tensor-core factorization (nb 128) + FP64
+    refinement, both through tqr_lstsq; equal-error criterion for a square system: the
+    normwise backward error ||b - A x|| / (||A||_F ||x|| + ||b||) of every right-hand
+    side, worst case, must not exceed the FP64 solve's by more than 2x."""
+    import torch
+
+    import paper_1303_3182_gb300 as tqr
+    import synthetic
+
+    dev = torch.device("cuda")
+    A = synthetic.conditioned_device(n, n, cond, synthetic.SEED_BASE + 5, dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(synthetic.SEED_BASE + 5 + 7919)
+    B = tqr.colmajor(torch.randn(n, nrhs, dtype=torch.float64, device=dev, generator=g))
+    anorm = float(torch.linalg.norm(A))
+    bnorm = torch.linalg.norm(B, dim=0)
+    flops = tqr.nominal_flops(n, n)
+    stream = torch.cuda.current_stream()
+
+    def backward_error(X):
+        R = B - A @ X
+        return float((torch.linalg.norm(R, dim=0) / (anorm * torch.linalg.norm(X, dim=0) + bnorm)).max())
+
+    def timed(prec, nb, tol, reps):
+        ws = torch.empty(tqr.lstsq_workspace_size(n, n, nrhs, nb, 32, prec), dtype=torch.uint8, device=dev)
+        X = tqr.colmajor(torch.empty((n, nrhs), dtype=torch.float64, device=dev))
+        it = tqr.lstsq(A, B, nb, 32, "greedy", 4, prec, tol=tol, max_iter=1000, X=X, workspace=ws, stream=stream,
+                       return_iters=True)[1]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            tqr.lstsq(A, B, nb, 32, "greedy", 4, prec, tol=tol, max_iter=1000, X=X, workspace=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        err = backward_error(X)
+        del ws
+        torch.cuda.empty_cache()
+        return {"prec": prec, "nb": nb, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12, "backward_error": err,
+                "refinement_iterations": it}
+
+    out = {"workload": f"square solve {n}x{n}, cond {cond:g}, {nrhs} right-hand sides N(0,1), seed 1303318205; "
+                       "Greedy, ib 32; FP64 nb 256 vs tensor-core nb 128 + FP64 refinement",
+           "nominal_flops": flops}
+    fp64 = timed("fp64", 256, 1e-14, 1)
+    out["fp64"] = fp64
+    out["mixed"] = []
+    for prec in [p for p in args.c5_precs.split(",") if p]:
+        r = timed(prec, 128, 1e-14, 2)
+        r["speedup_vs_fp64"] = fp64["ms"] / r["ms"]
+        r["equal_error"] = r["backward_error"] <= 2 * fp64["backward_error"]
+        out["mixed"].append(r)
+    return out
 
 
 # ---------------------------------------------------------------------------------
@@ -309,21 +380,19 @@ def main_gpu(args):
     import paper_1303_3182_gb300 as tqr
     import synthetic
     from paper_1303_3182_gb300 import build as _build
+    from paper_1303_3182_gb300 import replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, local, world = replicas.env_ranks()
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    replicas.init("nccl", torch.device("cuda", local))
     _build.build()
     tqr.lib()
     dev = torch.device("cuda", local)
     m, n = args.m, args.n
     stream = torch.cuda.current_stream()
     # independent replicas: each rank solves its own seeded problem
-    A, xtrue, b = synthetic.least_squares_device(m, n, args.cond, 1e-3, 1, synthetic.SEED_BASE + 3 + 1000 * rank,
-                                                 dev)
+    A, xtrue, b = synthetic.least_squares_device(m, n, args.cond, 1e-3, 1,
+                                                 replicas.replica_seed(synthetic.SEED_BASE + 3, rank), dev)
     anorm = float(torch.linalg.norm(A))
 
     def optimality(X):
@@ -362,8 +431,7 @@ def main_gpu(args):
     for kind in ("factor", "apply_q", "trsm", "refine"):
         tqr.kernel_time(kind, reset=True)
     tqr.launch_count(reset=True)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters = []
@@ -373,8 +441,7 @@ def main_gpu(args):
             iters.append(step())
         e1.record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     ms_total = e0.elapsed_time(e1)
     launches = tqr.launch_count(reset=True)
     kt = {k: tqr.kernel_time(k, reset=True) for k in ("factor", "apply_q", "trsm", "refine")}
@@ -418,8 +485,9 @@ def main_gpu(args):
         tqr.set_timing(False)
 
     batched = None
-    if world == 1 and not args.no_batched:
-        batched = batched_measurement(args, hbm_peak())
+    if not args.no_batched:
+        batched = batched_measurement(args, hbm_peak(), rank, world, dev)
+    c5 = c5_measurement(args) if (args.c5 and world == 1) else None
 
     # ---- end to end: host buffers, copies inside the timed region ----
     A_host = A.t().contiguous().cpu().pin_memory()   # (n, m) row-major == A column-major
@@ -445,11 +513,7 @@ def main_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
 
-    step_ms = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, e2e_ms = float(t[0]), float(t[1])
+    step_ms, e2e_ms = replicas.max_over_ranks([ms_total / args.steps, e2e_ms], dev)
     flops = tqr.nominal_flops(m, n)
     value = flops * world / (step_ms * 1e-3) / 1e12
     fac_ms, fac_n = kt["factor"]
@@ -477,6 +541,7 @@ def main_gpu(args):
         "also": also,
         "fp64_trees": trees,
         "batched": batched,
+        "c5": c5,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "clocks": clk.summary(),
     }
@@ -484,8 +549,7 @@ def main_gpu(args):
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finalize()
 
 
 def main():

@@ -220,11 +220,16 @@ int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, double *B, 
  *   prec == TQR_FP64 : X = R^{-1} (Q^T B)(0:n) from an FP64 tiled QR.
  *   otherwise        : the tiled QR runs in "prec" on a float copy of A; X is then
  *                      computed by FP64 iterative refinement from X = 0: each step
- *                      forms r = B - A X and A^T r in FP64, stops when
- *                      ||A^T r|| / (||A||_F ||r||) <= tol or when a step no longer
- *                      halves that quantity (the FP64-attainable level), else solves
- *                      for the correction with LSQR (Paige & Saunders, 1982) in FP64,
- *                      right-preconditioned with the low-precision R.
+ *                      forms r = B - A X and A^T r in FP64; a right-hand side is done
+ *                      when ||A^T r|| / (||A||_F ||r||) <= tol (least-squares optimal)
+ *                      or ||r|| / (||A||_F ||x|| + ||b||) <= tol (backward error of a
+ *                      consistent system, e.g. square A); the refinement also stops
+ *                      when a step no longer halves the worst optimality (the
+ *                      FP64-attainable level).  Otherwise it solves for the correction
+ *                      with LSQR (Paige & Saunders, 1982) in FP64, right-preconditioned
+ *                      with the low-precision R, using LSQR's two stopping rules (the
+ *                      normal-equation estimate, and the residual estimate against the
+ *                      backward-error threshold).
  *   A, B    : device, not modified.  X : device n x nrhs, ldx >= n.
  *   iters   : out (may be NULL), refinement iterations used (max over right-hand sides).
  *   workspace / ws_bytes : device scratch of at least tqr_lstsq_workspace_size() bytes.

@@ -77,10 +77,8 @@ __device__ __forceinline__ S warp_sum(S v) {
 // Shared-memory layout of one CTA (element type S = compute type).
 template <typename S>
 struct Smem {
-  double *tau;   // [ib] tau of the current block, FP64
-  double *scal;  // [ib] 1 / (alpha - beta) of each reflector of the block
-  S *tau_s;      // [ib] tau in the compute type (read by every warp)
-  S *scal_s;     // [ib] scal in the compute type
+  S *tau_s;      // [ib] tau of each reflector of the current block
+  S *scal_s;     // [ib] 1 / (alpha - beta) of each reflector of the block
   S *V;          // [ldv * ib]  panel / reflector block
   S *C;          // [ldv * kCW] update chunk (C, or C2 of a TT pair)
   S *C1;         // [ldv * kCW] C1 chunk of a TT pair
@@ -96,9 +94,8 @@ __host__ __device__ inline int odd_ld(int x) { return x | 1; }
 
 __host__ __device__ inline size_t smem_elems(int nb, int ib, size_t s_size) {
   const size_t ldv = odd_ld(nb), ldw = ib + 1, ldt = ib + 1;
-  const size_t d_bytes = 2 * static_cast<size_t>(ib) * sizeof(double);
   const size_t s_elems = ldv * ib + 2 * ldv * kCW + ldw * kCW + 3 * ldt * ib + 2 * ib;
-  return d_bytes + s_elems * s_size;
+  return s_elems * s_size;
 }
 
 template <typename S>
@@ -107,9 +104,7 @@ __device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
   s.ldv = odd_ld(nb);
   s.ldw = ib + 1;
   s.ldt = ib + 1;
-  s.tau = reinterpret_cast<double *>(raw);
-  s.scal = s.tau + ib;
-  S *p = reinterpret_cast<S *>(s.scal + ib);
+  S *p = reinterpret_cast<S *>(raw);
   s.V = p;
   p += s.ldv * ib;
   s.C = p;
@@ -290,13 +285,40 @@ __device__ __forceinline__ DFloat df_sq_acc(DFloat acc, float x) {
   return r;
 }
 
-__device__ __forceinline__ double df_warp_sum(DFloat v) {
+__device__ __forceinline__ DFloat df_warp_reduce(DFloat v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     DFloat w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
     v = df_add(v, w);
   }
-  return static_cast<double>(v.hi) + static_cast<double>(v.lo);
+  return v;
+}
+
+// FP32 reflector parameters (LAPACK convention, as reflector() above) from alpha and a
+// double-float ||x||^2: alpha^2 is split exactly and added in double-float, so that
+// s = alpha^2 + ||x||^2 carries one FP32 rounding; beta = -sign(alpha) sqrt(s),
+// alpha - beta has no cancellation, tau = (beta - alpha) / beta, scal = 1 / (alpha - beta).
+// Each scalar is within a few FP32 ulps, the precision they are stored in.  Returns false
+// (nothing written) when s is outside the range where FP32 keeps full precision.
+__device__ __forceinline__ bool reflector_f32(float alpha, DFloat xx, float *beta, float *tau, float *scal) {
+  if (xx.hi == 0.f && xx.lo == 0.f) {
+    *beta = alpha;
+    *tau = 0.f;
+    *scal = 0.f;
+    return true;
+  }
+  const float a2 = alpha * alpha;
+  DFloat sd = df_add(xx, a2);
+  sd.lo += fmaf(alpha, alpha, -a2);
+  const float sv = sd.hi + sd.lo;
+  if (!(sv > 1e-30f && sv < 1e30f)) return false;
+  const float nrm = sqrtf(sv);
+  const float b = alpha >= 0.f ? -nrm : nrm;
+  const float amb = alpha - b;
+  *beta = b;
+  *scal = 1.0f / amb;
+  *tau = -amb / b;
+  return true;
 }
 
 // Householder factorization of one panel block (kb columns) held in shared memory.
@@ -304,11 +326,13 @@ __device__ __forceinline__ double df_warp_sum(DFloat v) {
 //   TT:    head = P1(c, c) (row c of R(piv)), tail = V(0 .. min(c0+c+1, mb)-1, c)
 // Reflector c updates every later column cc of the block:
 //   w = head(c, cc) + v . tail(cc);  head(c, cc) -= tau w;  tail(cc) -= tau v w,
-// with v = tail(c) * scal.  Warp 0 updates column c+1 first and at once forms the next
-// reflector (FP64 norm and tau) from it; warps 1.. update the remaining columns; column
-// c's tail is scaled in place one step later, when no warp reads it any more.  One
-// block-wide barrier per reflector.  On return the tails hold v, the heads beta, and
-// s.tau the taus.
+// with v = tail(c) * scal.  Warp 0 updates column c+1 first and, in the same pass over
+// its rows, accumulates the sum of squares of the next reflector's tail (FP64-accurate),
+// then forms that reflector; warps 1.. update the remaining columns, four at a time;
+// column c's tail is scaled in place one step later, when no warp reads it any more.
+// One block-wide barrier per reflector.  On return the tails hold v, the heads beta,
+// and s.tau_s / s.scal_s the taus and 1 / (alpha - beta).  FP32 storage takes its
+// scalars in FP32 from the FP64-accurate sum of squares (reflector_f32).
 template <typename S, bool kTT>
 __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -316,90 +340,162 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
   auto tlo = [&](int c) { return kTT ? 0 : c + 1; };
   auto thi = [&](int c) { return kTT ? min(c0 + c + 1, mb) : rows; };
   auto col = [&](int c) -> S * { return s.V + c * s.ldv; };
-  // the reflector of column c, by one warp, from its current values
-  auto make_reflector = [&](int c) {
-    const S *x = col(c);
-    double xx;
-    if (sizeof(S) == sizeof(float)) {
-      DFloat acc{0.f, 0.f};
-      for (int r = tlo(c) + lane; r < thi(c); r += 32) acc = df_sq_acc(acc, static_cast<float>(x[r]));
-      xx = df_warp_sum(acc);
+  constexpr bool kF32 = sizeof(S) == sizeof(float);
+  // Sum of squares accumulated per lane: double-float for FP32 storage (FP64-accurate
+  // with FP32 instructions), plain FP64 otherwise.
+  struct Acc {
+    DFloat d;
+    double x;
+  };
+  auto acc_add = [&](Acc &a, S v) {
+    if (kF32)
+      a.d = df_sq_acc(a.d, static_cast<float>(v));
+    else
+      a.x = fma(static_cast<double>(v), static_cast<double>(v), a.x);
+  };
+  // Lane 0 turns column c's reduced sum of squares into its reflector: beta over the
+  // head, tau and 1 / (alpha - beta) into shared memory.
+  auto set_reflector = [&](int c, Acc a) {
+    if (kF32) {
+      a.d = df_warp_reduce(a.d);
     } else {
-      xx = 0.0;
-      for (int r = tlo(c) + lane; r < thi(c); r += 32) {
-        const double v = static_cast<double>(x[r]);
-        xx = fma(v, v, xx);
-      }
-      xx = warp_sum(xx);
+      a.x = warp_sum(a.x);
     }
     if (lane == 0) {
-      double beta, tau, scal;
-      // FP32 storage keeps ~2^-24 of these scalars: one Newton step (2^-46) suffices
-      if (sizeof(S) == sizeof(float))
-        reflector<1>(static_cast<double>(head(c, c)), xx, &beta, &tau, &scal);
-      else
-        reflector<2>(static_cast<double>(head(c, c)), xx, &beta, &tau, &scal);
-      head(c, c) = static_cast<S>(beta);
-      s.tau[c] = tau;
-      s.scal[c] = scal;
-      s.tau_s[c] = static_cast<S>(tau);
-      s.scal_s[c] = static_cast<S>(scal);
+      if (kF32) {
+        float beta, tau, scal;
+        if (!reflector_f32(static_cast<float>(head(c, c)), a.d, &beta, &tau, &scal)) {
+          double bd, td, sd;  // outside FP32's comfortable range: FP64 scalars
+          reflector<1>(static_cast<double>(head(c, c)), static_cast<double>(a.d.hi) + a.d.lo, &bd, &td, &sd);
+          beta = static_cast<float>(bd);
+          tau = static_cast<float>(td);
+          scal = static_cast<float>(sd);
+        }
+        head(c, c) = static_cast<S>(beta);
+        s.tau_s[c] = static_cast<S>(tau);
+        s.scal_s[c] = static_cast<S>(scal);
+      } else {
+        double beta, tau, scal;
+        reflector<2>(static_cast<double>(head(c, c)), a.x, &beta, &tau, &scal);
+        head(c, c) = static_cast<S>(beta);
+        s.tau_s[c] = static_cast<S>(tau);
+        s.scal_s[c] = static_cast<S>(scal);
+      }
     }
   };
-  auto update = [&](int c, int cc, S t, S sc) {
+  auto fresh_reflector = [&](int c) {
+    Acc a{{0.f, 0.f}, 0.0};
     const S *x = col(c);
-    S *y = col(cc);
+    for (int r = tlo(c) + lane; r < thi(c); r += 32) acc_add(a, x[r]);
+    set_reflector(c, a);
+  };
+  // Warp 0, look-ahead: reflector c applied to column c+1, whose updated values feed
+  // the sum of squares of reflector c+1 in the same pass.
+  auto update_and_reflect = [&](int c, S t, S sc) {
+    const int cn = c + 1;
+    const S *x = col(c);
+    S *y = col(cn);
+    const int lo = tlo(c), hi = thi(c), nlo = tlo(cn), nhi = thi(cn);
+    S tw = 0;
+    if (t != S(0)) {
+      S part = 0;
+      for (int r = lo + lane; r < hi; r += 32) part += (x[r] * sc) * y[r];
+      const S w = head(c, cn) + warp_sum(part);
+      tw = t * w;
+      if (lane == 0) head(c, cn) -= tw;
+    }
+    Acc a{{0.f, 0.f}, 0.0};
+    const int rlo = min(lo, nlo), rhi = max(hi, nhi);
+    for (int r = rlo + lane; r < rhi; r += 32) {
+      S v = y[r];
+      if (r >= lo && r < hi && t != S(0)) {
+        v -= (x[r] * sc) * tw;
+        y[r] = v;
+      }
+      if (r >= nlo && r < nhi) acc_add(a, v);
+    }
+    __syncwarp();  // alpha of column c+1 (GEQRT: row c+1, updated above) for lane 0
+    set_reflector(cn, a);
+  };
+  // Warps 1..: reflector c applied to up to kG columns cc0, cc0 + step, ... at once, so
+  // that their dot products and butterfly reductions overlap.
+  constexpr int kG = 4;
+  auto update_group = [&](int c, int cc0, int step, int count, S t, S sc) {
+    const S *x = col(c);
     const int lo = tlo(c), hi = thi(c);
-    S part = 0;
-    for (int r = lo + lane; r < hi; r += 32) part += (x[r] * sc) * y[r];
-    const S w = head(c, cc) + warp_sum(part);
-    if (lane == 0) head(c, cc) -= t * w;
-    const S tw = t * w;
-    for (int r = lo + lane; r < hi; r += 32) y[r] -= (x[r] * sc) * tw;
+    S part[kG];
+#pragma unroll
+    for (int u = 0; u < kG; ++u) part[u] = 0;
+    for (int r = lo + lane; r < hi; r += 32) {
+      const S xv = x[r] * sc;
+#pragma unroll
+      for (int u = 0; u < kG; ++u)
+        if (u < count) part[u] += xv * col(cc0 + u * step)[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < kG; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+    S tw[kG];
+#pragma unroll
+    for (int u = 0; u < kG; ++u) tw[u] = u < count ? t * (head(c, cc0 + u * step) + part[u]) : S(0);
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kG; ++u)
+        if (u < count) head(c, cc0 + u * step) -= tw[u];
+    }
+    for (int r = lo + lane; r < hi; r += 32) {
+      const S xv = x[r] * sc;
+#pragma unroll
+      for (int u = 0; u < kG; ++u)
+        if (u < count) col(cc0 + u * step)[r] -= xv * tw[u];
+    }
   };
   auto scale_tail = [&](int c) {
     const S sc = s.scal_s[c];
     S *x = col(c);
     for (int r = tlo(c) + lane; r < thi(c); r += 32) x[r] = x[r] * sc;
   };
-  if (warp == 0) make_reflector(0);
+  if (warp == 0) fresh_reflector(0);
   __syncthreads();
   for (int c = 0; c < kb; ++c) {
-    // only lane 0 of warp 0 touches FP64: the other warps share its FP64 pipe
     const S t = s.tau_s[c];
     const S sc = s.scal_s[c];
     if (warp == 0) {
-      if (c + 1 < kb) {
-        if (t != S(0)) update(c, c + 1, t, sc);
-        __syncwarp();
-        make_reflector(c + 1);
+      if (c + 1 < kb) update_and_reflect(c, t, sc);
+    } else if (t != S(0)) {
+      constexpr int kStep = kWarps - 1;
+      for (int cc0 = c + 1 + warp; cc0 < kb; cc0 += kG * kStep) {
+        const int count = min(kG, (kb - 1 - cc0) / kStep + 1);
+        update_group(c, cc0, kStep, count, t, sc);
       }
-    } else {
-      if (t != S(0))
-        for (int cc = c + 1 + warp; cc < kb; cc += kWarps - 1) update(c, cc, t, sc);
-      if (warp == kWarps - 1 && c >= 1) scale_tail(c - 1);
     }
+    if (warp == kWarps - 1 && c >= 1) scale_tail(c - 1);
     __syncthreads();
   }
   if (warp == kWarps - 1) scale_tail(kb - 1);
   __syncthreads();
 }
 
-// Gram matrix G(a, c) = v_a . v_c (all a, c < kb) of a panel block's reflectors, with the
-// explicit vectors (GEQRT: unit diagonal, zeros above; TT: the stored tails, zeros below).
-template <typename S, bool kTT>
+// Gram matrix G(a, c) = v_a . v_c (all a, c < kb) of a panel block's reflectors, held
+// explicitly in s.V (GEQRT: unit diagonal and zeros above written in; TT: zeros below
+// the triangle from the load).  Lane a and warp g form G(a, g + 8u), u < 4; column
+// indices beyond kb are clamped (their results are not stored) so the row loop has no
+// branches and unrolls.
+template <typename S>
 __device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
   const int a = threadIdx.x & 31, cg = threadIdx.x >> 5;
-  auto vexp = [&](int r, int c) -> S {
-    if (c >= kb) return S(0);
-    if (kTT) return s.V[r + c * s.ldv];
-    return r > c ? s.V[r + c * s.ldv] : (r == c ? S(1) : S(0));
-  };
-  S acc[4] = {0, 0, 0, 0};
-  for (int r = 0; r < nrows; ++r) {
-    const S va = vexp(r, a);
+  const S *va = s.V + min(a, kb - 1) * s.ldv;
+  const S *vc[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] += va * vexp(r, cg + kWarps * u);
+  for (int u = 0; u < 4; ++u) vc[u] = s.V + min(cg + kWarps * u, kb - 1) * s.ldv;
+  S acc[4] = {0, 0, 0, 0};
+#pragma unroll 4
+  for (int r = 0; r < nrows; ++r) {
+    const S x = va[r];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += x * vc[u][r];
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -409,26 +505,35 @@ __device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
   __syncthreads();
 }
 
-// Builds T (kb x kb, upper) from the Gram matrix G and tau (Schreiber-Van Loan):
-// T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c).  Columns of T not yet formed
-// are zero, so each step is one fixed-length dot product per lane.
+// Builds T (kb x kb, upper) from the Gram matrix G and tau.  The compact-WY recurrence
+// (Schreiber-Van Loan) T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c) makes
+// T the inverse of the upper-triangular S with S(c,c) = 1/tau_c and S(a,c) = G(a,c)
+// above the diagonal (the inverse of [S1 g; 0 1/tau] has last column
+// [-tau S1^{-1} g; tau]).  Lane j forms column j of T by back substitution without a
+// division: x_j = tau_j, x_a = -tau_a sum_{a<k<=j} G(a,k) x_k, accumulating the sums
+// right to left so that each step is independent FMAs.  tau_c = 0 (an identity
+// reflector) gives a zero row and column, as the recurrence does.
 template <typename S>
 __device__ void build_t(Smem<S> &s, int kb) {
   if (threadIdx.x < 32) {
-    const int a = threadIdx.x;
-    for (int b = 0; b < kb; ++b)
-      if (a < kb) s.T[a + b * s.ldt] = 0;
-    __syncwarp();
-    for (int c = 0; c < kb; ++c) {
-      const S tc = s.tau_s[c];
-      S acc = 0;
+    const int j = threadIdx.x;
+    if (j < kb) {
+      S acc[32];
 #pragma unroll
-      for (int b = 0; b < 32; ++b)
-        if (b < c) acc += s.T[a + b * s.ldt] * s.G[b + c * s.ldt];
-      const S val = a < c ? -tc * acc : (a == c ? tc : S(0));
-      __syncwarp();
-      if (a < kb) s.T[a + c * s.ldt] = val;
-      __syncwarp();
+      for (int a = 0; a < 32; ++a) acc[a] = 0;
+#pragma unroll
+      for (int k = 31; k >= 0; --k) {
+        if (k < kb) {
+          S xk = 0;
+          if (k == j)
+            xk = s.tau_s[j];
+          else if (k < j)
+            xk = -s.tau_s[k] * acc[k];
+          s.T[k + j * s.ldt] = xk;  // zero below the diagonal (k > j)
+#pragma unroll
+          for (int a = 0; a < k; ++a) acc[a] += s.G[a + k * s.ldt] * xk;
+        }
+      }
     }
   }
   __syncthreads();
@@ -494,18 +599,19 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
     __syncthreads();
     panel_factor<S, false>(s, kb, rows, c0, mb);
     phase_mark(s.ph, 0);
-    panel_gram<S, false>(s, kb, rows);
-    build_t(s, kb);
     store_block(blk, p.lda, s.V, s.ldv, rows, kb);
-    store_t(Tg, ib, c0, width, s, kb);
     __syncthreads();
-    phase_mark(s.ph, 1);
     // explicit reflector block: unit diagonal, zeros above
     for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
       const int c = idx / kb, r = idx - c * kb;
       if (r <= c) s.V[r + c * s.ldv] = (r == c) ? S(1) : S(0);
     }
     __syncthreads();
+    panel_gram(s, kb, rows);
+    build_t(s, kb);
+    store_t(Tg, ib, c0, width, s, kb);
+    __syncthreads();
+    phase_mark(s.ph, 1);
     for (int cs = c0 + kb; cs < ncol; cs += kCW) {
       const int w = min(kCW, ncol - cs);
       Real *cblk = tile + c0 + static_cast<int64_t>(cs) * p.lda;
@@ -556,7 +662,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
     __syncthreads();
     panel_factor<S, true>(s, kb, rb, c0, mb);
     phase_mark(s.ph, 0);
-    panel_gram<S, true>(s, kb, rb);
+    panel_gram(s, kb, rb);
     build_t(s, kb);
     // write back the upper parts only (the lower parts hold GEQRT reflectors)
     for (int c = warp; c < kb; c += kWarps)

@@ -374,26 +374,38 @@ __device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int nc
 
 // Split image of C^T (row c, k = r) in shared memory, one 16-byte chunk (8 rows of one
 // column) per thread step; the rows come as two float4 loads when the tile is 16-byte
-// aligned (vec4), else one by one.
+// aligned (vec4), else one by one.  Each thread issues the loads of four chunks before
+// converting any, so that enough bytes are in flight to hide the memory latency.
 __device__ void c_transposed_image(unsigned char *img, const float *C, int64_t ldc, int mb, int ncols, int fmt,
                                    int nparts, bool vec4) {
-  for (int ch = threadIdx.x; ch < kMNB * kMNB / 8; ch += kThreads) {
-    const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
-    const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
-    float x[8];
-    const float *colp = C + static_cast<int64_t>(row) * ldc + k0;
-    if (row < ncols && vec4 && k0 + 8 <= mb) {
-      const float4 a = __ldcg(reinterpret_cast<const float4 *>(colp));
-      const float4 b = __ldcg(reinterpret_cast<const float4 *>(colp + 4));
-      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-      x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-    } else {
+  constexpr int kU = 4;
+  constexpr int kSteps = kMNB * kMNB / 8 / kThreads;  // 8 chunks per thread
+  static_assert(kSteps % kU == 0, "chunk groups");
+  for (int g = 0; g < kSteps; g += kU) {
+    float x[kU][8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[j] = (row < ncols && k0 + j < mb) ? __ldcg(colp + j) : 0.f;
+    for (int u = 0; u < kU; ++u) {
+      const int ch = threadIdx.x + (g + u) * kThreads;
+      const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
+      const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
+      const float *colp = C + static_cast<int64_t>(row) * ldc + k0;
+      if (row < ncols && vec4 && k0 + 8 <= mb) {
+        const float4 a = __ldcg(reinterpret_cast<const float4 *>(colp));
+        const float4 b = __ldcg(reinterpret_cast<const float4 *>(colp + 4));
+        x[u][0] = a.x; x[u][1] = a.y; x[u][2] = a.z; x[u][3] = a.w;
+        x[u][4] = b.x; x[u][5] = b.y; x[u][6] = b.z; x[u][7] = b.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[u][j] = (row < ncols && k0 + j < mb) ? __ldcg(colp + j) : 0.f;
+      }
     }
-    uint4 parts[3];
-    split8(x, parts, nparts, fmt);
-    for (int q = 0; q < nparts; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int ch = threadIdx.x + (g + u) * kThreads;
+      uint4 parts[3];
+      split8(x[u], parts, nparts, fmt);
+      for (int q = 0; q < nparts; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
+    }
   }
 }
 
@@ -475,8 +487,8 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   }
   float *C = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
   tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 128);
+  c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
   umma::fence_proxy_async();
   sync_all_tc();
   phase_mark(ms.ph, 0);
@@ -532,9 +544,9 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   float *C1 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, piv, j);
   float *C2 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
   tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 128);
   tile_rows_to_tmem(C1, p.lda, kMNB, ncols, ms.tmem, 256);
+  c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
   // D1 (lane c, column a) = C1(a, c): the identity part of the TT reflectors
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

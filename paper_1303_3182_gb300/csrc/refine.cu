@@ -259,7 +259,8 @@ size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
   // LSQR state sets, and the inverses of R's 64 x 64 diagonal blocks
   const size_t nblk = static_cast<size_t>((n + 63) / 64);
   return static_cast<size_t>(nrhs) * (m + 5 * n) + 5 * static_cast<size_t>(nrhs) + 2 +
-         2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8 + nblk * 64 * 64;
+         2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8 + nblk * 64 * 64 +
+         2 * static_cast<size_t>(nrhs);
 }
 
 int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream) {
@@ -286,6 +287,8 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   double *eta2 = anorm2 + 1;                            // [nrhs] ||A^T u||^2, u = r / ||r||
   LsqrScalars *sc = reinterpret_cast<LsqrScalars *>(eta2 + nrhs + ((nrhs + 1) & 1));  // [2][nrhs]
   double *Dinv = reinterpret_cast<double *>(sc + 2 * nrhs) + 4;                 // [nblk][64][64]
+  double *bn2 = Dinv + static_cast<size_t>((n + 63) / 64) * 64 * 64;               // [nrhs] ||b||^2
+  double *xn2 = bn2 + nrhs;                                                       // [nrhs] ||x||^2
   const int64_t chunk = 512;
   const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
   const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
@@ -310,8 +313,12 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   auto solve_r = [&](double *Vec, bool lower_t) -> int {
     return launch_trsv_blocked(n, R, ldr, false, Dinv, Vec, n, nrhs, flags, status, wait_limit_ns, stream, lower_t);
   };
-  std::vector<double> host_eta(nrhs + 1);
+  std::vector<double> host_eta(nrhs + 1), host_rn2(nrhs), host_xn2(nrhs), host_bn2(nrhs), thr(nrhs);
   std::vector<LsqrScalars> host(nrhs);
+  TQR_CK(cudaMemsetAsync(bn2, 0, sizeof(double) * nrhs, st));
+  colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, B, ldb, bn2, nrhs);
+  TQR_CKL();
+  TQR_CK(cudaMemcpyAsync(host_bn2.data(), bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   int total_it = 0;
   bool converged = false;
   double prev_eta = 1e300;
@@ -336,13 +343,33 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
     TQR_CKL();
     axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, eta2, nrhs);
     TQR_CKL();
+    // ||x|| of the current solution for the backward error of a consistent system
+    TQR_CK(cudaMemsetAsync(xn2, 0, sizeof(double) * nrhs, st));
+    colnorm<<<vgrid(n, nrhs), kT, 0, st>>>(n, X, ldx, xn2, nrhs);
+    TQR_CKL();
     TQR_CK(cudaMemcpyAsync(host_eta.data(), anorm2, sizeof(double) * (nrhs + 1), cudaMemcpyDeviceToHost, st));
+    TQR_CK(cudaMemcpyAsync(host_rn2.data(), ssq_b, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    TQR_CK(cudaMemcpyAsync(host_xn2.data(), xn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
     TQR_CK(cudaStreamSynchronize(st));
-    double worst_eta = 0.0;
-    for (int r = 0; r < nrhs; ++r) worst_eta = fmax(worst_eta, sqrt(host_eta[1 + r] / host_eta[0]));
-    if (debug) std::fprintf(stderr, "[tqr refine] outer %d: optimality %.3e after %d LSQR iterations\n", outer,
-                            worst_eta, total_it);
-    if (!(worst_eta > tol)) {
+    // A right-hand side is done when X is least-squares optimal to tol (||A^T r|| small)
+    // or, for a consistent system, when the normwise backward error
+    // ||r|| / (||A||_F ||x|| + ||b||) is below tol.
+    const double anorm = sqrt(host_eta[0]);
+    double worst_eta = 0.0, worst_omega = 0.0;
+    bool all_done = true;
+    for (int r = 0; r < nrhs; ++r) {
+      const double eta = sqrt(host_eta[1 + r] / host_eta[0]);
+      const double scale = anorm * sqrt(host_xn2[r]) + sqrt(host_bn2[r]);
+      const double omega = scale > 0.0 ? sqrt(host_rn2[r]) / scale : 0.0;
+      worst_eta = fmax(worst_eta, eta);
+      worst_omega = fmax(worst_omega, omega);
+      all_done = all_done && (!(eta > tol) || !(omega > tol));
+      thr[r] = 0.1 * tol * scale;
+    }
+    if (debug)
+      std::fprintf(stderr, "[tqr refine] outer %d: optimality %.3e backward error %.3e after %d LSQR iterations\n",
+                   outer, worst_eta, worst_omega, total_it);
+    if (all_done) {
       converged = true;
       break;
     }
@@ -382,9 +409,13 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
       TQR_CKL();
       TQR_CK(cudaMemcpyAsync(host.data(), nxt, sizeof(LsqrScalars) * nrhs, cudaMemcpyDeviceToHost, st));
       TQR_CK(cudaStreamSynchronize(st));
-      double worst = 0.0;
-      for (int r = 0; r < nrhs; ++r) worst = fmax(worst, host[r].conv);
-      if (!(worst > 0.1 * tol)) {
+      // LSQR's two stopping rules per right-hand side: the normal-equation estimate
+      // (inconsistent systems) or the residual estimate phibar against the backward-error
+      // threshold of the outer solution (consistent systems)
+      bool inner_done = true;
+      for (int r = 0; r < nrhs; ++r)
+        inner_done = inner_done && (!(host[r].conv > 0.1 * tol) || !(host[r].phibar > thr[r]));
+      if (inner_done) {
         ++total_it;
         break;
       }

@@ -62,3 +62,27 @@ def test_mixed_lstsq_matches_fp64(prec, m, n, nrhs, cond, noise):
     # LSQR stops on the preconditioned quantity; the plain one then meets the FP64 target
     assert refine.ls_optimality(A, Xg, B) <= max(10 * refine.ls_optimality(A, Xo, B), 1e-13)
     assert iters >= 1
+
+
+@pytest.mark.parametrize("prec,cond,max_iters", [("bf16x6", 1e4, 16), ("bf16x3", 1e4, 24), ("fp32", 1e6, 24)])
+def test_consistent_square_system_stops_at_backward_error(prec, cond, max_iters):
+    """A square nonsingular system (every right-hand side consistent): ||A^T r|| / (||A|| ||r||)
+    does not shrink when r is rounding noise, so the refinement must stop on the backward
+    error ||r|| / (||A||_F ||x|| + ||b||) <= tol - after a few LSQR steps, not the cap - with
+    the FP64 solve's backward error or better."""
+    n, nrhs = 640, 3
+    A = synthetic.conditioned(n, n, cond, seed=17)
+    B = np.asfortranarray(np.random.default_rng(18).standard_normal((n, nrhs)))
+    p, q = H.tile_grid(n, n, 128)
+    Xo = H.lstsq(A, B, 128, 32, E.elimination_list(p, q, E.GREEDY))
+    Xg, iters = tqr.lstsq(to_dev(A), to_dev(B), 128, 32, "greedy", 1, prec, tol=1e-14, max_iter=600,
+                          return_iters=True)
+    Xg = Xg.cpu().numpy()
+
+    def omega(X):
+        R = B - A @ X
+        return np.max(np.linalg.norm(R, axis=0) / (np.linalg.norm(A) * np.linalg.norm(X, axis=0) +
+                                                   np.linalg.norm(B, axis=0)))
+
+    assert omega(Xg) <= max(2 * omega(Xo), 1e-14), (omega(Xg), omega(Xo))
+    assert 1 <= iters <= max_iters, iters
