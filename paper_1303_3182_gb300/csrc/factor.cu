@@ -31,7 +31,9 @@ __host__ __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return 
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kCW = 16;  // columns of an update chunk held in shared memory
+// Columns of an update chunk held in shared memory: 32 for FP32 storage, 16 for FP64
+// (whose 256-row chunks would not fit twice in one SM's shared memory at 32).
+__host__ __device__ constexpr int chunk_cols(size_t s_size) { return s_size == sizeof(float) ? 32 : 16; }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
@@ -80,9 +82,9 @@ struct Smem {
   S *tau_s;      // [ib] tau of each reflector of the current block
   S *scal_s;     // [ib] 1 / (alpha - beta) of each reflector of the block
   S *V;          // [ldv * ib]  panel / reflector block
-  S *C;          // [ldv * kCW] update chunk (C, or C2 of a TT pair)
-  S *C1;         // [ldv * kCW] C1 chunk of a TT pair
-  S *W;          // [ldw * kCW]
+  S *C;          // [ldv * chunk] update chunk (C, or C2 of a TT pair)
+  S *C1;         // [ldv * chunk] C1 chunk of a TT pair
+  S *W;          // [ldw * chunk]
   S *T;          // [ldt * ib]
   S *G;          // [ldt * ib]  Gram matrix of the reflectors of a block
   S *P1;         // [ldt * ib]  diagonal block of R(piv) during TTQRT
@@ -94,7 +96,8 @@ __host__ __device__ inline int odd_ld(int x) { return x | 1; }
 
 __host__ __device__ inline size_t smem_elems(int nb, int ib, size_t s_size) {
   const size_t ldv = odd_ld(nb), ldw = ib + 1, ldt = ib + 1;
-  const size_t s_elems = ldv * ib + 2 * ldv * kCW + ldw * kCW + 3 * ldt * ib + 2 * ib;
+  const size_t cw = chunk_cols(s_size);
+  const size_t s_elems = ldv * ib + 2 * ldv * cw + ldw * cw + 3 * ldt * ib + 2 * ib;
   return s_elems * s_size;
 }
 
@@ -108,11 +111,11 @@ __device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
   s.V = p;
   p += s.ldv * ib;
   s.C = p;
-  p += s.ldv * kCW;
+  p += s.ldv * chunk_cols(sizeof(S));
   s.C1 = p;
-  p += s.ldv * kCW;
+  p += s.ldv * chunk_cols(sizeof(S));
   s.W = p;
-  p += s.ldw * kCW;
+  p += s.ldw * chunk_cols(sizeof(S));
   s.T = p;
   p += s.ldt * ib;
   s.G = p;
@@ -199,6 +202,7 @@ __device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols
   }
   __syncthreads();
   // C -= V W
+  constexpr int kCW = chunk_cols(sizeof(S));
   for (int r = tid; r < nrows; r += kThreads) {
     S acc[kCW];
 #pragma unroll
@@ -612,6 +616,7 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
     store_t(Tg, ib, c0, width, s, kb);
     __syncthreads();
     phase_mark(s.ph, 1);
+    constexpr int kCW = chunk_cols(sizeof(S));
     for (int cs = c0 + kb; cs < ncol; cs += kCW) {
       const int w = min(kCW, ncol - cs);
       Real *cblk = tile + c0 + static_cast<int64_t>(cs) * p.lda;
@@ -676,6 +681,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
     __syncthreads();
     phase_mark(s.ph, 1);
     // trailing columns of the same tile column: [R(piv) rows c0..c0+kb-1 ; tile i rows 0..rb-1]
+    constexpr int kCW = chunk_cols(sizeof(S));
     for (int cs = c0 + kb; cs < K; cs += kCW) {
       const int w = min(kCW, K - cs);
       Real *c1 = t1 + c0 + static_cast<int64_t>(cs) * p.lda;
@@ -704,6 +710,7 @@ __device__ void task_unmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *cp
   const Real *Tg = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 0);
   const int mb = geo.rows(i), K = min(mb, geo.cols(k));
   const int nblk = (K + ib - 1) / ib;
+  constexpr int kCW = chunk_cols(sizeof(S));
   for (int cs = 0; cs < ncols; cs += kCW) {
     const int w = min(kCW, ncols - cs);
     CT *cblk = cptr + static_cast<int64_t>(cs) * ldc;
@@ -738,6 +745,7 @@ __device__ void task_ttmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *c1
   const Real *Tt = t_ptr(static_cast<Real *>(p.T), p.P, ib, nb, i, k, 1);
   const int mb = geo.rows(i), K = geo.cols(k);
   const int nblk = (K + ib - 1) / ib;
+  constexpr int kCW = chunk_cols(sizeof(S));
   for (int cs = 0; cs < ncols; cs += kCW) {
     const int w = min(kCW, ncols - cs);
     CT *b1 = c1ptr + static_cast<int64_t>(cs) * ldc;
