@@ -309,6 +309,43 @@ def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
 
 
 # ---------------------------------------------------------------------------------
+# Small case: 512 x 128 FP64, nb 64, ib 16, Greedy - latency / critical-path bound
+# ---------------------------------------------------------------------------------
+
+def c1_measurement(reps=20):
+    """Device time of one FP64 factorization of the 512 x 128 matrix (8 x 2 tiles of 64),
+    against its weighted critical path (34 units of 64^3/3 flops: the work of 34 GEQRT-
+    equivalents in a chain) - this size is bound by the task chain, not by a peak."""
+    import torch
+
+    import paper_1303_3182_gb300 as tqr
+    import synthetic
+
+    m, n, nb, ib = 512, 128, 64, 16
+    A0 = torch.from_numpy(synthetic.gaussian(m, n, synthetic.SEED_BASE + 1).T.copy()).cuda().t()
+    work = torch.empty_like(A0.t()).t()
+    T = torch.empty(tqr.workspace_size(m, n, nb, ib, "fp64"), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    work.copy_(A0)
+    tqr.factor(work, nb, ib, "greedy", 1, "fp64", T=T)
+    ts = []
+    for _ in range(reps):
+        work.copy_(A0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tqr.factor(work, nb, ib, "greedy", 1, "fp64", T=T)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ts.sort()
+    cp = tqr.elimlist(m // nb, n // nb, "greedy", 1)[1]
+    ms = ts[len(ts) // 2]
+    return {"workload": "512x128 FP64 N(0,1), seed 1303318201, nb 64, ib 16, Greedy", "ms_median": ms,
+            "cp_units": cp, "us_per_cp_unit": ms * 1e3 / cp, "tflops": tqr.nominal_flops(m, n) / (ms * 1e-3) / 1e12,
+            "note": "includes the synchronizing status read of the call"}
+
+
+# ---------------------------------------------------------------------------------
 # Square solve: A = U diag(sigma) V^T 16384 x 16384, cond 1e4, 64 right-hand sides N(0,1)
 # ---------------------------------------------------------------------------------
 
@@ -488,6 +525,7 @@ def main_gpu(args):
     if not args.no_batched:
         batched = batched_measurement(args, hbm_peak(), rank, world, dev)
     c5 = c5_measurement(args) if (args.c5 and world == 1) else None
+    c1 = c1_measurement() if world == 1 else None
 
     # ---- end to end: host buffers, copies inside the timed region ----
     A_host = A.t().contiguous().cpu().pin_memory()   # (n, m) row-major == A column-major
@@ -542,6 +580,7 @@ def main_gpu(args):
         "fp64_trees": trees,
         "batched": batched,
         "c5": c5,
+        "c1": c1,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "clocks": clk.summary(),
     }

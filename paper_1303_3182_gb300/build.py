@@ -15,7 +15,7 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-SOURCES = ["api.cu", "batch.cu", "factor.cu", "solve.cu", "refine.cu", "graph.cpp", "elim.cpp"]
+SOURCES = ["api.cu", "batch.cu", "factor.cu", "solve.cu", "precond.cu", "refine.cu", "graph.cpp", "elim.cpp"]
 HEADERS = ["tqr_internal.h", "umma.cuh", "mixed_tasks.cuh"]
 LIB = os.path.join(PKG, "libtqr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

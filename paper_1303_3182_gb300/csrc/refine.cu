@@ -260,7 +260,7 @@ size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
   const size_t nblk = static_cast<size_t>((n + 63) / 64);
   return static_cast<size_t>(nrhs) * (m + 5 * n) + 5 * static_cast<size_t>(nrhs) + 2 +
          2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8 + nblk * 64 * 64 +
-         2 * static_cast<size_t>(nrhs);
+         2 * static_cast<size_t>(nrhs) + precond_work_doubles(n, false);
 }
 
 int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream) {
@@ -289,6 +289,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   double *Dinv = reinterpret_cast<double *>(sc + 2 * nrhs) + 4;                 // [nblk][64][64]
   double *bn2 = Dinv + static_cast<size_t>((n + 63) / 64) * 64 * 64;               // [nrhs] ||b||^2
   double *xn2 = bn2 + nrhs;                                                       // [nrhs] ||x||^2
+  double *Pw = xn2 + nrhs;                                                        // preconditioner solves
   const int64_t chunk = 512;
   const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
   const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
@@ -309,9 +310,10 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   fro_norm2<<<1216, kT, 0, st>>>(m, n, A, lda, anorm2);
   TQR_CKL();
   if ((rc = launch_diag_inverse(n, R, ldr, false, Dinv, stream)) != 0) return rc;
-  // R^{-1} and R^{-T} applied by the blocked solves with the diagonal-block inverses
+  if ((rc = precond_setup(n, R, ldr, false, Dinv, Pw, stream)) != 0) return rc;
+  // R^{-1} and R^{-T} applied with the inverses of R's 512 x 512 diagonal blocks
   auto solve_r = [&](double *Vec, bool lower_t) -> int {
-    return launch_trsv_blocked(n, R, ldr, false, Dinv, Vec, n, nrhs, flags, status, wait_limit_ns, stream, lower_t);
+    return precond_solve(n, R, ldr, false, Pw, Vec, n, nrhs, flags, status, wait_limit_ns, stream, lower_t);
   };
   std::vector<double> host_eta(nrhs + 1), host_rn2(nrhs), host_xn2(nrhs), host_bn2(nrhs), thr(nrhs);
   std::vector<LsqrScalars> host(nrhs);

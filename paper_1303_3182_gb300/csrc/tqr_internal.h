@@ -173,6 +173,17 @@ int launch_trsv_blocked(int64_t n, const void *A, int64_t lda, bool real_is_doub
                         int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
                         void *stream, bool lower_transposed);
 
+// Preconditioner solves of the refinement (precond.cu): FP64 inverses of R's 512 x 512
+// diagonal blocks built once from the 64 x 64 ones (precond_setup), then R X = B or
+// R^T X = B by one cooperative launch per four right-hand sides (precond_solve).
+// work: precond_work_doubles(n, real_is_double) doubles; bar: one int32 of device scratch.
+size_t precond_work_doubles(int64_t n, bool real_is_double);
+int precond_setup(int64_t n, const void *R, int64_t ldr, bool real_is_double, const double *Dinv64, double *work,
+                  void *stream);
+int precond_solve(int64_t n, const void *R, int64_t ldr, bool real_is_double, const double *work, double *B,
+                  int64_t ldb, int64_t nrhs, int32_t *bar, int32_t *status, int64_t wait_limit_ns, void *stream,
+                  bool lower_transposed);
+
 // LSQR refinement (refine.cu): X (in: x0, out: refined) for min ||A X - B||, operator
 // A R^{-1} with the FP32 R of a tensor-core factorization.  work: lsqr_work_doubles()
 // doubles; flags: trsm_flag_count(n) int32; status: device status word.
