@@ -195,13 +195,9 @@ int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, doub
 int trsm_flag_count(int64_t n) { return trsm_flag_count_impl(n); }
 
 // ---------------------------------------------------------------------------------
-// Triangular solves of the refinement: many solves with the same R, one or a few
-// right-hand sides.  The inverses of the 64 x 64 diagonal blocks are formed once (FP64),
-// so each wavefront step is a parallel matrix-vector product instead of a sequential
-// substitution; the off-diagonal block of the next step is fetched before its wait.
+// Inverses of the 64 x 64 diagonal blocks of R (FP64), the starting point of the
+// refinement's preconditioner set-up (precond.cu).
 namespace {
-
-constexpr int kRhsV = 4;  // right-hand sides per pass of the blocked solve
 
 // Dinv[k] = inverse of the k-th 64 x 64 diagonal block of the upper-triangular R.
 template <typename Real>
@@ -243,110 +239,6 @@ __global__ void __launch_bounds__(kThreads) diag_inverse_kernel(int64_t n, const
   }
 }
 
-// out[r][j] = sum_c M[r][c] x[c][j], r < 64, j < nr, c < 64, four threads per (r, j)
-// when nr == 1 (partial sums combined with shuffles); M is smem [64][65].
-__device__ __forceinline__ void small_matvec(double (*M)[kTB + 1], double (*X)[kRhsV],
-                                             double (*out)[kRhsV], int nr, bool subtract) {
-  const int tid = threadIdx.x;
-  const int nout = kTB * nr;                        // <= 256
-  const int split = nout <= 64 ? 4 : (nout <= 128 ? 2 : 1);
-  const int o = tid / split, part = tid - o * split;
-  double acc = 0.0;
-  if (o < nout) {
-    const int r = o % kTB, j = o / kTB;
-    const int len = kTB / split;
-    for (int c = part * len; c < (part + 1) * len; ++c) acc = fma(M[r][c], X[c][j], acc);
-  }
-  if (split >= 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  if (split >= 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  if (o < nout && part == 0) {
-    const int r = o % kTB, j = o / kTB;
-    out[r][j] = subtract ? out[r][j] - acc : acc;
-  }
-}
-
-template <typename Real, bool kLowerT>
-__global__ void __launch_bounds__(kThreads) trsv_blocked_kernel(int64_t n, const Real *A, int64_t lda,
-                                                                const double *Dinv, double *B, int64_t ldb,
-                                                                int nrhs, int32_t *flags, int32_t *status,
-                                                                int64_t wait_limit_ns) {
-  extern __shared__ double trsv_smem[];
-  double(*Ms)[kTB + 1] = reinterpret_cast<double(*)[kTB + 1]>(trsv_smem);
-  double(*Ds)[kTB + 1] = reinterpret_cast<double(*)[kTB + 1]>(trsv_smem + kTB * (kTB + 1));
-  double(*Xs)[kRhsV] = reinterpret_cast<double(*)[kRhsV]>(trsv_smem + 2 * kTB * (kTB + 1));
-  double(*Cs)[kRhsV] = reinterpret_cast<double(*)[kRhsV]>(trsv_smem + 2 * kTB * (kTB + 1) + kTB * kRhsV);
-  __shared__ int s_kb, s_stop;
-  const int nblk = static_cast<int>((n + kTB - 1) / kTB);
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    const int ticket = atomicAdd(flags, 1);
-    s_kb = kLowerT ? ticket : nblk - 1 - ticket;
-    s_stop = 0;
-  }
-  __syncthreads();
-  const int kb = s_kb;
-  if (kb < 0 || kb >= nblk) return;
-  const int64_t r0 = static_cast<int64_t>(kb) * kTB;
-  const int rb = static_cast<int>(lmin(kTB, n - r0));
-  // diagonal-block inverse (transposed for R^T) and the right-hand side
-  const double *dk = Dinv + static_cast<int64_t>(kb) * kTB * kTB;
-  for (int idx = tid; idx < kTB * kTB; idx += kThreads) {
-    const int c = idx / kTB, r = idx - c * kTB;
-    Ds[r][c] = kLowerT ? __ldcg(dk + c + r * kTB) : __ldcg(dk + r + c * kTB);
-  }
-  for (int idx = tid; idx < kTB * nrhs; idx += kThreads) {
-    const int j = idx / kTB, r = idx - j * kTB;
-    Cs[r][j] = r < rb ? ld_cg(B + r0 + r + j * ldb) : 0.0;
-  }
-  for (int step = 0; step < (kLowerT ? kb : nblk - 1 - kb); ++step) {
-    const int kk = kLowerT ? step : nblk - 1 - step;
-    const int64_t c0 = static_cast<int64_t>(kk) * kTB;
-    const int cb = static_cast<int>(lmin(kTB, n - c0));
-    __syncthreads();
-    for (int idx = tid; idx < kTB * kTB; idx += kThreads) {
-      const int c = idx / kTB, r = idx - c * kTB;
-      double v = 0.0;
-      if (r < rb && c < cb) v = kLowerT ? ld_cg(A + (c0 + c) + (r0 + r) * lda) : ld_cg(A + (r0 + r) + (c0 + c) * lda);
-      Ms[r][c] = v;
-    }
-    if (tid == 0) {
-      const uint64_t t0 = gtimer();
-      for (uint64_t it = 0; ld_acq(flags + 1 + kk) == 0; ++it) {
-        if (*(volatile int32_t *)status != 0) { s_stop = 1; break; }
-        if (gtimer() - t0 > static_cast<uint64_t>(wait_limit_ns) ||
-            it > (static_cast<uint64_t>(wait_limit_ns) >> 4) + 1000000ull) {
-          atomicCAS(status, 0, kStatusTimeout | (kk << 8));
-          s_stop = 1;
-          break;
-        }
-        __nanosleep(32);
-      }
-      __threadfence();
-    }
-    __syncthreads();
-    if (s_stop) return;
-    for (int idx = tid; idx < kTB * nrhs; idx += kThreads) {
-      const int j = idx / kTB, r = idx - j * kTB;
-      Xs[r][j] = r < cb ? ld_cg(B + c0 + r + j * ldb) : 0.0;
-    }
-    __syncthreads();
-    small_matvec(Ms, Xs, Cs, nrhs, true);
-  }
-  __syncthreads();
-  small_matvec(Ds, Cs, Xs, nrhs, false);
-  __syncthreads();
-  for (int idx = tid; idx < kTB * nrhs; idx += kThreads) {
-    const int j = idx / kTB, r = idx - j * kTB;
-    if (r < rb) B[r0 + r + j * ldb] = Xs[r][j];
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    st_rel(flags + 1 + kb, 1);
-  }
-}
-
 }  // namespace
 
 int launch_diag_inverse(int64_t n, const void *A, int64_t lda, bool real_is_double, double *Dinv, void *stream) {
@@ -363,43 +255,6 @@ int launch_diag_inverse(int64_t n, const void *A, int64_t lda, bool real_is_doub
     diag_inverse_kernel<float><<<nblk, kThreads, smem, st>>>(n, static_cast<const float *>(A), lda, Dinv);
   count_launch();
   return static_cast<int>(cudaGetLastError());
-}
-
-int launch_trsv_blocked(int64_t n, const void *A, int64_t lda, bool real_is_double, const double *Dinv, double *B,
-                        int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
-                        void *stream, bool lower_transposed) {
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int nblk = static_cast<int>((n + kTB - 1) / kTB);
-  const size_t smem = sizeof(double) * (2 * kTB * (kTB + 1) + 2 * kTB * kRhsV);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(trsv_blocked_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(trsv_blocked_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(trsv_blocked_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(trsv_blocked_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_done = true;
-  }
-  for (int64_t j0 = 0; j0 < nrhs; j0 += kRhsV) {
-    const int nr = static_cast<int>(nrhs - j0 < kRhsV ? nrhs - j0 : kRhsV);
-    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int32_t) * (nblk + 1), st);
-    if (e != cudaSuccess) return static_cast<int>(e);
-    double *Bj = B + j0 * ldb;
-    if (real_is_double) {
-      if (lower_transposed)
-        trsv_blocked_kernel<double, true><<<nblk, kThreads, smem, st>>>(n, static_cast<const double *>(A), lda, Dinv, Bj, ldb, nr, flags, status, wait_limit_ns);
-      else
-        trsv_blocked_kernel<double, false><<<nblk, kThreads, smem, st>>>(n, static_cast<const double *>(A), lda, Dinv, Bj, ldb, nr, flags, status, wait_limit_ns);
-    } else {
-      if (lower_transposed)
-        trsv_blocked_kernel<float, true><<<nblk, kThreads, smem, st>>>(n, static_cast<const float *>(A), lda, Dinv, Bj, ldb, nr, flags, status, wait_limit_ns);
-      else
-        trsv_blocked_kernel<float, false><<<nblk, kThreads, smem, st>>>(n, static_cast<const float *>(A), lda, Dinv, Bj, ldb, nr, flags, status, wait_limit_ns);
-    }
-    count_launch();
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return static_cast<int>(e);
-  }
-  return 0;
 }
 
 // ---------------------------------------------------------------------------------

@@ -167,11 +167,8 @@ int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, doub
                 int64_t wait_limit_ns, void *stream, bool lower_transposed = false);
 int trsm_flag_count(int64_t n);
 // Inverses of the 64 x 64 diagonal blocks of an upper-triangular R (FP64, 64*64 doubles
-// per block), and the blocked solve R X = B or R^T X = B that uses them.
+// per block; identity on the padding of a partial last block).
 int launch_diag_inverse(int64_t n, const void *A, int64_t lda, bool real_is_double, double *Dinv, void *stream);
-int launch_trsv_blocked(int64_t n, const void *A, int64_t lda, bool real_is_double, const double *Dinv, double *B,
-                        int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
-                        void *stream, bool lower_transposed);
 
 // Preconditioner solves of the refinement (precond.cu): FP64 inverses of R's 512 x 512
 // diagonal blocks built once from the 64 x 64 ones (precond_setup), then R X = B or
