@@ -35,6 +35,13 @@ FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 rate (the FP64 arm runs on the FP64 
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BATCH_COUNT = 2048
+# DRAM bytes (read + write) per nominal flop of the two executors, from one ncu capture
+# each of the unchanged kernels on smaller inputs of the same kind (the tensor-core
+# executor on a 24576 x 2048 matrix: 10.773 GB for 2.004e11 nominal flops, traffic
+# growing with the number of tile updates as the flops do; the batched FP32 executor on
+# the first 256 matrices of the batch: 1.331 GB for 4.907e10 flops).
+MIXED_TRAFFIC_PER_FLOP = 10.773e9 / 2.004e11
+BATCH_TRAFFIC_PER_FLOP = 1.331e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
 
 
@@ -303,6 +310,8 @@ def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
                      "peak_tflops": peak, "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
                      if prec == "fp32" else "FP64 nominal", "hbm_gbs": hbm_gbs,
                      "algorithmic_bytes": byts, "flops": flops, "bound_ms": t_bound,
+                     "traffic": flops * BATCH_TRAFFIC_PER_FLOP,
+                     "traffic_note": "bytes per launch, ncu capture of 256 matrices scaled by nominal flops",
                      "frac": t_bound / graph_ms, "classes": classes},
         "l2": "inputs larger than L2 (%.2f GB), restored before every launch" % (a_bytes / 2 / 1e9),
     }
@@ -568,7 +577,8 @@ def main_gpu(args):
         "gpu_launches": launches,
         "roofline": {"kernel": "executor_kernel<float,float,1> (mixed tiled-QR task graph, one launch per step)",
                      "bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                     "frac": achieved / bf16_sust, "traffic": None,
+                     "frac": achieved / bf16_sust, "traffic": flops * MIXED_TRAFFIC_PER_FLOP,
+                     "traffic_note": "bytes per launch, ncu capture at 24576x2048 scaled by nominal flops",
                      "peak_source": f"{peak_src} bf16 dense sustained (MEASURED_PEAKS.json)",
                      "flops_per_launch": flops, "avg_launch_ms": fac_avg},
         "ls_optimality": {"mixed": eta_mixed, "fp64": eta64, "target": tol},
