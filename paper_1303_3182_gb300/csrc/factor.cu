@@ -88,17 +88,23 @@ struct Smem {
   S *T;          // [ldt * ib]
   S *G;          // [ldt * ib]  Gram matrix of the reflectors of a block
   S *P1;         // [ldt * ib]  diagonal block of R(piv) during TTQRT
+  float *Wv;     // FP32 storage: [32 * kWvLd] W by rows (16-byte aligned), else null
+  float *red;    // FP32 storage: [3 * 32 * 33] partial sums of V^T C, else null
   int ldv, ldw, ldt;
   uint64_t *ph;  // phase clock of the execution trace, or null
 };
 
 __host__ __device__ inline int odd_ld(int x) { return x | 1; }
 
+// Row stride of the FP32 row-major copy of W (a multiple of 4 floats: 16-byte rows).
+constexpr int kWvLd = 36;
+constexpr size_t kF32Extra = 16 + (32 * kWvLd + 3 * 32 * 33) * sizeof(float);
+
 __host__ __device__ inline size_t smem_elems(int nb, int ib, size_t s_size) {
   const size_t ldv = odd_ld(nb), ldw = ib + 1, ldt = ib + 1;
   const size_t cw = chunk_cols(s_size);
   const size_t s_elems = ldv * ib + 2 * ldv * cw + ldw * cw + 3 * ldt * ib + 2 * ib;
-  return s_elems * s_size;
+  return s_elems * s_size + (s_size == sizeof(float) ? kF32Extra : 0);
 }
 
 template <typename S>
@@ -125,16 +131,64 @@ __device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
   s.tau_s = p;
   p += ib;
   s.scal_s = p;
+  p += ib;
+  s.Wv = nullptr;
+  s.red = nullptr;
+  if (sizeof(S) == sizeof(float)) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~static_cast<uintptr_t>(15);
+    s.Wv = reinterpret_cast<float *>(a);
+    s.red = s.Wv + 32 * kWvLd;
+  }
   return s;
 }
 
-// dst[r + c*ldd] = src[r + c*lds], r < nrows, c < ncols (warp per column, lanes on rows).
+// Tile loads keep many loads in flight per thread: every load of a pass is issued before
+// the first shared-memory store, so their latencies (hundreds of cycles from L2 or HBM)
+// overlap instead of adding up element by element.
+//
+// dst[r + c*ldd] = value(r, c) for r < nrows, c < ncols, where mode(r, c) selects the
+// value: kLoad -> src[r + c*lds] (through L2), kOne -> 1, kZero -> 0.  Warps take columns,
+// lanes rows; a pass covers kCU columns per warp and kRG groups of 32 rows.
+enum : int { kZero = 0, kOne = 1, kLoad = 2 };
+
+template <int kRG, int kCU, typename S, typename G, typename Mode>
+__device__ __forceinline__ void load_block_pass(S *dst, int ldd, const G *src, int64_t lds, int nrows,
+                                                int ncols, Mode mode) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < nrows; r0 += 32 * kRG)
+    for (int c0 = warp; c0 < ncols; c0 += kWarps * kCU) {
+      S v[kCU][kRG];
+#pragma unroll
+      for (int u = 0; u < kCU; ++u)
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) {
+          const int c = c0 + kWarps * u, r = r0 + lane + 32 * g;
+          const int md = (c < ncols && r < nrows) ? mode(r, c) : kZero;
+          v[u][g] = md == kLoad ? static_cast<S>(ldcg(src + r + static_cast<int64_t>(c) * lds))
+                                : (md == kOne ? S(1) : S(0));
+        }
+#pragma unroll
+      for (int u = 0; u < kCU; ++u)
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) {
+          const int c = c0 + kWarps * u, r = r0 + lane + 32 * g;
+          if (c < ncols && r < nrows) dst[r + c * ldd] = v[u][g];
+        }
+    }
+}
+
+template <typename S, typename G, typename Mode>
+__device__ void load_block_mode(S *dst, int ldd, const G *src, int64_t lds, int nrows, int ncols, Mode mode) {
+  if (nrows <= 128)
+    load_block_pass<4, 4>(dst, ldd, src, lds, nrows, ncols, mode);
+  else
+    load_block_pass<8, 2>(dst, ldd, src, lds, nrows, ncols, mode);
+}
+
+// dst[r + c*ldd] = src[r + c*lds], r < nrows, c < ncols.
 template <typename S, typename G>
 __device__ void load_block(S *dst, int ldd, const G *src, int64_t lds, int nrows, int ncols) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int c = warp; c < ncols; c += kWarps)
-    for (int r = lane; r < nrows; r += 32)
-      dst[r + c * ldd] = static_cast<S>(ldcg(src + r + static_cast<int64_t>(c) * lds));
+  load_block_mode(dst, ldd, src, lds, nrows, ncols, [](int, int) { return static_cast<int>(kLoad); });
 }
 
 template <typename S, typename G>
@@ -150,9 +204,138 @@ __device__ void store_block(G *dst, int64_t ldd, const S *src, int lds, int nrow
 //   W = T^T W  (Q^T, transpose_q = false)   or   W = T W  (Q, transpose_q = true)
 //   C1(0:kb, :) -= W,   C -= V W
 // V is nrows x kb (explicit zeros / unit entries), T upper triangular kb x kb.
+//
+// FP32 storage (s.Wv, s.red present) takes a register-blocked form: V^T C as 4 x 4 blocks
+// of W per thread over a quarter of the rows (four row groups, partial sums added in
+// shared memory), and C -= V W with 8 columns of a W row per 16-byte load.  Each thread
+// keeps the summation order of its own partial sums, so results are deterministic.
+__device__ void apply_block_f32(float *C, int ldc, int nrows, float *C1, int ldc1, int ncols, const float *V,
+                                int ldv, const float *T, int ldt, int kb, float *Wv, float *red, bool transpose_q) {
+  const int tid = threadIdx.x;
+  {
+    // W = C1 + V^T C: thread -> 4 x 4 block (a = 4 ab + x, c = 4 cb + y), row group rg
+    const int blk = tid & 63, rg = tid >> 6;
+    const int ab = blk & 7, cb = blk >> 3;
+    const float *va[4], *cc[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) va[x] = V + min(4 * ab + x, kb - 1) * ldv;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) cc[y] = C + min(4 * cb + y, ncols - 1) * ldc;
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 2
+    for (int r = rg; r < nrows; r += 4) {
+      float v[4], c[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) v[x] = va[x][r];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) c[y] = cc[y][r];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += v[x] * c[y];
+    }
+    if (rg > 0) {
+      float *part = red + (rg - 1) * 32 * 33;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) part[(4 * ab + x) + (4 * cb + y) * 33] = acc[x][y];
+    }
+    __syncthreads();
+    if (rg == 0) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int a = 4 * ab + x, c = 4 * cb + y, o = a + c * 33;
+          float w = acc[x][y] + red[o] + red[32 * 33 + o] + red[2 * 32 * 33 + o];
+          if (a < kb && c < ncols) {
+            if (C1) w += C1[a + c * ldc1];
+            red[o] = w;  // the full sum replaces this slot of the first partial buffer
+          }
+        }
+    }
+    __syncthreads();
+  }
+  {
+    // W = op(T) W (W read from red's first buffer, ld 33); C1 -= W; W kept by rows in Wv
+    const int a = tid & 31, g = tid >> 5;
+    float nw[4] = {0.f, 0.f, 0.f, 0.f};
+    if (a < kb) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = g + kWarps * u;
+        if (c >= ncols) continue;
+        float sum = 0.f;
+        if (!transpose_q) {
+          for (int b = 0; b <= a; ++b) sum += T[b + a * ldt] * red[b + c * 33];
+        } else {
+          for (int b = a; b < kb; ++b) sum += T[a + b * ldt] * red[b + c * 33];
+        }
+        nw[u] = sum;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = g + kWarps * u;
+        if (c < ncols) {
+          Wv[a * kWvLd + c] = nw[u];
+          if (C1) C1[a + c * ldc1] -= nw[u];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  {
+    // C -= V W: thread -> rows rt + 64 x, columns 8 cg .. 8 cg + 7
+    const int rt = tid & 63, cg = tid >> 6;
+    float acc[4][8];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+    int rr[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) rr[x] = min(rt + 64 * x, nrows - 1);
+    for (int b = 0; b < kb; ++b) {
+      const float4 w0 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg);
+      const float4 w1 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg + 4);
+      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const float v = V[rr[x] + b * ldv];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] += v * w[y];
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int r = rt + 64 * x;
+      if (r < nrows) {
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int c = 8 * cg + y;
+          if (c < ncols) C[r + c * ldc] -= acc[x][y];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename S>
 __device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols, const S *V,
-                            int ldv, const S *T, int ldt, int kb, S *W, int ldw, bool transpose_q) {
+                            int ldv, const S *T, int ldt, int kb, S *W, int ldw, bool transpose_q,
+                            float *Wv = nullptr, float *red = nullptr) {
+  if constexpr (sizeof(S) == sizeof(float)) {
+    if (Wv) {
+      apply_block_f32(C, ldc, nrows, C1, ldc1, ncols, V, ldv, T, ldt, kb, Wv, red, transpose_q);
+      return;
+    }
+  }
   const int tid = threadIdx.x;
   const int a = tid & 31, g = tid >> 5;
   // W = C1 + V^T C
@@ -557,10 +740,7 @@ __device__ void store_t(Real *Tg, int ib, int c0, int width, const Smem<S> &s, i
 
 template <typename S, typename Real>
 __device__ void load_t(S *dst, int ldt, const Real *Tg, int ib, int c0, int kb) {
-  for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
-    const int c = idx / kb, a = idx - c * kb;
-    dst[a + c * ldt] = static_cast<S>(ldcg(Tg + a + static_cast<int64_t>(c0 + c) * ib));
-  }
+  load_block(dst, ldt, Tg + static_cast<int64_t>(c0) * ib, ib, kb, kb);
 }
 
 struct TileGeom {
@@ -623,7 +803,7 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
       load_block(s.C, s.ldv, cblk, p.lda, rows, w);
       __syncthreads();
       apply_block(s.C, s.ldv, rows, static_cast<S *>(nullptr), 0, w, s.V, s.ldv, s.T, s.ldt, kb,
-                  s.W, s.ldw, false);
+                  s.W, s.ldw, false, s.Wv, s.red);
       store_block(cblk, p.lda, s.C, s.ldv, rows, w);
       __syncthreads();
     }
@@ -654,16 +834,11 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
     }
     const int rb = min(c0 + kb, mb);  // rows of tile i touched by this block
     // P2 = upper part of tile i, rows 0..rb-1, columns c0..c0+kb-1
-    for (int c = warp; c < kb; c += kWarps)
-      for (int r = lane; r < rb; r += 32)
-        s.V[r + c * s.ldv] =
-            (r <= c0 + c) ? static_cast<S>(ldcg(t2 + r + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
+    load_block_mode(s.V, s.ldv, t2 + static_cast<int64_t>(c0) * p.lda, p.lda, rb, kb,
+                    [c0](int r, int c) { return r <= c0 + c ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
     // P1 = upper part of the diagonal block of R(piv)
-    for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
-      const int c = idx / kb, r = idx - c * kb;
-      s.P1[r + c * s.ldt] =
-          (r <= c) ? static_cast<S>(ldcg(t1 + (c0 + r) + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
-    }
+    load_block_mode(s.P1, s.ldt, t1 + c0 + static_cast<int64_t>(c0) * p.lda, p.lda, kb, kb,
+                    [](int r, int c) { return r <= c ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
     __syncthreads();
     panel_factor<S, true>(s, kb, rb, c0, mb);
     phase_mark(s.ph, 0);
@@ -689,7 +864,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
       load_block(s.C1, s.ldv, c1, p.lda, kb, w);
       load_block(s.C, s.ldv, c2, p.lda, rb, w);
       __syncthreads();
-      apply_block(s.C, s.ldv, rb, s.C1, s.ldv, w, s.V, s.ldv, s.T, s.ldt, kb, s.W, s.ldw, false);
+      apply_block(s.C, s.ldv, rb, s.C1, s.ldv, w, s.V, s.ldv, s.T, s.ldt, kb, s.W, s.ldw, false, s.Wv, s.red);
       store_block(c1, p.lda, s.C1, s.ldv, kb, w);
       store_block(c2, p.lda, s.C, s.ldv, rb, w);
       __syncthreads();
@@ -719,15 +894,13 @@ __device__ void task_unmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *cp
       const int b = transpose_q ? nblk - 1 - bb : bb;
       const int c0 = b * ib, kb = min(ib, K - c0), rows = mb - c0;
       const Real *vb = vt + c0 + static_cast<int64_t>(c0) * p.lda;
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int c = warp; c < kb; c += kWarps)
-        for (int r = lane; r < rows; r += 32)
-          s.V[r + c * s.ldv] = (r > c) ? static_cast<S>(ldcg(vb + r + static_cast<int64_t>(c) * p.lda))
-                                       : (r == c ? S(1) : S(0));
+      load_block_mode(s.V, s.ldv, vb, p.lda, rows, kb, [](int r, int c) {
+        return r > c ? static_cast<int>(kLoad) : (r == c ? static_cast<int>(kOne) : static_cast<int>(kZero));
+      });
       load_t(s.T, s.ldt, Tg, ib, c0, kb);
       __syncthreads();
       apply_block(s.C + c0, s.ldv, rows, static_cast<S *>(nullptr), 0, w, s.V, s.ldv, s.T, s.ldt, kb,
-                  s.W, s.ldw, transpose_q);
+                  s.W, s.ldw, transpose_q, s.Wv, s.red);
     }
     store_block(cblk, ldc, s.C, s.ldv, mb, w);
     __syncthreads();
@@ -755,15 +928,13 @@ __device__ void task_ttmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *c1
     for (int bb = 0; bb < nblk; ++bb) {
       const int b = transpose_q ? nblk - 1 - bb : bb;
       const int c0 = b * ib, kb = min(ib, K - c0), rb = min(c0 + kb, mb);
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int c = warp; c < kb; c += kWarps)
-        for (int r = lane; r < rb; r += 32)
-          s.V[r + c * s.ldv] =
-              (r <= c0 + c) ? static_cast<S>(ldcg(vt + r + static_cast<int64_t>(c0 + c) * p.lda)) : S(0);
+      load_block_mode(s.V, s.ldv, vt + static_cast<int64_t>(c0) * p.lda, p.lda, rb, kb, [c0](int r, int c) {
+        return r <= c0 + c ? static_cast<int>(kLoad) : static_cast<int>(kZero);
+      });
       load_t(s.T, s.ldt, Tt, ib, c0, kb);
       __syncthreads();
       apply_block(s.C, s.ldv, rb, s.C1 + c0, s.ldv, w, s.V, s.ldv, s.T, s.ldt, kb, s.W, s.ldw,
-                  transpose_q);
+                  transpose_q, s.Wv, s.red);
     }
     store_block(b1, ldc, s.C1, s.ldv, K, w);
     store_block(b2, ldc, s.C, s.ldv, mb, w);
@@ -796,10 +967,50 @@ __device__ bool wait_ready(const ExecParams &p, int t) {
   }
 }
 
+// L2 prefetch hints for the tiles task ta reads and writes (GEQRT: its tile; TTQRT: the
+// two triangles' tiles; UNMQR / TTMQR: the target tile(s)), one tile column per thread in
+// 128-byte lines.  Every hinted address is an element of the matrix.  A hint only moves
+// data towards L2 (the point of coherence), so it may be issued before the task's
+// predecessors have finished, with no effect on results.
+template <typename Real>
+__device__ void prefetch_task_tiles(const ExecParams &p, int ta) {
+  const Task task = p.tasks[ta];
+  const Real *A = static_cast<const Real *>(p.A);
+  int64_t lda = p.lda, m = p.m, n = p.n;
+  int nb = p.nb;
+  if (p.mats) {
+    const BatchMat *d = p.mats + p.mat_of[ta];
+    A = static_cast<const Real *>(d->A);
+    lda = d->lda;
+    m = d->m;
+    n = d->n;
+    nb = d->nb;
+  }
+  int tcol = task.k, nt = 0;  // tile column; tile rows task.i and (second tile) task.piv
+  switch (task.kind) {
+    case kGeqrt: nt = 1; break;
+    case kTtqrt: nt = 2; break;
+    case kUnmqr: tcol = task.j; nt = 1; break;
+    case kTtmqr: tcol = task.j; nt = 2; break;
+    default: return;
+  }
+  for (int w = threadIdx.x; w < nt * nb; w += kThreads) {
+    const bool second = w >= nb;
+    const int c = second ? w - nb : w;
+    const int64_t row0 = static_cast<int64_t>(second ? task.piv : task.i) * nb;
+    const int64_t col = static_cast<int64_t>(tcol) * nb + c;
+    if (col >= n || row0 >= m) continue;
+    const int64_t bytes = lmin(nb, m - row0) * static_cast<int64_t>(sizeof(Real));
+    const char *base = reinterpret_cast<const char *>(A + row0 + col * lda);
+    for (int64_t off = 0; off < bytes; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(base + bytes - 1));
+  }
+}
+
 template <typename Real, typename S, bool kMixed>
 __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_task, s_stop;
+  __shared__ int s_task, s_stop, s_ahead;
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ uint64_t s_ph[5];
@@ -827,10 +1038,13 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   // task functions read the parameters from shared memory; the claim barrier below
   // publishes this copy (and each batched task's geometry) to the block
   if (threadIdx.x == 0) s_q = p;
+  // While task t runs, the CTA pulls the tiles of task t + gridDim.x into L2: with every
+  // CTA claiming one task per task duration, that task is claimed about one round later.
   for (;;) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(p.next, 1);
       int stop = t >= p.ntask;
+      s_ahead = t + static_cast<int>(gridDim.x) < p.ntask ? t + static_cast<int>(gridDim.x) : -1;
       const uint64_t t_claim = p.trace ? globaltimer_ns() : 0;
       if (!stop && !wait_ready(p, t)) stop = 1;
       if (p.trace && !stop) {
@@ -864,6 +1078,7 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     __syncthreads();
     if (s_stop) break;
     const int t = s_task;
+    if (s_ahead >= 0) prefetch_task_tiles<Real>(p, s_ahead);
     const Task task = p.tasks[t];
     const ExecParams &q = s_q;
     const int nb = q.nb;

@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "umma.cuh"
 
 namespace tqr {
@@ -60,68 +62,71 @@ __device__ __forceinline__ unsigned char *align1024(unsigned char *raw) {
   return raw + ((1024u - (a & 1023u)) & 1023u);
 }
 
-// Splits 8 floats into nparts 16-bit parts x = p0 + p1 + p2 (each the rounding of what
-// the previous parts leave), packed 8 to a uint4.
-__device__ __forceinline__ void split8(const float *x, uint4 *parts, int nparts, int fmt) {
+// Splits 8 floats into NP 16-bit parts x = p0 + p1 + p2 (each the rounding to nearest of
+// what the previous parts leave), packed 8 to a uint4.  Two values are converted per
+// instruction (packed bf16x2 / f16x2 conversions; the rounding of each value is the same
+// as a single conversion's).
+template <int NP>
+__device__ __forceinline__ void split8(const float *x, uint4 *parts, int fmt) {
   float rem[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) rem[j] = x[j];
-  for (int q = 0; q < nparts; ++q) {
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
     uint32_t w[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      uint32_t lo16, hi16;
       if (fmt == 1) {
-        const __nv_bfloat16 a = __float2bfloat16_rn(rem[2 * j]);
-        const __nv_bfloat16 b = __float2bfloat16_rn(rem[2 * j + 1]);
-        rem[2 * j] -= __bfloat162float(a);
-        rem[2 * j + 1] -= __bfloat162float(b);
-        lo16 = __bfloat16_as_ushort(a);
-        hi16 = __bfloat16_as_ushort(b);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(rem[2 * j], rem[2 * j + 1]);
+        if (q + 1 < NP) {
+          const float2 back = __bfloat1622float2(h);
+          rem[2 * j] -= back.x;
+          rem[2 * j + 1] -= back.y;
+        }
+        w[j] = *reinterpret_cast<const uint32_t *>(&h);
       } else {
-        const __half a = __float2half_rn(rem[2 * j]);
-        const __half b = __float2half_rn(rem[2 * j + 1]);
-        rem[2 * j] -= __half2float(a);
-        rem[2 * j + 1] -= __half2float(b);
-        lo16 = __half_as_ushort(a);
-        hi16 = __half_as_ushort(b);
+        const __half2 h = __floats2half2_rn(rem[2 * j], rem[2 * j + 1]);
+        if (q + 1 < NP) {
+          const float2 back = __half22float2(h);
+          rem[2 * j] -= back.x;
+          rem[2 * j + 1] -= back.y;
+        }
+        w[j] = *reinterpret_cast<const uint32_t *>(&h);
       }
-      w[j] = lo16 | (hi16 << 16);
     }
     parts[q] = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
-// One element split into nparts 16-bit parts (raw bits).
-__device__ __forceinline__ void split1(float x, uint16_t *parts, int nparts, int fmt) {
-  float rem = x;
-  for (int q = 0; q < nparts; ++q) {
-    if (fmt == 1) {
-      const __nv_bfloat16 a = __float2bfloat16_rn(rem);
-      rem -= __bfloat162float(a);
-      parts[q] = __bfloat16_as_ushort(a);
-    } else {
-      const __half a = __float2half_rn(rem);
-      rem -= __half2float(a);
-      parts[q] = __half_as_ushort(a);
-    }
-  }
+// Calls f(std::integral_constant<int, NP>) with the compile-time part count NP = nparts.
+template <typename F>
+__device__ __forceinline__ void with_parts(int nparts, F f) {
+  if (nparts == 3)
+    f(std::integral_constant<int, 3>{});
+  else if (nparts == 2)
+    f(std::integral_constant<int, 2>{});
+  else
+    f(std::integral_constant<int, 1>{});
 }
 
 // Writes the nparts images (consecutive, kImg apart) of an operand whose element
 // (row, kk) is get(row, kk).
 template <typename F>
 __device__ void write_image(unsigned char *img, F get, int fmt, int nparts) {
-  for (int ch = threadIdx.x; ch < kMNB * kMNB / 8; ch += kThreads) {
-    const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
-    const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
-    float x[8];
+  with_parts(nparts, [&](auto np) {
+    constexpr int NP = decltype(np)::value;
+    for (int ch = threadIdx.x; ch < kMNB * kMNB / 8; ch += kThreads) {
+      const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
+      const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
+      float x[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = get(row, k0 + j);
-    uint4 parts[3];
-    split8(x, parts, nparts, fmt);
-    for (int q = 0; q < nparts; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
-  }
+      for (int j = 0; j < 8; ++j) x[j] = get(row, k0 + j);
+      uint4 parts[NP];
+      split8<NP>(x, parts, fmt);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
+    }
+  });
 }
 
 // G(a, c) = sum_r V(r, a) V(r, c) for a < c.  Thread (warp w, lane l) forms rows
@@ -257,15 +262,35 @@ __device__ void v_times_tt(float *Z, const float *V, const float *Ts, Bounds bou
     for (int y = 0; y < 16; ++y) Z[(lane + 32 * x) + (ab + y) * kMLD] = acc[x][y];
 }
 
+// Fills the 128 x 128 shared-memory matrix dst[r + c * kMLD] with *src(r, c) (a global
+// address, loaded through L2) or zero where src(r, c) is null.  Each thread issues 16
+// loads before its first store, so that their latencies overlap.
+template <typename Src>
+__device__ void gather_tile(float *dst, Src src) {
+  constexpr int kB = 16;
+  static_assert(kMNB * kMNB % (kThreads * kB) == 0, "whole passes");
+  for (int e0 = threadIdx.x; e0 < kMNB * kMNB; e0 += kThreads * kB) {
+    float v[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * kThreads, r = e % kMNB, c = e / kMNB;
+      const float *ptr = src(r, c);
+      v[u] = ptr ? __ldcg(ptr) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * kThreads, r = e % kMNB, c = e / kMNB;
+      dst[r + c * kMLD] = v[u];
+    }
+  }
+}
+
 // Loads the ib-blocked T of a factored tile into the block diagonal of Ts (zeros elsewhere).
 __device__ void load_t_blocks(float *Ts, const float *Tg, int ib) {
-  for (int idx = threadIdx.x; idx < kMNB * kMNB; idx += kThreads) {
-    const int c = idx >> 7, a = idx & 127;
+  gather_tile(Ts, [&](int a, int c) -> const float * {
     const int cb = (c / ib) * ib;
-    float v = 0.f;
-    if (a >= cb && a <= c) v = static_cast<float>(ldcg(Tg + (a - cb) + static_cast<int64_t>(c) * ib));
-    Ts[a + c * kMLD] = v;
-  }
+    return (a >= cb && a <= c) ? Tg + (a - cb) + static_cast<int64_t>(c) * ib : nullptr;
+  });
 }
 
 // Operand images of GEQRT(i,k): V and Z = V T_full^T.
@@ -277,12 +302,10 @@ __device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   const float *tile = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, k);
   const float *Tg = t_ptr(static_cast<float *>(p.T), p.P, p.ib, kMNB, i, k, 0);
   const int mb = geo.rows(i), K = min(mb, geo.cols(k));
-  for (int idx = threadIdx.x; idx < kMNB * kMNB; idx += kThreads) {
-    const int c = idx >> 7, r = idx & 127;
-    float v = 0.f;
-    if (c < K && r < mb) v = r > c ? static_cast<float>(ldcg(tile + r + static_cast<int64_t>(c) * p.lda)) : (r == c ? 1.f : 0.f);
-    Vs[r + c * kMLD] = v;
-  }
+  load_block_mode(Vs, kMLD, tile, p.lda, kMNB, kMNB, [K, mb](int r, int c) {
+    if (c >= K || r >= mb) return static_cast<int>(kZero);
+    return r > c ? static_cast<int>(kLoad) : (r == c ? static_cast<int>(kOne) : static_cast<int>(kZero));
+  });
   load_t_blocks(Ts, Tg, p.ib);
   __syncthreads();
   // G(a, c) = v_a . v_c over rows r >= c (v_c is zero above its diagonal)
@@ -308,12 +331,9 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   const float *tile = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, k);
   const float *Tt = t_ptr(static_cast<float *>(p.T), p.P, p.ib, kMNB, i, k, 1);
   const int mb = geo.rows(i), K = geo.cols(k);
-  for (int idx = threadIdx.x; idx < kMNB * kMNB; idx += kThreads) {
-    const int c = idx >> 7, r = idx & 127;
-    float v = 0.f;
-    if (c < K && r < mb && r <= c) v = static_cast<float>(ldcg(tile + r + static_cast<int64_t>(c) * p.lda));
-    Vs[r + c * kMLD] = v;
-  }
+  load_block_mode(Vs, kMLD, tile, p.lda, kMNB, kMNB, [K, mb](int r, int c) {
+    return (c < K && r < mb && r <= c) ? static_cast<int>(kLoad) : static_cast<int>(kZero);
+  });
   load_t_blocks(Ts, Tt, p.ib);
   __syncthreads();
   // G(a, c) = v_a . v_c over rows r <= a (the tails live in the upper triangle)
@@ -334,12 +354,15 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
 // D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) op(B)^T over K = 128 for split operands:
 // sum of the products A_qa B_qb with qa + qb < nparts (hi*hi; + hi*lo + lo*hi for two
 // parts; + hi*lo2 + mid*mid + lo2*hi for three), smallest terms first.  neg_b negates B.
+// Only the k-steps ks0 .. ks1-1 (16 columns of K each) are issued, so that a GEMM can be
+// issued in parts as its operands become ready.
 __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const unsigned char *bufA, const unsigned char *bufB,
-                                           int nparts, int fmt, int neg_b, uint32_t accumulate_first) {
+                                           int nparts, int fmt, int neg_b, uint32_t accumulate_first,
+                                           int ks0 = 0, int ks1 = kMNB / 16) {
   const uint32_t idesc = umma::idesc_f16(128, 128, fmt, neg_b);
   const uint32_t a0 = umma::smem_u32(bufA), b0 = umma::smem_u32(bufB);
 #pragma unroll 1
-  for (int ks = 0; ks < kMNB / 16; ++ks) {
+  for (int ks = ks0; ks < ks1; ++ks) {
     const uint32_t off = (ks >> 2) * (kMNB * 128) + (ks & 3) * 32;
     uint32_t acc = (ks > 0 || accumulate_first) ? 1u : 0u;
     for (int s = nparts - 1; s >= 0; --s) {        // s = qa + qb
@@ -372,60 +395,65 @@ __device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int nc
   umma::tmem_wait_st();
 }
 
-// Split image of C^T (row c, k = r) in shared memory, one 16-byte chunk (8 rows of one
-// column) per thread step; the rows come as two float4 loads when the tile is 16-byte
-// aligned (vec4), else one by one.  Each thread issues the loads of four chunks before
+// Split image of C^T (row c, k = r) in shared memory, K half h only (rows r of C in
+// 64h .. 64h+63, one 1024-byte-swizzled K atom), one 16-byte chunk (8 rows of one column)
+// per thread step; the rows come as two float4 loads when the tile is 16-byte aligned
+// (vec4), else one by one.  Each thread issues the loads of its four chunks before
 // converting any, so that enough bytes are in flight to hide the memory latency.
 __device__ void c_transposed_image(unsigned char *img, const float *C, int64_t ldc, int mb, int ncols, int fmt,
-                                   int nparts, bool vec4) {
-  constexpr int kU = 4;
-  constexpr int kSteps = kMNB * kMNB / 8 / kThreads;  // 8 chunks per thread
-  static_assert(kSteps % kU == 0, "chunk groups");
-  for (int g = 0; g < kSteps; g += kU) {
-    float x[kU][8];
+                                   int nparts, bool vec4, int h) {
+  constexpr int kU = 4;  // chunks per thread and half
+  static_assert(kMNB * kMNB / 16 == kU * kThreads, "one group of chunks per half");
+  float x[kU][8];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int ch = threadIdx.x + (g + u) * kThreads;
-      const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
-      const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
-      const float *colp = C + static_cast<int64_t>(row) * ldc + k0;
-      if (row < ncols && vec4 && k0 + 8 <= mb) {
-        const float4 a = __ldcg(reinterpret_cast<const float4 *>(colp));
-        const float4 b = __ldcg(reinterpret_cast<const float4 *>(colp + 4));
-        x[u][0] = a.x; x[u][1] = a.y; x[u][2] = a.z; x[u][3] = a.w;
-        x[u][4] = b.x; x[u][5] = b.y; x[u][6] = b.z; x[u][7] = b.w;
-      } else {
+  for (int u = 0; u < kU; ++u) {
+    const int ch = threadIdx.x + (4 * h + u) * kThreads;
+    const int kb = ch >> 10, rem = ch & 1023, row = rem >> 3, sub = rem & 7;
+    const int k0 = kb * 64 + ((sub ^ (row & 7)) << 3);
+    const float *colp = C + static_cast<int64_t>(row) * ldc + k0;
+    if (row < ncols && vec4 && k0 + 8 <= mb) {
+      const float4 a = __ldcg(reinterpret_cast<const float4 *>(colp));
+      const float4 b = __ldcg(reinterpret_cast<const float4 *>(colp + 4));
+      x[u][0] = a.x; x[u][1] = a.y; x[u][2] = a.z; x[u][3] = a.w;
+      x[u][4] = b.x; x[u][5] = b.y; x[u][6] = b.z; x[u][7] = b.w;
+    } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[u][j] = (row < ncols && k0 + j < mb) ? __ldcg(colp + j) : 0.f;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int ch = threadIdx.x + (g + u) * kThreads;
-      uint4 parts[3];
-      split8(x[u], parts, nparts, fmt);
-      for (int q = 0; q < nparts; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
+      for (int j = 0; j < 8; ++j) x[u][j] = (row < ncols && k0 + j < mb) ? __ldcg(colp + j) : 0.f;
     }
   }
+  with_parts(nparts, [&](auto np) {
+    constexpr int NP = decltype(np)::value;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int ch = threadIdx.x + (4 * h + u) * kThreads;
+      uint4 parts[NP];
+      split8<NP>(x[u], parts, fmt);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) reinterpret_cast<uint4 *>(img + q * kImg)[ch] = parts[q];
+    }
+  });
 }
 
-// W^T (TMEM lane c, column a) -> split image of W as a B operand (row c, k = a).
-__device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, int nparts) {
+// W^T (TMEM lane c, column a) -> split image of W as a B operand (row c, k = a), K half h
+// only (a in 64h .. 64h+63: warps 0-3 take the first 32 columns, warps 4-7 the next 32).
+__device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, int nparts, int h) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = (warp & 3) * 32 + lane;
   const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
-  for (int g = 0; g < 2; ++g) {
-    const int a0 = (warp >> 2) * 64 + g * 32;
-    float v[32];
-    umma::tmem_ld32(tmem_w + lane_base + a0, v);
+  const int a0 = 64 * h + (warp >> 2) * 32;
+  float v[32];
+  umma::tmem_ld32(tmem_w + lane_base + a0, v);
+  with_parts(nparts, [&](auto np) {
+    constexpr int NP = decltype(np)::value;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      uint4 parts[3];
-      split8(v + 8 * u, parts, nparts, fmt);
+      uint4 parts[NP];
+      split8<NP>(v + 8 * u, parts, fmt);
       const uint32_t off = umma::sw128_offset(c, a0 + 8 * u, kMNB);
-      for (int q = 0; q < nparts; ++q) *reinterpret_cast<uint4 *>(img + q * kImg + off) = parts[q];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) *reinterpret_cast<uint4 *>(img + q * kImg + off) = parts[q];
     }
-  }
+  });
 }
 
 // Stores the accumulator at tmem_d (lane r, column c) into C(r, c).
@@ -474,6 +502,8 @@ __device__ __forceinline__ OperandBufs operand_bufs(unsigned char *raw, int npar
 }
 
 // UNMQR(i,k,j) on tensor cores:  D2 = C (TMEM),  W^T = C^T V,  D2 += Z (-W),  C = D2.
+// Each GEMM is issued in two K halves: the MMAs of the first half run while the second
+// half of its split operand (C^T, then W) is being written.
 __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int k, int j) {
   const TileGeom geo{p.m, p.n, kMNB};
   const OperandBufs b = operand_bufs(raw, p.nparts);
@@ -488,17 +518,21 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   float *C = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
   tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 128);
-  c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
-  umma::fence_proxy_async();
-  sync_all_tc();
-  phase_mark(ms.ph, 0);
-  if (threadIdx.x == 0) {
-    wait_or_flag(p, ms.bar_ld, ms.ld_phase);
-    umma::fence_after();
-    issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 0);
-    umma::commit(ms.bar_mma);
+  for (int h = 0; h < 2; ++h) {
+    c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
+    umma::fence_proxy_async();
+    sync_all_tc();
+    if (threadIdx.x == 0) {
+      if (h == 0) {
+        wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+        umma::fence_after();
+      }
+      issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 0, 4 * h, 4 * h + 4);
+      if (h == 1) umma::commit(ms.bar_mma);
+    }
   }
   ms.ld_phase ^= 1;
+  phase_mark(ms.ph, 0);
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
@@ -507,19 +541,21 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     umma::bulk_g2s(b.Y, imgZ, b.bytes, ms.bar_ld);
   }
   phase_mark(ms.ph, 1);
-  w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts);
-  umma::fence_proxy_async();
-  sync_all_tc();
-  phase_mark(ms.ph, 2);
-  if (threadIdx.x == 0) {
-    if (!b.Zb) {
-      wait_or_flag(p, ms.bar_ld, ms.ld_phase);
-      umma::fence_after();
+  for (int h = 0; h < 2; ++h) {
+    w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h);
+    umma::fence_proxy_async();
+    sync_all_tc();
+    if (threadIdx.x == 0) {
+      if (h == 0 && !b.Zb) {
+        wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+        umma::fence_after();
+      }
+      issue_gemm(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
+      if (h == 1) umma::commit(ms.bar_mma);
     }
-    issue_gemm(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, 1);
-    umma::commit(ms.bar_mma);
   }
   if (!b.Zb) ms.ld_phase ^= 1;
+  phase_mark(ms.ph, 2);
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
@@ -529,7 +565,8 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
 }
 
 // TTMQR(i,piv,k,j):  D1 = C1^T (TMEM), D2 = C2, D3 = C1;  W^T = D1 + C2^T V2;
-// D2 += Z2 (-W);  D3 += T^T (-W);  C2 = D2, C1 = D3.
+// D2 += Z2 (-W);  D3 += T^T (-W);  C2 = D2, C1 = D3.  GEMM1 and GEMM2 are issued in two
+// K halves like UNMQR's.
 __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int piv, int k,
                                 int j) {
   const TileGeom geo{p.m, p.n, kMNB};
@@ -546,7 +583,6 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   const int mb = geo.rows(i), ncols = geo.cols(j);
   tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 128);
   tile_rows_to_tmem(C1, p.lda, kMNB, ncols, ms.tmem, 256);
-  c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0);
   // D1 (lane c, column a) = C1(a, c): the identity part of the TT reflectors
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -570,16 +606,21 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     }
     umma::tmem_wait_st();
   }
-  umma::fence_proxy_async();
-  sync_all_tc();
-  phase_mark(ms.ph, 0);
-  if (threadIdx.x == 0) {
-    wait_or_flag(p, ms.bar_ld, ms.ld_phase);
-    umma::fence_after();
-    issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 1);
-    umma::commit(ms.bar_mma);
+  for (int h = 0; h < 2; ++h) {
+    c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
+    umma::fence_proxy_async();
+    sync_all_tc();
+    if (threadIdx.x == 0) {
+      if (h == 0) {
+        wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+        umma::fence_after();
+      }
+      issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 1, 4 * h, 4 * h + 4);
+      if (h == 1) umma::commit(ms.bar_mma);
+    }
   }
   ms.ld_phase ^= 1;
+  phase_mark(ms.ph, 0);
   wait_or_flag(p, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
@@ -588,25 +629,31 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     umma::bulk_g2s(b.Y, b.Zb ? imgT : imgZ, b.bytes, ms.bar_ld);
   }
   phase_mark(ms.ph, 1);
-  w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts);
-  umma::fence_proxy_async();
-  sync_all_tc();
-  phase_mark(ms.ph, 2);
-  if (threadIdx.x == 0) {
-    if (b.Zb) {
-      issue_gemm(ms.tmem + 128, b.Zb, b.X, p.nparts, p.fmt, 1, 1);   // C2 -= Z2 W
-      wait_or_flag(p, ms.bar_ld, ms.ld_phase);                      // T^T in Y
-      umma::fence_after();
-      issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);    // C1 -= T^T W
-      umma::commit(ms.bar_mma);
-    } else {
-      wait_or_flag(p, ms.bar_ld, ms.ld_phase);                      // Z2 in Y
-      umma::fence_after();
-      issue_gemm(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, 1);
-      umma::commit(ms.bar_mma);
+  for (int h = 0; h < 2; ++h) {
+    w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h);
+    umma::fence_proxy_async();
+    sync_all_tc();
+    if (threadIdx.x == 0) {
+      if (b.Zb) {
+        issue_gemm(ms.tmem + 128, b.Zb, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);  // C2 -= Z2 W
+        if (h == 1) {
+          wait_or_flag(p, ms.bar_ld, ms.ld_phase);                                       // T^T in Y
+          umma::fence_after();
+          issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);                    // C1 -= T^T W
+          umma::commit(ms.bar_mma);
+        }
+      } else {
+        if (h == 0) {
+          wait_or_flag(p, ms.bar_ld, ms.ld_phase);                                       // Z2 in Y
+          umma::fence_after();
+        }
+        issue_gemm(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
+        if (h == 1) umma::commit(ms.bar_mma);
+      }
     }
   }
   ms.ld_phase ^= 1;
+  phase_mark(ms.ph, 2);
   if (!b.Zb) {
     // Y held Z2: wait for that product, then bring T^T into Y
     wait_or_flag(p, ms.bar_mma, ms.mma_phase);

@@ -143,38 +143,5 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32
       : "memory");
 }
 
-// bf16 round-to-nearest split x = hi + lo (+ O(2^-16 |x|)) of 8 values, packed.
-__device__ __forceinline__ void split8_bf16(const float *x, uint4 &hi, uint4 &lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * j]);
-    const __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * j + 1]);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * j] - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * j + 1] - __bfloat162float(h1));
-    h[j] = static_cast<uint32_t>(__bfloat16_as_ushort(h0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(h1)) << 16);
-    l[j] = static_cast<uint32_t>(__bfloat16_as_ushort(l0)) | (static_cast<uint32_t>(__bfloat16_as_ushort(l1)) << 16);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// fp16 rounding of 8 values (the lo part is the fp16 residual, used only by callers that
-// want it).
-__device__ __forceinline__ void split8_f16(const float *x, uint4 &hi, uint4 &lo) {
-  uint32_t h[4], l[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const __half h0 = __float2half_rn(x[2 * j]);
-    const __half h1 = __float2half_rn(x[2 * j + 1]);
-    const __half l0 = __float2half_rn(x[2 * j] - __half2float(h0));
-    const __half l1 = __float2half_rn(x[2 * j + 1] - __half2float(h1));
-    h[j] = static_cast<uint32_t>(__half_as_ushort(h0)) | (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
-    l[j] = static_cast<uint32_t>(__half_as_ushort(l0)) | (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 }  // namespace umma
 }  // namespace tqr
