@@ -10,9 +10,12 @@ the library; the two share only the seeded generators of ``synthetic``.
 * ``householder`` - unblocked FP64 Householder QR, the four TT tile kernels applied one
   reflector at a time, the tiled algorithm, apply-Q, back substitution, least squares.
 * ``refine``     - FP64 least-squares checks (backward error, residual).
+* ``schedule``   - bounded-processor scheduling of the task graph (thesis Chapter 5):
+  Backflow priorities, the CP-method list schedule, the ALAP Derived bound.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` (thesis tables,
 closed forms, brute force against unblocked QR and LAPACK), except the ASAP critical
 path of the 128 x 64 case, where the thesis prints 1748 and this oracle gives 1734
-(parity unpinned for that one cell; GrASAP does not depend on it).
+(parity unpinned for that one cell; GrASAP does not depend on it), and three cells of
+the 5 x 5 schedule-length table (listed in tests/golden/schedule_5x5.txt).
 """
