@@ -43,6 +43,10 @@ BATCH_COUNT = 2048
 MIXED_TRAFFIC_PER_FLOP = 10.773e9 / 2.004e11
 BATCH_TRAFFIC_PER_FLOP = 1.331e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
+# Mean task durations (us) of the tensor-core executor on GB300 (GEQRT, TTQRT, UNMQR,
+# TTMQR at nb 128, bf16x6): the weights of the library's default claim order for the
+# tensor-core precisions (tqr_set_claim_order mode 2), used here for the schedule bound.
+TENSOR_TASK_US = (295, 323, 20, 32)
 
 
 def parse_args():
@@ -592,6 +596,7 @@ def main_gpu(args):
         "c5": c5,
         "c1": c1,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "schedule": schedule_bound(args, fac_avg),
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -599,6 +604,23 @@ def main_gpu(args):
     if rank == 0:
         print(json.dumps(line))
     replicas.finalize()
+
+
+def schedule_bound(args, executor_ms):
+    """The executor's span against the thesis's Chapter 5 bounds for its task graph on
+    the GPU's resident CTAs, with the measured mean task durations as weights: the
+    CP-method list schedule (the default claim order of the tensor-core path) and the
+    ALAP Derived Performance Bound."""
+    import torch
+
+    import paper_1303_3182_gb300 as tqr
+    nproc = torch.cuda.get_device_properties(0).multi_processor_count
+    p, q = -(-args.m // 128), -(-args.n // 128)
+    ms, bound, lost = tqr.schedule(p, q, args.tree, 4, nproc, TENSOR_TASK_US)
+    return {"claim_order": "CP-method list schedule on the resident CTAs (library default for tensor-core "
+                           "precisions)", "processors": nproc, "weights_us": list(TENSOR_TASK_US),
+            "list_schedule_ms": ms / 1e3, "alap_bound_ms": bound / 1e3, "executor_ms": executor_ms,
+            "executor_over_alap_bound": executor_ms / (bound / 1e3)}
 
 
 def main():

@@ -78,6 +78,43 @@ enum {
 int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len,
                  int64_t *cp_units);
 
+/* Bounded-processor schedule of the factorization task graph (thesis Chapter 5: Sections
+ * "ALAP Derived Performance Bound", Eq. (alapbound), and "Critical Path Scheduling";
+ * Section 5.5, Table "Schedule lengths for matrix of 5x5 tiles").  The graph is the one
+ * of tqr_elimlist (p x q tiles, tree, bs).
+ *   nproc      : number of processors, >= 1.
+ *   weights    : 4 int64 kernel weights (GEQRT, TTQRT, UNMQR, TTMQR), each >= 1; NULL =
+ *                the thesis's 4, 2, 6, 6.
+ *   makespan   : out (may be NULL), the length of the "CP Method" list schedule: every
+ *                task gets its Backflow priority (its weight plus the largest priority
+ *                of a successor) and at every moment the free processors take the ready
+ *                tasks of largest priority, ties to the task earlier in the sequential
+ *                program.
+ *   alap_bound : out (may be NULL), the ALAP Derived Performance Bound on the makespan,
+ *                max(critical path, ceil((T_seq + LA) / nproc)).
+ *   lost_area  : out (may be NULL), LA: the idle area of nproc processors at the end of
+ *                the as-late-as-possible execution on unbounded processors, walking back
+ *                from its end until more than nproc tasks are active.
+ * Host only; no device work.  Errors: -1/-2 p or q < 1, -3 unknown tree, -4 bs < 1 for
+ * PlasmaTree, -5 nproc < 1, -6 a weight < 1. */
+int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
+                 int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
+
+/* Claim order of the persistent executor for the factorizations planned after this call
+ * (plans are cached per order setting; results never depend on the order).
+ *   mode 0: earliest start on unbounded processors with the thesis weights, ties to the
+ *           longer remaining path.
+ *   mode 1: the start order of tqr_schedule's CP-method list schedule on as many
+ *           processors as the executor keeps resident CTAs, with the given per-kind
+ *           weights (GEQRT, TTQRT, UNMQR, TTMQR; each >= 1; NULL = 4, 2, 6, 6), e.g.
+ *           measured task durations of the chosen precision.
+ *   mode 2 (default): mode 1 with built-in weights for the tensor-core precisions (the
+ *           mean task durations in microseconds measured on GB300 at nb 128: 295, 323,
+ *           20, 32), mode 0 for TQR_FP64 and TQR_FP32.  weights is ignored.
+ * Every order is topological, so the executor's dependency waits always end.
+ * Host only.  Errors: -1 unknown mode, -2 a weight < 1. */
+int tqr_set_claim_order(int mode, const int64_t *weights);
+
 /* Bytes of the caller-owned T workspace of tqr_factor: two ib x nb compact-WY T
  * factors (GEQRT's and TTQRT's, Schreiber-Van Loan form, LAPACK GEQRT layout: block b
  * in columns b*ib..) per tile (i,k), i < p, k < min(p,q), in the precision's element

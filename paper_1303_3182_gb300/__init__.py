@@ -49,6 +49,8 @@ def lib() -> ctypes.CDLL:
         vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         sig = {
             "tqr_elimlist": (i32, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), c_i64p, c_i64p]),
+            "tqr_schedule": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
+            "tqr_set_claim_order": (i32, [i32, c_i64p]),
             "tqr_workspace_size": (i32, [i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
             "tqr_factor": (i32, [i64, i64, i32, i32, i32, i32, i32, vp, i64, vp, vp]),
             "tqr_apply_qt": (i32, [i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64, i64, vp]),
@@ -151,6 +153,31 @@ def elimlist(p: int, q: int, tree="greedy", bs: int = 1):
                                           arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                           ctypes.byref(n), ctypes.byref(cp)))
     return arr[:n.value], cp.value
+
+
+def _weights4(weights):
+    if weights is None:
+        return None
+    w = (ctypes.c_int64 * 4)(*[int(x) for x in weights])
+    return ctypes.cast(w, ctypes.POINTER(ctypes.c_int64))
+
+
+def schedule(p: int, q: int, tree="greedy", bs: int = 1, nproc: int = 1, weights=None):
+    """Bounded-processor schedule of the factorization task graph on nproc processors:
+    (CP-method makespan, ALAP Derived bound, lost area); weights are the four kernel
+    weights (GEQRT, TTQRT, UNMQR, TTMQR), None = 4, 2, 6, 6."""
+    ms, bound, la = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check("tqr_schedule", lib().tqr_schedule(p, q, _tree(tree), bs, nproc, _weights4(weights),
+                                              ctypes.byref(ms), ctypes.byref(bound), ctypes.byref(la)))
+    return ms.value, bound.value, la.value
+
+
+def set_claim_order(mode: int, weights=None) -> None:
+    """Executor claim order of later factorization plans: 0 = earliest start on unbounded
+    processors, 1 = start order of the bounded-processor CP-method schedule with the given
+    kernel weights (GEQRT, TTQRT, UNMQR, TTMQR), 2 = the default (1 with built-in GB300
+    weights for the tensor-core precisions, 0 otherwise)."""
+    _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))
 
 
 def plan_stats(m: int, n: int, nb: int, tree="greedy", bs: int = 1):

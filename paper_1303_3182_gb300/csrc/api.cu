@@ -20,6 +20,29 @@ namespace {
 
 std::mutex g_mu;
 int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
+// Claim order of factorization plans (tqr_set_claim_order): mode 0 or 1 as set, or
+// the automatic default (mode 2): the bounded-processor CP-method order for the
+// tensor-core precisions, with kernel weights equal to the mean task durations in
+// microseconds measured on GB300 (nb 128, split-bf16 x6: GEQRT 295, TTQRT 323, UNMQR
+// 20, TTMQR 32 - panels cost 15 times an update there, while the thesis's weights give
+// them less than an update), and the unbounded-processor order for FP64 / FP32, whose
+// measured task durations are close to the thesis's proportions.
+int g_order_mode = 2;
+int64_t g_order_w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
+constexpr int64_t kTensorOrderWeights[4] = {295, 323, 20, 32};
+
+OrderSpec effective_order(int prec) {
+  OrderSpec spec;
+  if (g_order_mode == 1) {
+    spec.mode = 1;
+    for (int c = 0; c < 4; ++c) spec.w[c] = g_order_w[c];
+  } else if (g_order_mode == 2 && is_tensor_prec(prec)) {
+    spec.mode = 1;
+    for (int c = 0; c < 4; ++c) spec.w[c] = kTensorOrderWeights[c];
+  }
+  return spec;
+}
 int g_debug_plans = 0;
 thread_local std::string g_last_error;
 int64_t g_wait_limit_ns = 20LL * 1000 * 1000 * 1000;
@@ -82,7 +105,8 @@ struct Plan {
 };
 
 // kind 0 = factorization, 1 = apply Q^T, 2 = apply Q
-using PlanKey = std::tuple<int, int, int, int, int, int>;  // device, kind, P, Q, tree, bs
+// device, kind, P, Q, tree, bs, claim-order generation (0: default order), processors
+using PlanKey = std::tuple<int, int, int, int, int, int, int, int>;
 std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
 
 struct Scratch {
@@ -108,15 +132,25 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 }
 
 // Returns the cached plan for (kind, P, Q, tree, bs) on the current device.
-int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out) {
+// order: the claim order of a factorization plan (kind 0), with spec.nproc the
+// executor's resident CTAs; ignored for the apply-Q plans.
+int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSpec *order = nullptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   std::lock_guard<std::mutex> lock(g_mu);
   const int64_t drop = kind == 0 ? g_drop_edge : -1;
+  OrderSpec spec;
+  if (order) spec = *order;
+  spec.nproc = std::max(1, spec.nproc);
+  const bool bounded = kind == 0 && spec.mode == 1;
+  // the order's identity: user weights carry the setting's generation, the built-in
+  // tensor-core weights a key of their own
+  const bool builtin = bounded && g_order_mode == 2;
   // a plan built with the test hook is never reused: it gets a key of its own
   const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : kind, P, Q, tree,
-                    tree == TQR_PLASMA ? bs : 0};
+                    tree == TQR_PLASMA ? bs : 0, bounded ? (builtin ? -1 : 1 + g_order_gen) : 0,
+                    bounded ? spec.nproc : 0};
   auto it = g_plans.find(key);
   if (it != g_plans.end()) {
     *out = it->second.get();
@@ -127,7 +161,7 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out) {
   auto plan = std::make_unique<Plan>();
   plan->device = dev;
   if (kind == 0)
-    build_factor_graph(P, Q, elims, plan->g, drop);
+    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr);
   else
     build_applyq_graph(P, Q, elims, kind == 2, plan->g);
   if (drop >= 0) g_drop_edge = -1;  // the test hook applies to one plan only
@@ -301,6 +335,63 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len, in
   return TQR_OK;
 }
 
+int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights, int64_t *makespan,
+                 int64_t *alap_bound, int64_t *lost_area) {
+  if (p < 1) return -1;
+  if (q < 1) return -2;
+  if (tree < TQR_FLAT || tree > TQR_ASAP) return -3;
+  if (tree == TQR_PLASMA && bs < 1) return -4;
+  if (nproc < 1) return -5;
+  int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+  if (weights)
+    for (int c = 0; c < 4; ++c) {
+      if (weights[c] < 1) return -6;
+      w[c] = weights[c];
+    }
+  try {
+    std::vector<Elim> elims;
+    elimination_list(p, q, tree, bs, elims);
+    GraphBuilder b(p * q * 2);
+    add_factor_program(b, p, q, elims);
+    const int n = static_cast<int>(b.tasks.size());
+    std::vector<std::vector<int32_t>> succ(n);
+    std::vector<int32_t> npred(n);
+    std::vector<int64_t> wt(n);
+    for (int t = 0; t < n; ++t) {
+      npred[t] = static_cast<int32_t>(b.preds[t].size());
+      for (int32_t x : b.preds[t]) succ[x].push_back(t);
+      wt[t] = w[b.tasks[t].kind];
+    }
+    const std::vector<int64_t> prio = backflow_priorities(succ, wt);
+    if (makespan) *makespan = cp_list_schedule(succ, npred, wt, prio, nproc, nullptr);
+    int64_t la = 0;
+    const int64_t bound = alap_derived_bound(wt, prio, nproc, &la);
+    if (alap_bound) *alap_bound = bound;
+    if (lost_area) *lost_area = la;
+  } catch (const std::bad_alloc &) {
+    return TQR_ENOMEM;
+  } catch (...) {
+    g_last_error = "internal error in tqr_schedule";
+    return TQR_ECUDA;
+  }
+  return TQR_OK;
+}
+
+int tqr_set_claim_order(int mode, const int64_t *weights) {
+  if (mode < 0 || mode > 2) return -1;
+  int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+  if (weights && mode == 1)
+    for (int c = 0; c < 4; ++c) {
+      if (weights[c] < 1) return -2;
+      w[c] = weights[c];
+    }
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_order_mode = mode;
+  for (int c = 0; c < 4; ++c) g_order_w[c] = w[c];
+  ++g_order_gen;
+  return TQR_OK;
+}
+
 int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T_bytes) {
   const int rc = check_tiles(m, n, nb, ib, TQR_GREEDY, 1, prec);
   if (rc) return rc;
@@ -324,7 +415,13 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
   try {
     const int P = static_cast<int>(ceil_div(m, nb)), Q = static_cast<int>(ceil_div(n, nb));
     Plan *plan = nullptr;
-    if ((rc = get_plan(0, P, Q, tree, bs, &plan)) != 0) return rc;
+    OrderSpec order;
+    {
+      std::lock_guard<std::mutex> lock(g_mu);
+      order = effective_order(prec);
+    }
+    if (order.mode == 1) order.nproc = executor_slots(dbl, is_tensor_prec(prec), nb, ib);
+    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order)) != 0) return rc;
     ExecParams prm{};
     prm.A = A;
     prm.lda = lda;

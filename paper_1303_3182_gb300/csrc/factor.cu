@@ -1038,8 +1038,9 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   // task functions read the parameters from shared memory; the claim barrier below
   // publishes this copy (and each batched task's geometry) to the block
   if (threadIdx.x == 0) s_q = p;
-  // While task t runs, the CTA pulls the tiles of task t + gridDim.x into L2: with every
-  // CTA claiming one task per task duration, that task is claimed about one round later.
+  // While task t runs, a SIMT executor's CTA pulls the tiles of task t + gridDim.x into
+  // L2: with every CTA claiming one task per task duration, that task is claimed about one
+  // round later.
   for (;;) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(p.next, 1);
@@ -1078,7 +1079,9 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     __syncthreads();
     if (s_stop) break;
     const int t = s_task;
-    if (s_ahead >= 0) prefetch_task_tiles<Real>(p, s_ahead);
+    // (the tensor-core executor runs faster without it: its tasks are short and the
+    // prefetched tiles add DRAM traffic)
+    if (!kMixed && s_ahead >= 0) prefetch_task_tiles<Real>(p, s_ahead);
     const Task task = p.tasks[t];
     const ExecParams &q = s_q;
     const int nb = q.nb;

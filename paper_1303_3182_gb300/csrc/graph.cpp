@@ -8,7 +8,10 @@
 // its strictly-lower part (GEQRT reflectors, read by UNMQR) and its upper part (R and
 // later the TTQRT reflectors) lets UNMQR overlap TTQRT as Section 3.1.1 states.
 #include <algorithm>
+#include <functional>
+#include <map>
 #include <numeric>
+#include <queue>
 
 #include "tqr_internal.h"
 
@@ -73,30 +76,128 @@ void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col)
   }
 }
 
-void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge) {
+std::vector<int64_t> backflow_priorities(const std::vector<std::vector<int32_t>> &succ,
+                                         const std::vector<int64_t> &w) {
+  const int n = static_cast<int>(w.size());
+  std::vector<int64_t> cp(n, 0);
+  for (int t = n - 1; t >= 0; --t) {  // program order is topological
+    int64_t best = 0;
+    for (int32_t s : succ[t]) best = std::max(best, cp[s]);
+    cp[t] = best + w[t];
+  }
+  return cp;
+}
+
+int64_t cp_list_schedule(const std::vector<std::vector<int32_t>> &succ, const std::vector<int32_t> &npred,
+                         const std::vector<int64_t> &w, const std::vector<int64_t> &prio, int nproc,
+                         std::vector<int64_t> *start) {
+  const int n = static_cast<int>(w.size());
+  using Item = std::pair<int64_t, int32_t>;
+  // ready tasks: largest priority first, then the earlier task of the program
+  auto later = [](const Item &a, const Item &c) { return a.first != c.first ? a.first < c.first : a.second > c.second; };
+  std::priority_queue<Item, std::vector<Item>, decltype(later)> ready(later);
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> running;  // (finish, task)
+  std::vector<int32_t> missing(npred);
+  for (int t = 0; t < n; ++t)
+    if (missing[t] == 0) ready.push({prio[t], t});
+  if (start) start->assign(n, 0);
+  int free = nproc, done = 0;
+  int64_t now = 0, makespan = 0;
+  while (done < n) {
+    while (free > 0 && !ready.empty()) {
+      const int32_t t = ready.top().second;
+      ready.pop();
+      if (start) (*start)[t] = now;
+      running.push({now + w[t], t});
+      makespan = std::max(makespan, now + w[t]);
+      --free;
+    }
+    now = running.top().first;
+    while (!running.empty() && running.top().first == now) {
+      const int32_t t = running.top().second;
+      running.pop();
+      ++free;
+      ++done;
+      for (int32_t s : succ[t])
+        if (--missing[s] == 0) ready.push({prio[s], s});
+    }
+  }
+  return makespan;
+}
+
+int64_t alap_derived_bound(const std::vector<int64_t> &w, const std::vector<int64_t> &prio, int nproc,
+                           int64_t *lost) {
+  // every task as late as possible on unbounded processors: t runs over
+  // [crit - prio[t], crit - prio[t] + w[t])
+  int64_t crit = 0, tseq = 0;
+  for (size_t t = 0; t < w.size(); ++t) {
+    crit = std::max(crit, prio[t]);
+    tseq += w[t];
+  }
+  std::map<int64_t, int64_t> delta;
+  for (size_t t = 0; t < w.size(); ++t) {
+    delta[crit - prio[t]] += 1;
+    delta[crit - prio[t] + w[t]] -= 1;
+  }
+  // active count per segment, then the idle area of nproc processors walking back from
+  // the end until more than nproc tasks are active
+  std::vector<std::pair<int64_t, int64_t>> seg;  // (length, active)
+  int64_t active = 0;
+  for (auto it = delta.begin(); it != delta.end(); ++it) {
+    active += it->second;
+    auto nx = std::next(it);
+    if (nx != delta.end()) seg.push_back({nx->first - it->first, active});
+  }
+  int64_t la = 0;
+  for (auto it = seg.rbegin(); it != seg.rend(); ++it) {
+    if (it->second > nproc) break;
+    la += (nproc - it->second) * it->first;
+  }
+  if (lost) *lost = la;
+  const int64_t tp = (tseq + la + nproc - 1) / nproc;
+  return std::max(crit, tp);
+}
+
+void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge, const OrderSpec *spec) {
   const int n = static_cast<int>(b.tasks.size());
   // successors in program order
   std::vector<std::vector<int32_t>> succ(n);
   for (int t = 0; t < n; ++t)
     for (int32_t x : b.preds[t]) succ[x].push_back(t);
-  // longest path to a sink, including the task itself (program order is topological)
-  std::vector<int64_t> bottom(n, 0);
-  for (int t = n - 1; t >= 0; --t) {
-    int64_t best = 0;
-    for (int32_t s : succ[t]) best = std::max(best, bottom[s]);
-    bottom[t] = best + b.weight[t];
-  }
-  // executor order: earliest start with unbounded processors, then the longer
-  // remaining path first, then program order.  Earliest start strictly increases
-  // along every edge, so this order is topological.
+  // longest path to a sink, including the task itself (thesis weights)
+  const std::vector<int64_t> wt(b.weight.begin(), b.weight.end());
+  const std::vector<int64_t> bottom = backflow_priorities(succ, wt);
   std::vector<int32_t> order(n);
   std::iota(order.begin(), order.end(), 0);
-  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
-    const int64_t sa = b.finish[a] - b.weight[a], sc = b.finish[c] - b.weight[c];
-    if (sa != sc) return sa < sc;
-    if (bottom[a] != bottom[c]) return bottom[a] > bottom[c];
-    return a < c;
-  });
+  if (spec && spec->mode == 1) {
+    // start times of the bounded-processor CP-method schedule with the given kind
+    // weights (all positive): a task starts after its predecessors finished, so this
+    // order is topological
+    std::vector<int64_t> w(n);
+    std::vector<int32_t> npred(n);
+    for (int t = 0; t < n; ++t) {
+      w[t] = spec->w[b.tasks[t].kind];
+      npred[t] = static_cast<int32_t>(b.preds[t].size());
+    }
+    const std::vector<int64_t> prio = backflow_priorities(succ, w);
+    std::vector<int64_t> st;
+    cp_list_schedule(succ, npred, w, prio, std::max(1, spec->nproc), &st);
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+      if (st[a] != st[c]) return st[a] < st[c];
+      if (prio[a] != prio[c]) return prio[a] > prio[c];
+      return a < c;
+    });
+  } else {
+    // earliest start with unbounded processors, then the longer remaining path first,
+    // then program order.  Earliest start strictly increases along every edge, so this
+    // order is topological.
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+      const int64_t sa = b.finish[a] - b.weight[a], sc = b.finish[c] - b.weight[c];
+      if (sa != sc) return sa < sc;
+      if (bottom[a] != bottom[c]) return bottom[a] > bottom[c];
+      return a < c;
+    });
+  }
   std::vector<int32_t> pos(n);
   for (int r = 0; r < n; ++r) pos[order[r]] = r;
 
@@ -135,8 +236,7 @@ void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge) {
   }
 }
 
-void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge) {
-  GraphBuilder b(p * q * 2);
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims) {
   const int kmax = std::min(p, q);
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : elims) by_col[e.k].push_back(e);
@@ -144,7 +244,13 @@ void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, 
     add_panel_tasks(b, p, q, k);
     add_elim_tasks(b, q, k, by_col[k]);
   }
-  finalize_graph(b, g, drop_edge);
+}
+
+void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge,
+                        const OrderSpec *order) {
+  GraphBuilder b(p * q * 2);
+  add_factor_program(b, p, q, elims);
+  finalize_graph(b, g, drop_edge, order);
 }
 
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g) {

@@ -88,13 +88,39 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k);
 void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col);
 // Orders a built graph for the executor (earliest start, then longest remaining path)
 // and fills the successor CSR.
-void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1);
+// Executor (claim) order of a factorization graph.  mode 0: earliest start with
+// unbounded processors (thesis weights), then the longer remaining path first.  mode 1:
+// the bounded-processor list schedule of thesis Chapter 5 ("CP Method") on nproc
+// processors with per-kind weights w[4] (GEQRT, TTQRT, UNMQR, TTMQR), tasks ordered by
+// their start in that schedule.
+struct OrderSpec {
+  int mode = 0;
+  int nproc = 1;
+  int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+};
+void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1, const OrderSpec *order = nullptr);
+// Tasks of the sequential program (all panels, in column order) added to b.
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims);
+// Backflow priorities (a task's weight plus the largest priority of its successors) of
+// a graph in program order with successor lists succ and weights w.
+std::vector<int64_t> backflow_priorities(const std::vector<std::vector<int32_t>> &succ,
+                                         const std::vector<int64_t> &w);
+// CP-method list schedule on nproc processors: at every moment free processors take the
+// ready tasks of largest priority (ties: earlier in program order).  Returns the
+// makespan; start (if not null) receives every task's start time.
+int64_t cp_list_schedule(const std::vector<std::vector<int32_t>> &succ, const std::vector<int32_t> &npred,
+                         const std::vector<int64_t> &w, const std::vector<int64_t> &prio, int nproc,
+                         std::vector<int64_t> *start);
+// ALAP Derived Performance Bound of Eq. (alapbound) for nproc processors; *lost (if not
+// null) receives the lost area LA_p.
+int64_t alap_derived_bound(const std::vector<int64_t> &w, const std::vector<int64_t> &prio, int nproc,
+                           int64_t *lost);
 
 // Builds the factorization task graph of a p x q tile matrix with the given list
 // (column-by-column program of Algorithm "elimTR"; dependencies from the tile regions
 // each kernel reads and writes, Eq. ttdeps / ttdeps2).
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
-                        int64_t drop_edge = -1);
+                        int64_t drop_edge = -1, const OrderSpec *order = nullptr);
 // Builds the graph that applies Q^T (or Q when reverse) to a right-hand-side block.
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g);
 

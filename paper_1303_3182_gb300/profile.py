@@ -101,11 +101,16 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=1303318202)
     ap.add_argument("--trace", default="")
+    ap.add_argument("--order", type=int, default=0,
+                    help="executor claim order: 0 = earliest start (unbounded processors), 1 = bounded CP method")
+    ap.add_argument("--weights", default="", help="claim-order kernel weights GEQRT,TTQRT,UNMQR,TTMQR (--order 1)")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: number of matrices")
     ap.add_argument("--lstsq", action="store_true", help="least-squares mode")
     ap.add_argument("--cond", type=float, default=1e6)
     a = ap.parse_args()
     build.build()
+    if a.order:
+        tqr.set_claim_order(a.order, [int(x) for x in a.weights.split(",")] if a.weights else None)
     if a.batch:
         _batch(a, tqr, torch)
     elif a.lstsq:

@@ -230,3 +230,27 @@ def test_serialized_equals_parallel_bitwise():
     tqr.factor(a2, 64, 16, "greedy", T=t2)
     torch.cuda.synchronize()
     assert torch.equal(a1, a2) and torch.equal(t1, t2)
+
+
+@pytest.mark.parametrize("prec,nb,ib,m,n", [("fp64", 64, 16, 1000, 300), ("bf16x6", 128, 32, 1408, 640),
+                                            ("fp32", 64, 16, 777, 200)])
+def test_bounded_claim_order_gives_identical_factors(prec, nb, ib, m, n):
+    """Claim orders of tqr_set_claim_order (unbounded earliest start, the bounded-processor
+    CP-method schedule with two weight sets, the default): each task's arithmetic is
+    independent of when it runs, so the factors and T are bit-identical."""
+    A = synthetic.gaussian(m, n, seed=1303318207)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    out = []
+    try:
+        for mode, w in ((0, None), (1, (4, 2, 6, 6)), (1, (300, 320, 20, 32)), (2, None)):
+            tqr.set_claim_order(mode, w)
+            Ad = to_dev(A, dtype)
+            T = torch.zeros(tqr.workspace_size(m, n, nb, ib, prec), dtype=torch.uint8, device="cuda")
+            tqr.factor(Ad, nb, ib, "greedy", 1, prec, T=T)
+            torch.cuda.synchronize()
+            out.append((Ad.cpu(), T.cpu()))
+    finally:
+        tqr.set_claim_order(2)
+    for Ad, T in out[1:]:
+        assert torch.equal(Ad, out[0][0])
+        assert torch.equal(T, out[0][1])

@@ -1,0 +1,69 @@
+"""Host-side tests of the library's bounded-processor schedule (no GPU): tqr_schedule's
+CP-method makespan, ALAP Derived bound and lost area are bit-exact against the oracle
+(oracle/schedule.py, itself pinned to the thesis's 5 x 5 schedule-length table) on the
+thesis weights and on other weights; invalid arguments return negative codes."""
+import random
+
+import pytest
+
+from oracle import elimlists as E
+from oracle import schedule as S
+
+import paper_1303_3182_gb300 as tqr
+
+TREES = {"flat": E.FLAT, "plasma": E.PLASMA, "binary": E.BINARY, "fibonacci": E.FIBONACCI,
+         "greedy": E.GREEDY, "grasap": E.GRASAP, "asap": E.ASAP}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    from paper_1303_3182_gb300 import build
+    build.build()
+
+
+def _oracle(p, q, tree, bs, nproc, weights):
+    g = S.task_graph(p, q, E.elimination_list(p, q, TREES[tree], bs=bs), weights)
+    ms, _ = S.list_schedule(g, nproc)
+    bound, la = S.alap_bound(g, nproc)
+    return ms, bound, la
+
+
+@pytest.mark.parametrize("tree", ["grasap", "greedy", "fibonacci", "flat"])
+def test_5x5_table_processors_1_to_14(tree):
+    for nproc in range(1, 15):
+        assert tqr.schedule(5, 5, tree, 1, nproc) == _oracle(5, 5, tree, 1, nproc, S.DEFAULT_WEIGHTS)
+
+
+def test_random_shapes_trees_weights_and_processors():
+    rng = random.Random(1303318206)
+    for _ in range(60):
+        p, q = rng.randint(1, 14), rng.randint(1, 8)
+        tree = rng.choice(sorted(TREES))
+        bs = rng.randint(1, 4)
+        nproc = rng.choice([1, 2, 3, 5, 8, 13, 40, 200])
+        weights = None if rng.random() < 0.3 else tuple(rng.randint(1, 40) for _ in range(4))
+        got = tqr.schedule(p, q, tree, bs, nproc, weights)
+        want = _oracle(p, q, tree, bs, nproc, weights or S.DEFAULT_WEIGHTS)
+        assert got == want, (p, q, tree, bs, nproc, weights)
+
+
+def test_gpu_scale_weights():
+    """The claim-order weights of the tensor-core executor (task durations in us) on the
+    128 x 16 tile grid of a 16384 x 2048 matrix: library and oracle agree."""
+    w = (295, 323, 20, 32)
+    assert tqr.schedule(128, 16, "greedy", 1, 152, w) == _oracle(128, 16, "greedy", 1, 152, w)
+
+
+def test_invalid_arguments():
+    L = tqr.lib()
+    assert L.tqr_schedule(0, 3, 4, 1, 2, None, None, None, None) == -1
+    assert L.tqr_schedule(3, 0, 4, 1, 2, None, None, None, None) == -2
+    assert L.tqr_schedule(3, 3, 9, 1, 2, None, None, None, None) == -3
+    assert L.tqr_schedule(3, 3, 1, 0, 2, None, None, None, None) == -4
+    assert L.tqr_schedule(3, 3, 4, 1, 0, None, None, None, None) == -5
+    assert L.tqr_schedule(3, 3, 4, 1, 2, tqr._weights4((4, 0, 6, 6)), None, None, None) == -6
+    assert L.tqr_set_claim_order(3, None) == -1
+    assert L.tqr_set_claim_order(-1, None) == -1
+    assert L.tqr_set_claim_order(1, tqr._weights4((1, 2, -3, 4))) == -2
+    assert L.tqr_set_claim_order(0, None) == 0
+    assert L.tqr_set_claim_order(2, None) == 0
