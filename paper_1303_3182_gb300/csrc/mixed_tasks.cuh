@@ -1,4 +1,4 @@
-// Mixed-precision tile tasks (included by factor.cu; uses its SIMT helpers).
+// Mixed-precision tile tasks (included by executor.cuh; uses its SIMT helpers).
 //
 // The matrix is FP32.  GEQRT and TTQRT run the SIMT kernels with FP64 Householder norms
 // and tau, then turn the tile's reflectors into tensor-core operand images:

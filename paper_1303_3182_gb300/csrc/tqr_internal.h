@@ -130,7 +130,7 @@ void count_launch(int64_t k = 1);
 int64_t wait_limit_ns();   // current device-wait limit (tqr_set_wait_limit_ns)
 bool sync_enabled();       // tqr_set_sync state
 
-// ---- device side (factor.cu, solve.cu) -------------------------------------------
+// ---- device side (executor.cuh, solve.cu) -------------------------------------------
 // Status word layout written by the device: code in the low 8 bits, task index above.
 constexpr int kStatusTimeout = 3;
 
@@ -165,6 +165,15 @@ struct ExecParams {
 // Launches the persistent tile-task executor on "stream".  real_is_double selects the
 // factor storage type.  Returns a cudaError_t value (0 = success).
 int launch_executor(const ExecParams &p, bool real_is_double, void *stream);
+// The executor instantiations (exec_*.cu): launch with smem bytes of dynamic shared
+// memory; resident CTAs of the whole GPU at that shared-memory size (0 on error).
+int exec_launch_f64(const ExecParams &p, void *stream, size_t smem);
+int exec_launch_f32(const ExecParams &p, void *stream, size_t smem);
+int exec_launch_f32_apply(const ExecParams &p, void *stream, size_t smem);
+int exec_launch_mixed(const ExecParams &p, void *stream, size_t smem);
+int exec_slots_f64(size_t smem);
+int exec_slots_f32(size_t smem);
+int exec_slots_mixed(size_t smem);
 // Dynamic shared memory the executor needs (0 if nb/ib do not fit on one SM).
 size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q);
 // Resident factorization CTAs on the current device (SMs x CTAs per SM), 0 on error.
