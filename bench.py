@@ -37,11 +37,11 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BATCH_COUNT = 2048
 # DRAM bytes (read + write) per nominal flop of the two executors, from one ncu capture
 # each of the unchanged kernels on smaller inputs of the same kind (the tensor-core
-# executor on a 24576 x 2048 matrix: 10.773 GB for 2.004e11 nominal flops, traffic
+# executor on a 24576 x 2048 matrix: 14.750 GB for 2.004e11 nominal flops, traffic
 # growing with the number of tile updates as the flops do; the batched FP32 executor on
-# the first 256 matrices of the batch: 1.331 GB for 4.907e10 flops).
-MIXED_TRAFFIC_PER_FLOP = 10.773e9 / 2.004e11
-BATCH_TRAFFIC_PER_FLOP = 1.331e9 / 4.907e10
+# the first 256 matrices of the batch: 1.328 GB for 4.907e10 flops).
+MIXED_TRAFFIC_PER_FLOP = 14.750e9 / 2.004e11
+BATCH_TRAFFIC_PER_FLOP = 1.328e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
 # Mean task durations (us) of the tensor-core executor on GB300 (GEQRT, TTQRT, UNMQR,
 # TTMQR at nb 128, bf16x6): the weights of the library's default claim order for the
