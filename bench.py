@@ -583,6 +583,10 @@ def main_gpu(args):
                      "bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                      "frac": achieved / bf16_sust, "traffic": flops * MIXED_TRAFFIC_PER_FLOP,
                      "traffic_note": "bytes per launch, ncu capture at 24576x2048 scaled by nominal flops",
+                     "algorithmic_bytes": tile_task_bytes(args),
+                     "algorithmic_bytes_note": "tile-task traffic: C tiles read and written by every task that "
+                                               "updates them, split operand images written once and read by "
+                                               "every update (no reuse in L2 assumed); A alone is 8mn bytes",
                      "peak_source": f"{peak_src} bf16 dense sustained (MEASURED_PEAKS.json)",
                      "flops_per_launch": flops, "avg_launch_ms": fac_avg},
         "ls_optimality": {"mixed": eta_mixed, "fp64": eta64, "target": tol},
@@ -604,6 +608,21 @@ def main_gpu(args):
     if rank == 0:
         print(json.dumps(line))
     replicas.finalize()
+
+
+def tile_task_bytes(args):
+    """Algorithmic bytes of one tensor-core factorization as a tile-task graph (nb 128, FP32
+    tiles of 64 KB, split operand images of nparts x 32 KB): every update reads and writes its
+    C tile(s) and reads its operand images (UNMQR: V, Z; TTMQR: V2, Z2, T^T); every panel task
+    reads and writes its tile (TTQRT: two triangles) and writes its images and T (16 KB).
+    A tile touched by consecutive tasks is counted each time: this is the traffic of the
+    method when no tile stays in L2 between tasks."""
+    import paper_1303_3182_gb300 as tqr
+    nparts = {"bf16": 1, "fp16": 1, "bf16x3": 2, "bf16x6": 3}[args.prec]
+    tile, img, tblk = 128 * 128 * 4, nparts * 128 * 128 * 2, 32 * 128 * 4
+    c = tqr.plan_stats(args.m, args.n, 128, args.tree, 4)
+    return (c["UNMQR"] * (2 * tile + 2 * img) + c["TTMQR"] * (4 * tile + 3 * img)
+            + c["GEQRT"] * (2 * tile + 2 * img + tblk) + c["TTQRT"] * (2 * tile + 3 * img + tblk))
 
 
 def schedule_bound(args, executor_ms):
