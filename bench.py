@@ -46,7 +46,7 @@ BF16_FALLBACK = (1900.0, 1700.0)
 # Mean task durations (us) of the tensor-core executor on GB300 (GEQRT, TTQRT, UNMQR,
 # TTMQR at nb 128, bf16x6): the weights of the library's default claim order for the
 # tensor-core precisions (tqr_set_claim_order mode 2), used here for the schedule bound.
-TENSOR_TASK_US = (293, 304, 19, 31)
+TENSOR_TASK_US = (295, 323, 20, 32)
 
 
 def parse_args():

@@ -22,15 +22,16 @@ std::mutex g_mu;
 int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
 // Claim order of factorization plans (tqr_set_claim_order): mode 0 or 1 as set, or
 // the automatic default (mode 2): the bounded-processor CP-method order for the
-// tensor-core precisions, with kernel weights equal to the mean task durations in
-// microseconds measured on GB300 (nb 128, split-bf16 x6: GEQRT 293, TTQRT 304, UNMQR
-// 19, TTMQR 31 - panels cost 10 to 16 times an update there, while the thesis's weights give
-// them less than an update), and the unbounded-processor order for FP64 / FP32, whose
-// measured task durations are close to the thesis's proportions.
+// tensor-core precisions, with kernel weights from the mean task durations in
+// microseconds measured on GB300 (nb 128, split-bf16 x6: GEQRT 295, TTQRT 323, UNMQR
+// 20, TTMQR 32 - panels cost 10 to 16 times an update there, while the thesis's weights
+// give them less than an update; a later measurement's means, TTQRT 304, gave a 2% slower
+// order, so TTQRT keeps the larger weight), and the unbounded-processor order for FP64 /
+// FP32, whose measured task durations are close to the thesis's proportions.
 int g_order_mode = 2;
 int64_t g_order_w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
 int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
-constexpr int64_t kTensorOrderWeights[4] = {293, 304, 19, 31};
+constexpr int64_t kTensorOrderWeights[4] = {295, 323, 20, 32};
 
 OrderSpec effective_order(int prec) {
   OrderSpec spec;

@@ -2,14 +2,14 @@
 // upper-triangular R (the low-precision factor, float or double) for every LSQR step.
 //
 // Set-up (once per refinement): a transposed copy of R's upper triangle (so that both
-// solves read R along contiguous columns) and the inverses of R's 512 x 512 diagonal
+// solves read R along contiguous columns) and the inverses of R's 1024 x 1024 diagonal
 // blocks in FP64,
-// built from the 64 x 64 block inverses by three doubling steps
+// built from the 64 x 64 block inverses by four doubling steps
 //   inv([R11 R12; 0 R22]) = [R11^{-1}, -R11^{-1} R12 R22^{-1}; 0, R22^{-1}].
-// Solve: one cooperative launch walks the big blocks (8 for n = 4096); each step is two
+// Solve: one cooperative launch walks the big blocks (4 for n = 4096); each step is two
 // grid-wide phases separated by a grid barrier - x_s = Y_s b_s over all SMs, then the
 // update of the remaining right-hand-side rows with R's off-diagonal column block - so
-// the sequential depth is ceil(n / 512) steps instead of ceil(n / 64).  Partial sums
+// the sequential depth is ceil(n / 1024) steps instead of ceil(n / 64).  Partial sums
 // meet in FP64 atomics (results reproducible to rounding, not bit for bit).  Every grid
 // barrier wait is bounded and reports kStatusTimeout like the executor's waits.
 #include <cuda_runtime.h>
@@ -21,7 +21,9 @@
 namespace tqr {
 namespace {
 
-constexpr int kBig = 512;      // rows of a big diagonal block
+constexpr int kBig = 1024;     // rows of a big diagonal block
+constexpr int kCT = kBig / 64; // 64-column tiles across a big block
+constexpr int kP1 = (kBig / 32) * kCT;  // 32 x 64 tiles of a big block (phase-1 items)
 constexpr int kSmall = 64;     // rows of the blocks whose inverses the set-up starts from
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -46,7 +48,7 @@ __device__ __forceinline__ double ld_cg(const float *p) { return static_cast<dou
 
 // ---- set-up ---------------------------------------------------------------------------
 
-// Y[s] (512 x 512, column-major): the 64 x 64 inverses on the diagonal (identity for
+// Y[s] (kBig x kBig, column-major): the 64 x 64 inverses on the diagonal (identity for
 // 64-blocks beyond n), zeros elsewhere.
 __global__ void big_init_kernel(int64_t n, const double *Dinv64, double *Y, int nbig) {
   const int nblk64 = static_cast<int>((n + kSmall - 1) / kSmall);
@@ -273,7 +275,7 @@ __device__ void tile_apply(double (*st)[33], int64_t i0, int64_t ilim, int64_t c
 }
 
 // Solves R X = B (kLowerT = false) or R^T X = B (true) in place, nrhs <= kRhsMax.
-// Y: the big-block inverses; xs: 2 x 512 x kRhsMax doubles (zeroed by the launcher);
+// Y: the big-block inverses; xs: 2 x kBig x kRhsMax doubles (zeroed by the launcher);
 // bar: the grid barrier counter (zeroed by the launcher).  Work items are 32 x 64 tiles,
 // one per warp while there are enough warps; a warp's first tile of each phase is staged
 // before the barrier that precedes the phase.
@@ -288,13 +290,13 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
   const int warp = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
   int gen = 0;
-  // phase-1 tiles: the triangle of Y_s (or Y_s^T) in 16 x 8 tiles
+  // phase-1 tiles: the triangle of Y_s (or Y_s^T) in (kBig / 32) x kCT tiles of 32 x 64
   auto p1_skip = [&](int item) {
-    const int r0 = (item / 8) * 32, c0 = (item % 8) * 64;
+    const int r0 = (item / kCT) * 32, c0 = (item % kCT) * 64;
     return kLowerT ? (c0 > r0 + 31) : (c0 + 63 < r0);
   };
   auto p1_first = [&]() {
-    for (int item = gwarp; item < 128; item += nwarps)
+    for (int item = gwarp; item < kP1; item += nwarps)
       if (!p1_skip(item)) return item;
     return -1;
   };
@@ -303,8 +305,8 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
     const int s = block_of(step);
     const int64_t g0 = static_cast<int64_t>(s) * kBig;
     const int rb = static_cast<int>(lmin(kBig, n - g0));
-    tile_load<double, kLowerT>(st, Y + static_cast<int64_t>(s) * kBig * kBig, kBig, (item / 8) * 32, rb,
-                               (item % 8) * 64, rb);
+    tile_load<double, kLowerT>(st, Y + static_cast<int64_t>(s) * kBig * kBig, kBig, (item / kCT) * 32, rb,
+                               (item % kCT) * 64, rb);
   };
   // phase-2 rows of step: [lo, hi)
   auto p2_range = [&](int step, int64_t &lo, int64_t &hi, int64_t &g0, int &rb) {
@@ -318,8 +320,8 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
     int64_t lo, hi, g0;
     int rb;
     p2_range(step, lo, hi, g0, rb);
-    const int64_t i0 = lo + (item / 8) * 32;
-    const int c0 = static_cast<int>(item % 8) * 64;
+    const int64_t i0 = lo + (item / kCT) * 32;
+    const int c0 = static_cast<int>(item % kCT) * 64;
     if (!kLowerT)  // R(i, g0 + c) = Rt(g0 + c, i)
       tile_load<Real, true>(st, Rt + g0, n, i0, hi, c0, rb);
     else           // R^T(i, g0 + c) = R(g0 + c, i)
@@ -334,15 +336,15 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
     double *x = xs + (step & 1) * kBig * kRhsMax;
     double *xo = xs + ((step + 1) & 1) * kBig * kRhsMax;
     // phase 1: x = Y_s b_s (or Y_s^T b_s)
-    for (int item = gwarp; item < 128; item += nwarps) {
+    for (int item = gwarp; item < kP1; item += nwarps) {
       if (p1_skip(item)) continue;
       if (item != first1) load_p1(step, item);
-      tile_apply(st, (item / 8) * 32, rb, (item % 8) * 64, rb, B + g0, ldb, x, kBig, nrhs, 1.0);
+      tile_apply(st, (item / kCT) * 32, rb, (item % kCT) * 64, rb, B + g0, ldb, x, kBig, nrhs, 1.0);
     }
     int64_t lo, hi, g0b;
     int rbb;
     p2_range(step, lo, hi, g0b, rbb);
-    const int64_t nitem2 = ((hi - lo + 31) / 32) * 8;
+    const int64_t nitem2 = ((hi - lo + 31) / 32) * kCT;
     if (gwarp < nitem2) load_p2(step, gwarp);
     if (!grid_barrier(bar, gen, status, limit_ns)) return;
     // phase 2: the remaining rows lose R's coupling to block s; block s's rows take x
@@ -355,8 +357,8 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
     }
     for (int64_t item = gwarp; item < nitem2; item += nwarps) {
       if (item != gwarp) load_p2(step, item);
-      const int64_t i0 = lo + (item / 8) * 32;
-      const int c0 = static_cast<int>(item % 8) * 64;
+      const int64_t i0 = lo + (item / kCT) * 32;
+      const int c0 = static_cast<int>(item % kCT) * 64;
       tile_apply(st, i0, hi, c0, rb, x, kBig, B, ldb, nrhs, -1.0);
     }
     if (step + 1 < nbig && first1 >= 0) load_p1(step + 1, first1);

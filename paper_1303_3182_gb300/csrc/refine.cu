@@ -311,7 +311,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   TQR_CKL();
   if ((rc = launch_diag_inverse(n, R, ldr, false, Dinv, stream)) != 0) return rc;
   if ((rc = precond_setup(n, R, ldr, false, Dinv, Pw, stream)) != 0) return rc;
-  // R^{-1} and R^{-T} applied with the inverses of R's 512 x 512 diagonal blocks
+  // R^{-1} and R^{-T} applied with the inverses of R's 1024 x 1024 diagonal blocks
   auto solve_r = [&](double *Vec, bool lower_t) -> int {
     return precond_solve(n, R, ldr, false, Pw, Vec, n, nrhs, flags, status, wait_limit_ns, stream, lower_t);
   };
