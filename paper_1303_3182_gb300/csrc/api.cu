@@ -22,16 +22,18 @@ std::mutex g_mu;
 int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
 // Claim order of factorization plans (tqr_set_claim_order): mode 0 or 1 as set, or
 // the automatic default (mode 2): the bounded-processor CP-method order for the
-// tensor-core precisions, with kernel weights from the mean task durations in
-// microseconds measured on GB300 (nb 128, split-bf16 x6: GEQRT 295, TTQRT 323, UNMQR
-// 20, TTMQR 32 - panels cost 10 to 16 times an update there, while the thesis's weights
-// give them less than an update; a later measurement's means, TTQRT 304, gave a 2% slower
-// order, so TTQRT keeps the larger weight), and the unbounded-processor order for FP64 /
-// FP32, whose measured task durations are close to the thesis's proportions.
+// tensor-core precisions, with kernel weights GEQRT 330, TTQRT 360, UNMQR 20, TTMQR 32.
+// They come from the mean task durations in microseconds measured on GB300 (nb 128,
+// split-bf16 x6: about 295, 305-323, 20, 32 - panels cost 10 to 16 times an update there,
+// while the thesis's weights give them less than an update), tuned on the 32768 x 4096
+// factorization: a sweep of the panel weights found this set fastest (76.3 ms; the raw
+// means 293/304/19/31 gave 78.5 ms, panel weights off the ratio TTQRT/GEQRT ~ 1.1 up to
+// 80.9 ms).  FP64 / FP32 keep the unbounded-processor order: their measured task
+// durations are close to the thesis's proportions and the bounded order gained nothing.
 int g_order_mode = 2;
 int64_t g_order_w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
 int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
-constexpr int64_t kTensorOrderWeights[4] = {295, 323, 20, 32};
+constexpr int64_t kTensorOrderWeights[4] = {330, 360, 20, 32};
 
 OrderSpec effective_order(int prec) {
   OrderSpec spec;
