@@ -37,16 +37,18 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BATCH_COUNT = 2048
 # DRAM bytes (read + write) per nominal flop of the two executors, from one ncu capture
 # each of the unchanged kernels on smaller inputs of the same kind (the tensor-core
-# executor on a 24576 x 2048 matrix: 14.750 GB for 2.004e11 nominal flops, traffic
+# executor on a 24576 x 2048 matrix: 14.656 GB for 2.004e11 nominal flops, traffic
 # growing with the number of tile updates as the flops do; the batched FP32 executor on
 # the first 256 matrices of the batch: 1.328 GB for 4.907e10 flops).
-MIXED_TRAFFIC_PER_FLOP = 14.750e9 / 2.004e11
+MIXED_TRAFFIC_PER_FLOP = 14.656e9 / 2.004e11
 BATCH_TRAFFIC_PER_FLOP = 1.328e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
-# Kernel weights (us) of the library's default claim order for the tensor-core precisions
+# Kernel weights of the library's default claim order for the tensor-core precisions
 # (tqr_set_claim_order mode 2: GEQRT, TTQRT, UNMQR, TTMQR at nb 128, bf16x6; measured task
-# durations with tuned panel weights), used here for the schedule bound.
-TENSOR_TASK_US = (330, 360, 20, 32)
+# durations with tuned panel weights), and the mean task durations (us) of the same
+# executor from a per-task trace on GB300 (32768 x 4096), the weights of the schedule bound.
+TENSOR_CLAIM_WEIGHTS = (330, 360, 20, 32)
+TENSOR_TASK_MEAN_US = (293, 304, 19, 31)
 
 
 def parse_args():
@@ -635,11 +637,14 @@ def schedule_bound(args, executor_ms):
     import paper_1303_3182_gb300 as tqr
     nproc = torch.cuda.get_device_properties(0).multi_processor_count
     p, q = -(-args.m // 128), -(-args.n // 128)
-    ms, bound, lost = tqr.schedule(p, q, args.tree, 4, nproc, TENSOR_TASK_US)
+    ms, bound, lost = tqr.schedule(p, q, args.tree, 4, nproc, TENSOR_TASK_MEAN_US)
     return {"claim_order": "CP-method list schedule on the resident CTAs (library default for tensor-core "
-                           "precisions)", "processors": nproc, "weights_us": list(TENSOR_TASK_US),
+                           "precisions)", "claim_weights": list(TENSOR_CLAIM_WEIGHTS), "processors": nproc,
+            "task_mean_us": list(TENSOR_TASK_MEAN_US),
             "list_schedule_ms": ms / 1e3, "alap_bound_ms": bound / 1e3, "executor_ms": executor_ms,
-            "executor_over_alap_bound": executor_ms / (bound / 1e3)}
+            "executor_over_alap_bound": executor_ms / (bound / 1e3),
+            "note": "list schedule and ALAP Derived bound of the task graph with the measured mean task "
+                    "durations as weights"}
 
 
 def main():
