@@ -37,7 +37,8 @@ def to_dev(a):
 
 # kappa * u of the factorization must stay below ~1 for R to precondition A well
 # (u = 2^-8 for bf16, 2^-11 fp16, ~2^-16 bf16 x3, 2^-24 fp32); harder cases need far
-# more refinement iterations.
+# more refinement iterations (the preconditioned operator A R^-1 then has a condition
+# number of order kappa * u, and LSQR's iteration count grows with it).
 CASES = [(prec, m, n, nrhs, cond, noise)
          for prec, conds in (("bf16x6", (1e4, 1e6)), ("bf16x3", (1e4, 1e6)), ("fp32", (1e4, 1e6)), ("fp16", (1e2, 1e3)),
                              ("bf16", (1e1, 1e2)))
