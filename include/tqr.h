@@ -108,10 +108,10 @@ int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weigh
  *           processors as the executor keeps resident CTAs, with the given per-kind
  *           weights (GEQRT, TTQRT, UNMQR, TTMQR; each >= 1; NULL = 4, 2, 6, 6), e.g.
  *           measured task durations of the chosen precision.
- *   mode 2 (default): mode 1 with built-in weights for the tensor-core precisions
- *           (330, 360, 20, 32: task durations in microseconds measured on GB300 at nb
- *           128, the panel weights tuned on a 32768 x 4096 factorization), mode 0 for
- *           TQR_FP64 and TQR_FP32.  weights is ignored.
+ *   mode 2 (default): mode 1 with built-in weights from task durations in
+ *           microseconds measured on GB300 - the tensor-core precisions 330, 360, 20, 32
+ *           (nb 128, panel weights tuned on a 32768 x 4096 factorization), TQR_FP64 5146,
+ *           4249, 6394, 6369 (nb 256) - and mode 0 for TQR_FP32.  weights is ignored.
  * Every order is topological, so the executor's dependency waits always end.
  * Host only.  Errors: -1 unknown mode, -2 a weight < 1. */
 int tqr_set_claim_order(int mode, const int64_t *weights);

@@ -176,7 +176,7 @@ def set_claim_order(mode: int, weights=None) -> None:
     """Executor claim order of later factorization plans: 0 = earliest start on unbounded
     processors, 1 = start order of the bounded-processor CP-method schedule with the given
     kernel weights (GEQRT, TTQRT, UNMQR, TTMQR), 2 = the default (1 with built-in GB300
-    weights for the tensor-core precisions, 0 otherwise)."""
+    weights for the tensor-core precisions and fp64, 0 for fp32)."""
     _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))
 
 

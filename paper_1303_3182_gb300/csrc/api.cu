@@ -21,28 +21,39 @@ namespace {
 std::mutex g_mu;
 int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
 // Claim order of factorization plans (tqr_set_claim_order): mode 0 or 1 as set, or
-// the automatic default (mode 2): the bounded-processor CP-method order for the
-// tensor-core precisions, with kernel weights GEQRT 330, TTQRT 360, UNMQR 20, TTMQR 32.
-// They come from the mean task durations in microseconds measured on GB300 (nb 128,
-// split-bf16 x6: about 295, 305-323, 20, 32 - panels cost 10 to 16 times an update there,
-// while the thesis's weights give them less than an update), tuned on the 32768 x 4096
-// factorization: a sweep of the panel weights found this set fastest (76.3 ms; the raw
-// means 293/304/19/31 gave 78.5 ms, panel weights off the ratio TTQRT/GEQRT ~ 1.1 up to
-// 80.9 ms).  FP64 / FP32 keep the unbounded-processor order: their measured task
-// durations are close to the thesis's proportions and the bounded order gained nothing.
+// the automatic default (mode 2): the bounded-processor CP-method order with built-in
+// kernel weights (GEQRT, TTQRT, UNMQR, TTMQR) for the tensor-core precisions and FP64,
+// the unbounded-processor order for FP32.  The weights come from task durations in
+// microseconds measured on GB300:
+//   tensor cores (nb 128, split-bf16 x6): about 295, 305-323, 20, 32 - panels cost 10 to
+//   16 times an update there, while the thesis's weights give them less than an update;
+//   the panel weights were tuned on the 32768 x 4096 factorization (330, 360: 76.3 ms;
+//   the plain means 293/304/19/31 gave 78.5 ms, other TTQRT/GEQRT ratios up to 80.9 ms);
+//   FP64 (nb 256): 5146, 4249, 6394, 6369 - with them FlatTree's 32768 x 4096
+//   factorization takes 1488 ms instead of 1635 ms with the unbounded order (its ALAP
+//   Derived bound is 1468 ms), Greedy's 1448 ms against 1443 ms (bound 1424 ms).
 int g_order_mode = 2;
 int64_t g_order_w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
 int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
 constexpr int64_t kTensorOrderWeights[4] = {330, 360, 20, 32};
+constexpr int64_t kFp64OrderWeights[4] = {5146, 4249, 6394, 6369};
 
 OrderSpec effective_order(int prec) {
   OrderSpec spec;
+  const int64_t *w = nullptr;
   if (g_order_mode == 1) {
-    spec.mode = 1;
-    for (int c = 0; c < 4; ++c) spec.w[c] = g_order_w[c];
+    w = g_order_w;
+    spec.id = 1 + g_order_gen;
   } else if (g_order_mode == 2 && is_tensor_prec(prec)) {
+    w = kTensorOrderWeights;
+    spec.id = -1;
+  } else if (g_order_mode == 2 && prec == TQR_FP64) {
+    w = kFp64OrderWeights;
+    spec.id = -2;
+  }
+  if (w) {
     spec.mode = 1;
-    for (int c = 0; c < 4; ++c) spec.w[c] = kTensorOrderWeights[c];
+    for (int c = 0; c < 4; ++c) spec.w[c] = w[c];
   }
   return spec;
 }
@@ -147,13 +158,11 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   if (order) spec = *order;
   spec.nproc = std::max(1, spec.nproc);
   const bool bounded = kind == 0 && spec.mode == 1;
-  // the order's identity: user weights carry the setting's generation, the built-in
-  // tensor-core weights a key of their own
-  const bool builtin = bounded && g_order_mode == 2;
-  // a plan built with the test hook is never reused: it gets a key of its own
+  // the order's identity (spec.id: user weights carry the setting's generation, each
+  // built-in weight set a negative key of its own) is part of the key; a plan built with
+  // the test hook is never reused: it gets a key of its own
   const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : kind, P, Q, tree,
-                    tree == TQR_PLASMA ? bs : 0, bounded ? (builtin ? -1 : 1 + g_order_gen) : 0,
-                    bounded ? spec.nproc : 0};
+                    tree == TQR_PLASMA ? bs : 0, bounded ? spec.id : 0, bounded ? spec.nproc : 0};
   auto it = g_plans.find(key);
   if (it != g_plans.end()) {
     *out = it->second.get();

@@ -97,6 +97,7 @@ struct OrderSpec {
   int mode = 0;
   int nproc = 1;
   int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+  int id = 0;  // identity of the weight set in the plan cache (built-in sets < 0)
 };
 void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1, const OrderSpec *order = nullptr);
 // Tasks of the sequential program (all panels, in column order) added to b.
