@@ -119,7 +119,8 @@ struct Plan {
 };
 
 // kind 0 = factorization, 1 = apply Q^T, 2 = apply Q
-// device, kind, P, Q, tree, bs, claim-order generation (0: default order), processors
+// device, kind, P, Q, tree, bs, claim-order identity (0: unbounded order; < 0: a built-in
+// weight set; > 0: the generation of a user setting), processors
 using PlanKey = std::tuple<int, int, int, int, int, int, int, int>;
 std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
 

@@ -16,8 +16,11 @@
 // Reflector conventions (LAPACK): H = I - tau v v^T, v(0) = 1, beta = -sign(alpha) *
 // ||[alpha; x]||, tau = (beta - alpha) / beta, v = x / (alpha - beta), tau = 0 when
 // x = 0.  T factors: compact-WY (Schreiber & Van Loan, 1989), blocks of ib reflectors,
-// stored ib x nb per factored tile (block b in columns b*ib..).  Householder norms,
-// beta, tau and the scaling of v are computed in FP64 for every storage precision.
+// stored ib x nb per factored tile (block b in columns b*ib..).  Householder sums of
+// squares are FP64-accurate for every storage precision (FP32 storage accumulates them
+// with error-free FP32 transformations); beta, tau and the scaling of v are formed in
+// FP64 for FP64 storage and, from that sum, in FP32 for FP32 storage (FP64 outside the
+// range where FP32 keeps full precision).
 #pragma once
 
 #include <cuda_runtime.h>
