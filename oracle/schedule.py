@@ -28,7 +28,10 @@ priority go to the task that comes first in the sequential program; the backward
 the lost area stops where more than p processors are needed ("more processors needed to
 keep the critical path length constant").  With these, the CP-method makespans and the
 ALAP Derived bounds of Table "Schedule lengths for matrix of 5x5 tiles" are reproduced
-except three cells (see tests/golden/schedule_5x5.txt).
+except three cells (see tests/golden/schedule_5x5.txt), and the lost areas of the thesis's
+own 5 x 5 tiled Cholesky example (Figure "ALAP execution for 5 x 5 tiles": 0, 4, 11, 24, 45
+for 1..5 processors; stopping at "p or more active tasks" would give 40 for 5) with the
+unrounded bounds of its Table "Upper bound on speedup and efficiency for 5x5 tiles".
 """
 from __future__ import annotations
 

@@ -94,3 +94,35 @@ def test_alap_bound_limits():
     tseq, cp = sum(g.weight), S.critical_path(g)
     assert S.alap_bound(g, 1) == (tseq, 0)
     assert S.alap_bound(g, len(g))[0] == cp
+
+
+def _tiled_cholesky(t):
+    """Task graph of the right-looking tiled Cholesky factorization of t x t tiles (one region
+    per tile), weights POTRF 1, TRSM 3, SYRK 3, GEMM 6: the thesis's own example for the ALAP
+    Derived bound (the procedure is the same for any task graph)."""
+    g = S.TaskGraph()
+    for k in range(t):
+        g.add(0, ("POTRF", k), 1, [], [(k, k)])
+        for i in range(k + 1, t):
+            g.add(1, ("TRSM", i, k), 3, [(k, k)], [(i, k)])
+        for i in range(k + 1, t):
+            g.add(2, ("SYRK", i, k), 3, [(i, k)], [(i, i)])
+            for j in range(k + 1, i):
+                g.add(3, ("GEMM", i, j, k), 6, [(i, k), (j, k)], [(i, j)])
+    return g
+
+
+def test_alap_lost_area_cholesky_5x5_figure_and_table():
+    """The lost areas of the ALAP execution (walking back until more than p tasks are
+    active) and the unrounded bound (T_seq + LA_p) / p of the thesis's 5 x 5 Cholesky example."""
+    g = _tiled_cholesky(5)
+    tseq, cp = sum(g.weight), S.critical_path(g)
+    assert (tseq, cp) == (125, 35)
+    path = os.path.join(os.path.dirname(__file__), "golden", "alap_cholesky_5x5.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    for procs, la, tp in rows:
+        p = int(procs)
+        _, lost = S.alap_bound(g, p)
+        if la != "-":
+            assert lost == int(la), p
+        assert round(max(cp, (tseq + lost) / p), 2) == float(tp), p
