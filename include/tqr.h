@@ -327,9 +327,20 @@ void tqr_finalize(void);               /* free every cached plan                
  *   #edges, critical path in units (same weights as tqr_elimlist).
  * tqr_debug_drop_edge: when set to e >= 0, the next plan built omits the release of
  *   its e-th dependency edge, so that a wait can never finish; used to check that the
- *   kernel returns TQR_ETIMEOUT instead of hanging.  -1 (default) disables it. */
+ *   kernel returns TQR_ETIMEOUT instead of hanging.  -1 (default) disables it.
+ * tqr_debug_claim_order: the executor (claim) order of the factorization task graph of a
+ *   p x q tile matrix, built as a plan is: mode 0 = earliest start on unbounded
+ *   processors, mode 1 = start order of the CP-method list schedule on nproc processors
+ *   with the four kernel weights (NULL = 4, 2, 6, 6; see tqr_set_claim_order).  tasks
+ *   receives 5 int32 per task in claim order: kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR),
+ *   i, piv (-1 if none), k, j (-1 if none); NULL to query the count.  ntask: in =
+ *   capacity in tasks, out = number of tasks.  Host only.  Errors: -1/-2 p or q < 1,
+ *   -3 unknown tree, -4 bs < 1 for PlasmaTree, -5 mode not 0 or 1, -6 nproc < 1, -7 a
+ *   weight < 1, -8 ntask NULL or capacity too small while tasks != NULL. */
 int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6]);
 void tqr_debug_drop_edge(int64_t e);
+int tqr_debug_claim_order(int p, int q, int tree, int bs, int mode, int nproc, const int64_t *weights,
+                          int32_t *tasks, int64_t *ntask);
 
 #ifdef __cplusplus
 }

@@ -51,6 +51,8 @@ def lib() -> ctypes.CDLL:
             "tqr_elimlist": (i32, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), c_i64p, c_i64p]),
             "tqr_schedule": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
             "tqr_set_claim_order": (i32, [i32, c_i64p]),
+            "tqr_debug_claim_order": (i32, [i32, i32, i32, i32, i32, i32, c_i64p, ctypes.POINTER(ctypes.c_int32),
+                                             c_i64p]),
             "tqr_workspace_size": (i32, [i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
             "tqr_factor": (i32, [i64, i64, i32, i32, i32, i32, i32, vp, i64, vp, vp]),
             "tqr_apply_qt": (i32, [i64, i64, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp, i64, i64, vp]),
@@ -178,6 +180,20 @@ def set_claim_order(mode: int, weights=None) -> None:
     kernel weights (GEQRT, TTQRT, UNMQR, TTMQR), 2 = the default (1 with built-in GB300
     weights for the tensor-core precisions and fp64, 0 for fp32)."""
     _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))
+
+
+def claim_order(p: int, q: int, tree="greedy", bs: int = 1, mode: int = 0, nproc: int = 1, weights=None):
+    """The executor's claim order of a p x q factorization task graph (test hook): an
+    (ntask, 5) int32 array of (kind, i, piv, k, j) rows in claim order."""
+    L = lib()
+    n = ctypes.c_int64(0)
+    _check("tqr_debug_claim_order", L.tqr_debug_claim_order(p, q, _tree(tree), bs, mode, nproc, _weights4(weights),
+                                                            None, ctypes.byref(n)))
+    arr = np.zeros((max(n.value, 1), 5), dtype=np.int32)
+    _check("tqr_debug_claim_order", L.tqr_debug_claim_order(p, q, _tree(tree), bs, mode, nproc, _weights4(weights),
+                                                            arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                            ctypes.byref(n)))
+    return arr[:n.value]
 
 
 def plan_stats(m: int, n: int, nb: int, tree="greedy", bs: int = 1):

@@ -762,4 +762,48 @@ void tqr_debug_drop_edge(int64_t e) {
   g_drop_edge = e;
 }
 
+int tqr_debug_claim_order(int p, int q, int tree, int bs, int mode, int nproc, const int64_t *weights,
+                          int32_t *tasks, int64_t *ntask) {
+  if (p < 1) return -1;
+  if (q < 1) return -2;
+  if (tree < TQR_FLAT || tree > TQR_ASAP) return -3;
+  if (tree == TQR_PLASMA && bs < 1) return -4;
+  if (mode != 0 && mode != 1) return -5;
+  if (nproc < 1) return -6;
+  if (!ntask) return -8;
+  OrderSpec spec;
+  spec.mode = mode;
+  spec.nproc = nproc;
+  if (weights)
+    for (int c = 0; c < 4; ++c) {
+      if (weights[c] < 1) return -7;
+      spec.w[c] = weights[c];
+    }
+  try {
+    std::vector<Elim> elims;
+    elimination_list(p, q, tree, bs, elims);
+    Graph g;
+    build_factor_graph(p, q, elims, g, -1, mode == 1 ? &spec : nullptr);
+    const int64_t n = static_cast<int64_t>(g.tasks.size());
+    if (tasks) {
+      if (*ntask < n) return -8;
+      for (int64_t t = 0; t < n; ++t) {
+        const Task &x = g.tasks[t];
+        tasks[5 * t + 0] = x.kind;
+        tasks[5 * t + 1] = x.i;
+        tasks[5 * t + 2] = x.piv;
+        tasks[5 * t + 3] = x.k;
+        tasks[5 * t + 4] = x.j;
+      }
+    }
+    *ntask = n;
+  } catch (const std::bad_alloc &) {
+    return TQR_ENOMEM;
+  } catch (...) {
+    g_last_error = "internal error in tqr_debug_claim_order";
+    return TQR_ECUDA;
+  }
+  return TQR_OK;
+}
+
 }  // extern "C"

@@ -67,3 +67,36 @@ def test_invalid_arguments():
     assert L.tqr_set_claim_order(1, tqr._weights4((1, 2, -3, 4))) == -2
     assert L.tqr_set_claim_order(0, None) == 0
     assert L.tqr_set_claim_order(2, None) == 0
+
+
+def _oracle_index(g):
+    names = {S.GEQRT: "GEQRT", S.TTQRT: "TTQRT", S.UNMQR: "UNMQR", S.TTMQR: "TTMQR"}
+    return {(names[g.kind[t]],) + tuple(g.key[t]): t for t in range(len(g))}
+
+
+def _lib_order_as_oracle_indices(order, index):
+    out = []
+    for kind, i, piv, k, j in order.tolist():
+        key = {0: ("GEQRT", i, k), 1: ("TTQRT", i, piv, k), 2: ("UNMQR", i, k, j), 3: ("TTMQR", i, piv, k, j)}[kind]
+        out.append(index[key])
+    return out
+
+
+@pytest.mark.parametrize("p,q,tree,bs", [(5, 5, "greedy", 1), (9, 4, "flat", 1), (12, 5, "plasma", 3),
+                                         (8, 8, "fibonacci", 1), (13, 6, "grasap", 1), (7, 3, "binary", 1)])
+def test_claim_orders_equal_the_oracle_schedules(p, q, tree, bs):
+    """The executor's claim order: mode 1 is the start order of the CP-method list schedule
+    (start time, then larger Backflow priority, then program order), mode 0 the same for
+    unbounded processors with the thesis weights; both are topological."""
+    rng = random.Random(p * 100 + q)
+    elims = E.elimination_list(p, q, TREES[tree], bs=bs)
+    for mode, nproc, weights in [(0, 1, None), (1, 3, None), (1, 17, (30, 32, 2, 3)),
+                                 (1, rng.randint(2, 40), tuple(rng.randint(1, 50) for _ in range(4)))]:
+        g = S.task_graph(p, q, elims, weights or S.DEFAULT_WEIGHTS)
+        order = _lib_order_as_oracle_indices(tqr.claim_order(p, q, tree, bs, mode, nproc, weights), _oracle_index(g))
+        assert sorted(order) == list(range(len(g)))
+        pos = {t: r for r, t in enumerate(order)}
+        assert all(pos[d] < pos[t] for t in range(len(g)) for d in g.preds[t])
+        prio = S.bottom_levels(g)
+        _, start = S.list_schedule(g, nproc if mode == 1 else len(g))
+        assert order == sorted(range(len(g)), key=lambda t: (start[t], -prio[t], t))
