@@ -100,3 +100,19 @@ def test_claim_orders_equal_the_oracle_schedules(p, q, tree, bs):
         prio = S.bottom_levels(g)
         _, start = S.list_schedule(g, nproc if mode == 1 else len(g))
         assert order == sorted(range(len(g)), key=lambda t: (start[t], -prio[t], t))
+
+
+def test_bench_tile_task_bytes_match_the_oracle_kernel_counts():
+    """bench.py's algorithmic bytes of the tensor-core factorization (tile-task traffic) from
+    the library's plan statistics equal the same sum over the oracle's kernel counts."""
+    import bench
+
+    class Args:
+        m, n, tree, prec = 32768, 4096, "greedy", "bf16x6"
+
+    p, q = 256, 32
+    c = E.kernel_counts(p, q, E.elimination_list(p, q, E.GREEDY))
+    tile, img, tblk = 128 * 128 * 4, 3 * 128 * 128 * 2, 32 * 128 * 4
+    want = (c["UNMQR"] * (2 * tile + 2 * img) + c["TTMQR"] * (4 * tile + 3 * img)
+            + c["GEQRT"] * (2 * tile + 2 * img + tblk) + c["TTQRT"] * (2 * tile + 3 * img + tblk))
+    assert bench.tile_task_bytes(Args) == want
