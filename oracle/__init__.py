@@ -7,8 +7,10 @@ the library; the two share only the seeded generators of ``synthetic``.
 
 * ``elimlists``  - the elimination-list generators, the validity conditions, the tile
   task graph and its critical path (integer-exact).
-* ``householder`` - unblocked FP64 Householder QR, the four TT tile kernels applied one
-  reflector at a time, the tiled algorithm, apply-Q, back substitution, least squares.
+* ``householder`` - unblocked FP64 Householder QR, the TT tile kernels and the TS
+  kernels TSQRT/TSMQR applied one reflector at a time, the tiled algorithm (TT form,
+  and the TS form of a list: TS kernels for the rows that never pivot in a column),
+  apply-Q, back substitution, least squares.
 * ``refine``     - FP64 least-squares checks (backward error, residual).
 * ``schedule``   - bounded-processor scheduling of the task graph (thesis Chapter 5):
   Backflow priorities, the CP-method list schedule, the ALAP Derived bound.

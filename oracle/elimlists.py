@@ -25,6 +25,8 @@ TREE_NAMES = {FLAT: "flat", PLASMA: "plasma", BINARY: "binary", FIBONACCI: "fibo
               GREEDY: "greedy", GRASAP: "grasap", ASAP: "asap"}
 
 W_GEQRT, W_TTQRT, W_UNMQR, W_TTMQR = 4, 2, 6, 6
+# TS (triangle on top of square) kernels, Table "Kernels for tiled QR"
+W_TSQRT, W_TSMQR = 6, 12
 
 
 def _v2(d: int) -> int:
@@ -200,22 +202,59 @@ class TileSchedule:
         return self.add(("TTMQR", i, piv, k, j), W_TTMQR, [(i, k, "U")],
                         [(piv, j, "L"), (piv, j, "U"), (i, j, "L"), (i, j, "U")])
 
+    def tsqrt(self, i, piv, k):
+        # the square tile (i, k) is overwritten as a whole by its reflectors
+        return self.add(("TSQRT", i, piv, k), W_TSQRT, [],
+                        [(piv, k, "U"), (i, k, "L"), (i, k, "U")])
 
-def _column_panel(sched: TileSchedule, p, q, k):
-    """GEQRT(i,k) then UNMQR(i,k,j) for every row i >= k of panel k."""
+    def tsmqr(self, i, piv, k, j):
+        return self.add(("TSMQR", i, piv, k, j), W_TSMQR, [(i, k, "L"), (i, k, "U")],
+                        [(piv, j, "L"), (piv, j, "U"), (i, j, "L"), (i, j, "U")])
+
+
+def _column_panel(sched: TileSchedule, p, q, k, skip=()):
+    """GEQRT(i,k) then UNMQR(i,k,j) for every row i >= k of panel k (except the rows in
+    skip, which a TS kernel zeroes while still square)."""
     g = {}
     for i in range(k, p):
+        if i in skip:
+            continue
         g[i] = sched.geqrt(i, k)
         for j in range(k + 1, q):
             sched.unmqr(i, k, j)
     return g
 
 
-def _column_elims(sched: TileSchedule, q, k, elims):
+def _column_elims(sched: TileSchedule, q, k, elims, ts_rows=()):
     for (_, i, piv) in elims:
-        sched.ttqrt(i, piv, k)
-        for j in range(k + 1, q):
-            sched.ttmqr(i, piv, k, j)
+        if i in ts_rows:
+            sched.tsqrt(i, piv, k)
+            for j in range(k + 1, q):
+                sched.tsmqr(i, piv, k, j)
+        else:
+            sched.ttqrt(i, piv, k)
+            for j in range(k + 1, q):
+                sched.ttmqr(i, piv, k, j)
+
+
+def ts_rows(elims):
+    """Rows zeroed by TS kernels in the TS form of a list: {k: set of rows}.
+
+    A TS elimination (Algorithm "elimSQ") zeroes a square tile, so its row must not
+    have been triangularized in that column; a pivot always is (GEQRT(piv,k) precedes
+    TSQRT).  The TS form of a list therefore zeroes with TSQRT/TSMQR every row that is
+    never a pivot in the column (a leaf of the column's tree) and keeps the TT kernels
+    for the rows that pivot before they are zeroed.  FlatTree's TS form is Sameh-Kuck
+    with TS kernels; PlasmaTree(BS)'s is the PLASMA algorithm (TS inside a domain, TT
+    between the domain heads)."""
+    piv_rows = {}
+    for (k, _, piv) in elims:
+        piv_rows.setdefault(k, set()).add(piv)
+    out = {}
+    for (k, i, _) in elims:
+        if i not in piv_rows.get(k, ()):
+            out.setdefault(k, set()).add(i)
+    return out
 
 
 def asap_column(p: int, k: int, ready: dict):
@@ -321,21 +360,22 @@ def check_valid(p: int, q: int, elims) -> None:
                 raise ValueError(f"tile {(i, k)} never zeroed")
 
 
-def schedule(p: int, q: int, elims) -> TileSchedule:
-    """Simulate the whole task graph of an elimination list."""
+def schedule(p: int, q: int, elims, ts: bool = False) -> TileSchedule:
+    """Simulate the whole task graph of an elimination list (its TS form when ts)."""
     sched = TileSchedule()
     by_col = {}
     for e in elims:
         by_col.setdefault(e[0], []).append(e)
+    tsr = ts_rows(elims) if ts else {}
     for k in range(min(p, q)):
-        _column_panel(sched, p, q, k)
-        _column_elims(sched, q, k, by_col.get(k, []))
+        _column_panel(sched, p, q, k, tsr.get(k, ()))
+        _column_elims(sched, q, k, by_col.get(k, []), tsr.get(k, ()))
     return sched
 
 
-def critical_path(p: int, q: int, elims) -> int:
+def critical_path(p: int, q: int, elims, ts: bool = False) -> int:
     """Weighted critical path (unit nb^3/3), the makespan with unbounded processors."""
-    return schedule(p, q, elims).makespan
+    return schedule(p, q, elims, ts).makespan
 
 
 def tiled_table(p: int, q: int, elims):
@@ -345,11 +385,21 @@ def tiled_table(p: int, q: int, elims):
     return {(i, k): sched.finish[("TTQRT", i, piv, k)] for (k, i, piv) in elims}
 
 
-def kernel_counts(p: int, q: int, elims):
-    """Number of tasks of each kernel in the task graph of the list."""
+def kernel_counts(p: int, q: int, elims, ts: bool = False):
+    """Number of tasks of each kernel in the task graph of the list (its TS form when
+    ts), enumerated from the column-by-column program."""
     kmax = min(p, q)
-    n_geqrt = sum(p - k for k in range(kmax))
-    n_unmqr = sum((p - k) * (q - 1 - k) for k in range(kmax))
-    n_ttqrt = len(elims)
-    n_ttmqr = sum(q - 1 - k for (k, _, _) in elims)
-    return {"GEQRT": n_geqrt, "TTQRT": n_ttqrt, "UNMQR": n_unmqr, "TTMQR": n_ttmqr}
+    tsr = ts_rows(elims) if ts else {}
+    c = {"GEQRT": 0, "TTQRT": 0, "UNMQR": 0, "TTMQR": 0, "TSQRT": 0, "TSMQR": 0}
+    for k in range(kmax):
+        panel_rows = (p - k) - len(tsr.get(k, ()))
+        c["GEQRT"] += panel_rows
+        c["UNMQR"] += panel_rows * (q - 1 - k)
+    for (k, i, _) in elims:
+        if i in tsr.get(k, ()):
+            c["TSQRT"] += 1
+            c["TSMQR"] += q - 1 - k
+        else:
+            c["TTQRT"] += 1
+            c["TTMQR"] += q - 1 - k
+    return c

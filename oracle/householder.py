@@ -1,4 +1,4 @@
-"""Plain FP64 Householder QR, the tiled TT algorithm, apply-Q and least squares.
+"""Plain FP64 Householder QR, the tiled TT / TS algorithms, apply-Q and least squares.
 
 Test infrastructure only: the CPU oracle for the numeric side of tiled QR.  Only the
 tests, the smoke check and the CPU-baseline leg of the benchmark use it; the library
@@ -14,7 +14,8 @@ LAPACK conventions are used, Section 1.3 and Section 3.1.1):
   v[1:] = x / (alpha - beta); tau = 0 and H = I when ||x|| = 0.
 * A factored tile keeps R in its upper triangle and the GEQRT reflectors below the
   diagonal (unit diagonal implicit).  TTQRT stores its reflectors in the upper triangle
-  of the zeroed tile: reflector c lives in rows 0..c of column c.
+  of the zeroed tile: reflector c lives in rows 0..c of column c.  TSQRT zeroes a
+  square tile and stores reflector c in the whole column c of that tile.
 * T factors are compact-WY (Schreiber-Van Loan): for each block of ib reflectors,
   H_1 ... H_b = I - V T V^T with T upper triangular, built by
   T <- [[T, -tau T V^T v], [0, tau]].  One factored tile stores its T blocks side by
@@ -172,6 +173,66 @@ def ttmqr(V2: np.ndarray, T: np.ndarray, C1: np.ndarray, C2: np.ndarray, ib: int
         C2[:r, :] -= t * np.outer(v, w)
 
 
+def tsqrt(R1: np.ndarray, A2: np.ndarray, ib: int):
+    """TSQRT: QR of the upper triangle R1 stacked on the square tile A2, in place
+    (Algorithm 'elimSQ').  Reflector c acts on row c of R1 and on every row of A2; its
+    tail overwrites column c of A2.  Returns T (ib x nb)."""
+    nb = R1.shape[1]
+    tau = np.zeros(nb)
+    for c in range(nb):
+        beta, t, v = householder(R1[c, c], A2[:, c].copy())
+        R1[c, c] = beta
+        A2[:, c] = v
+        tau[c] = t
+        if t != 0.0 and c + 1 < nb:
+            w = R1[c, c + 1:] + v @ A2[:, c + 1:]
+            R1[c, c + 1:] -= t * w
+            A2[:, c + 1:] -= t * np.outer(v, w)
+    # the implicit reflectors: unit entry in R1's row c, tail in A2's column c
+    V = np.vstack([np.eye(nb), A2[:, :nb]])
+    return build_t(V, tau, ib)
+
+
+def tsmqr(V2: np.ndarray, T: np.ndarray, C1: np.ndarray, C2: np.ndarray, ib: int):
+    """TSMQR: [C1; C2] <- Q^T [C1; C2] with Q from TSQRT (reflector c's tail is the
+    whole column c of V2), applied reflector by reflector."""
+    nb = V2.shape[1]
+    for c in range(nb):
+        t = T[c % ib, c]
+        if t == 0.0:
+            continue
+        v = V2[:, c]
+        w = C1[c, :] + v @ C2
+        C1[c, :] -= t * w
+        C2 -= t * np.outer(v, w)
+
+
+def _apply_ts_reflectors_reversed(V2, T, C1, C2, ib):
+    nb = V2.shape[1]
+    for c in reversed(range(nb)):
+        t = T[c % ib, c]
+        if t == 0.0:
+            continue
+        v = V2[:, c]
+        w = C1[c, :] + v @ C2
+        C1[c, :] -= t * w
+        C2 -= t * np.outer(v, w)
+
+
+def ts_rows(elims):
+    """Rows each column zeroes with TS kernels in the TS form of a list: the rows that
+    are never a pivot in that column (a TS elimination needs a square, not yet
+    triangularized, tile; every pivot was triangularized by GEQRT)."""
+    piv_rows = {}
+    for (k, _, piv) in elims:
+        piv_rows.setdefault(k, set()).add(piv)
+    out = {}
+    for (k, i, _) in elims:
+        if i not in piv_rows.get(k, ()):
+            out.setdefault(k, set()).add(i)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # The tiled TT algorithm driven by an elimination list (Algorithm 'elimTR')
 # ---------------------------------------------------------------------------
@@ -188,14 +249,18 @@ def pad(A: np.ndarray, nb: int) -> np.ndarray:
     return P
 
 
-def tiled_qr(A: np.ndarray, nb: int, ib: int, elims):
+def tiled_qr(A: np.ndarray, nb: int, ib: int, elims, ts: bool = False):
     """Tiled QR of A (m x n) following the column-by-column program: for each panel k,
     GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k, then TTQRT(i,piv,k) and
     TTMQR(i,piv,k,j) for each elimination of column k in list order.
 
+    ts: the TS form of the list - rows that are never a pivot in column k skip GEQRT /
+    UNMQR there and are zeroed by TSQRT(i,piv,k) / TSMQR(i,piv,k,j) instead (Algorithm
+    'elimSQ'); the other eliminations stay TT.
+
     Returns (F, Tg, Tt): F is the factored zero-padded matrix (p*nb x q*nb); Tg[i][k]
-    and Tt[i][k] are the ib x nb T factors of GEQRT(i,k) and of the TTQRT that zeroed
-    tile (i,k) (None where the kernel did not run)."""
+    and Tt[i][k] are the ib x nb T factors of GEQRT(i,k) and of the TTQRT or TSQRT that
+    zeroed tile (i,k) (None where the kernel did not run)."""
     m, n = A.shape
     p, q = tile_grid(m, n, nb)
     F = pad(np.asarray(A, dtype=np.float64), nb)
@@ -208,23 +273,32 @@ def tiled_qr(A: np.ndarray, nb: int, ib: int, elims):
     by_col = {}
     for e in elims:
         by_col.setdefault(e[0], []).append(e)
+    tsr = ts_rows(elims) if ts else {}
     for k in range(min(p, q)):
+        sq = tsr.get(k, ())
         for i in range(k, p):
+            if i in sq:
+                continue
             Tg[i][k] = geqrt(tile(i, k), ib)
             for j in range(k + 1, q):
                 unmqr(tile(i, k), Tg[i][k], tile(i, j), ib)
         for (_, i, piv) in by_col.get(k, []):
-            Tt[i][k] = ttqrt(tile(piv, k), tile(i, k), ib)
-            for j in range(k + 1, q):
-                ttmqr(tile(i, k), Tt[i][k], tile(piv, j), tile(i, j), ib)
+            if i in sq:
+                Tt[i][k] = tsqrt(tile(piv, k), tile(i, k), ib)
+                for j in range(k + 1, q):
+                    tsmqr(tile(i, k), Tt[i][k], tile(piv, j), tile(i, j), ib)
+            else:
+                Tt[i][k] = ttqrt(tile(piv, k), tile(i, k), ib)
+                for j in range(k + 1, q):
+                    ttmqr(tile(i, k), Tt[i][k], tile(piv, j), tile(i, j), ib)
     return F, Tg, Tt
 
 
 def apply_qt(F: np.ndarray, Tg, Tt, nb: int, ib: int, elims, B: np.ndarray,
-             transpose: bool = True) -> np.ndarray:
+             transpose: bool = True, ts: bool = False) -> np.ndarray:
     """Q^T B (transpose=True) or Q B for the tiled factorization; B has m rows.  Q^T
     replays the update kernels on B's tile rows in program order; Q applies the same
-    reflectors in the reverse order."""
+    reflectors in the reverse order.  ts: the factorization used the TS form."""
     p = F.shape[0] // nb
     q = F.shape[1] // nb
     m = B.shape[0]
@@ -241,21 +315,28 @@ def apply_qt(F: np.ndarray, Tg, Tt, nb: int, ib: int, elims, B: np.ndarray,
     by_col = {}
     for e in elims:
         by_col.setdefault(e[0], []).append(e)
+    tsr = ts_rows(elims) if ts else {}
     for k in range(min(p, q)):
+        sq = tsr.get(k, ())
         for i in range(k, p):
-            ops.append(("G", i, k, None))
+            if i not in sq:
+                ops.append(("G", i, k, None))
         for (_, i, piv) in by_col.get(k, []):
-            ops.append(("T", i, k, piv))
+            ops.append(("S" if i in sq else "T", i, k, piv))
     if transpose:
         for kind, i, k, piv in ops:
             if kind == "G":
                 unmqr(ftile(i, k), Tg[i][k], brow(i), ib)
+            elif kind == "S":
+                tsmqr(ftile(i, k), Tt[i][k], brow(piv), brow(i), ib)
             else:
                 ttmqr(ftile(i, k), Tt[i][k], brow(piv), brow(i), ib)
     else:
         for kind, i, k, piv in reversed(ops):
             if kind == "G":
                 _apply_geqrt_reflectors_reversed(ftile(i, k), Tg[i][k], brow(i), ib)
+            elif kind == "S":
+                _apply_ts_reflectors_reversed(ftile(i, k), Tt[i][k], brow(piv), brow(i), ib)
             else:
                 _apply_tt_reflectors_reversed(ftile(i, k), Tt[i][k], brow(piv), brow(i), ib)
     return Bp[:m].copy()
@@ -301,10 +382,10 @@ def back_substitute(R: np.ndarray, Y: np.ndarray) -> np.ndarray:
     return X
 
 
-def lstsq(A: np.ndarray, B: np.ndarray, nb: int, ib: int, elims) -> np.ndarray:
+def lstsq(A: np.ndarray, B: np.ndarray, nb: int, ib: int, elims, ts: bool = False) -> np.ndarray:
     """Least-squares solution of min ||A X - B|| (m >= n, full rank):
     X = R^{-1} (Q^T B)[0:n]."""
     m, n = A.shape
-    F, Tg, Tt = tiled_qr(A, nb, ib, elims)
-    QtB = apply_qt(F, Tg, Tt, nb, ib, elims, np.asarray(B, dtype=np.float64).reshape(m, -1))
+    F, Tg, Tt = tiled_qr(A, nb, ib, elims, ts)
+    QtB = apply_qt(F, Tg, Tt, nb, ib, elims, np.asarray(B, dtype=np.float64).reshape(m, -1), ts=ts)
     return back_substitute(r_factor(F, n), QtB[:n])

@@ -230,3 +230,55 @@ def test_check_valid_rejects_bad_lists():
     for bad in bad_cases:
         with pytest.raises(ValueError):
             E.check_valid(6, 3, bad)
+
+
+# ---------------------------------------------------------------------------
+# TS form of a list (Algorithm 'elimSQ'; Theorem 'thm.flops' for any TT/TS mix)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,q", [(1, 1), (1, 4), (3, 5), (4, 4), (6, 2), (11, 4), (17, 5)])
+@pytest.mark.parametrize("tree", [E.FLAT, E.PLASMA, E.BINARY, E.FIBONACCI, E.GREEDY, E.GRASAP])
+def test_ts_counts_total_weight(p, q, tree):
+    """Theorem 'thm.flops': with any combination of TT and TS kernels, L1 GEQRT = TTQRT +
+    q, L2 UNMQR = TTMQR + q(q-1)/2, L3 TTQRT + TSQRT = pq - q(q+1)/2, L4 TTMQR + TSMQR
+    = pq(q-1)/2 - (q-1)q(q+1)/6, and the total weight is 6pq^2 - 2q^3."""
+    lst = E.elimination_list(p, q, tree, bs=3)
+    c = E.kernel_counts(p, q, lst, ts=True)
+    sched = E.schedule(p, q, lst, ts=True)
+    run = {}
+    for key in sched.finish:
+        run[key[0]] = run.get(key[0], 0) + 1
+    for kname, v in c.items():
+        assert run.get(kname, 0) == v, kname
+    if p >= q:
+        assert c["GEQRT"] == c["TTQRT"] + q
+        assert c["UNMQR"] == c["TTMQR"] + q * (q - 1) // 2
+        assert c["TTQRT"] + c["TSQRT"] == p * q - q * (q + 1) // 2
+        assert 6 * (c["TTMQR"] + c["TSMQR"]) == 3 * p * q * (q - 1) - (q - 1) * q * (q + 1)
+        total = (4 * c["GEQRT"] + 6 * c["TSQRT"] + 2 * c["TTQRT"] + 6 * c["UNMQR"]
+                 + 6 * c["TTMQR"] + 12 * c["TSMQR"])
+        assert total == 6 * p * q * q - 2 * q ** 3
+    # a TS row is never a pivot of its column; FlatTree's TS form has no TT kernel
+    tsr = E.ts_rows(lst)
+    for (k, i, piv) in lst:
+        assert piv not in tsr.get(k, ())
+    if tree == E.FLAT:
+        assert c["TTQRT"] == 0 and c["TTMQR"] == 0
+
+
+def test_ts_elimination_parallel_time():
+    """One elimination with its updates on unbounded processors (Section 3.1.1): the TS
+    kernels take 4 + 6 + 12 = 22 time units, the TT kernels 4 + 6 + 6 = 16 (2 x 2 tiles,
+    FlatTree: the update of tile (1,1) finishes at those times; the final GEQRT(1,1)
+    adds 4)."""
+    lst = E.elimination_list(2, 2, E.FLAT)
+    ts = E.schedule(2, 2, lst, ts=True)
+    tt = E.schedule(2, 2, lst)
+    assert ts.finish[("TSMQR", 1, 0, 0, 1)] == 22
+    assert tt.finish[("TTMQR", 1, 0, 0, 1)] == 16
+    assert ts.makespan == 26 and tt.makespan == 20
+    # one column of three rows: GEQRT(0) then two TSQRT in sequence on the pivot's
+    # triangle (4 + 6 + 6), against GEQRTs in parallel and two TTQRTs (4 + 2 + 2)
+    lst = E.elimination_list(3, 1, E.FLAT)
+    assert E.critical_path(3, 1, lst, ts=True) == 16
+    assert E.critical_path(3, 1, lst) == 8

@@ -189,3 +189,96 @@ def test_t_layout_diagonal_holds_tau():
     Aw = np.array(A)
     T = H.geqrt(Aw, 3)
     assert np.allclose([T[c % 3, c] for c in range(8)], tau, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# TS kernels (triangle on top of square): Algorithm 'elimSQ', Table 'Kernels for tiled QR'
+# ---------------------------------------------------------------------------
+
+TS_TREES = [E.FLAT, E.PLASMA, E.BINARY, E.FIBONACCI, E.GREEDY, E.GRASAP]
+
+
+@pytest.mark.parametrize("m,n,nb,ib", CASES)
+@pytest.mark.parametrize("tree", TS_TREES)
+def test_ts_form_brute_force(m, n, nb, ib, tree):
+    """The TS form of every list vs unblocked Householder and LAPACK: |R| equal, A = QR
+    and Q^T Q = I to FP64 rounding, Q^T A = R."""
+    A = synthetic.gaussian(m, n, seed=m * 100 + n + 7)
+    p, q = H.tile_grid(m, n, nb)
+    elims = E.elimination_list(p, q, tree, bs=2)
+    F, Tg, Tt = H.tiled_qr(A, nb, ib, elims, ts=True)
+    k = min(m, n)
+    R_ts = np.triu(F[:k, :n])
+    R_lapack = np.linalg.qr(A, mode="r")[:k, :n]
+    Fu, _ = H.qr_unblocked(A)
+    scale = np.linalg.norm(A)
+    tol = 1e-14 * scale * max(m, n)
+    assert np.max(np.abs(np.abs(R_ts) - np.abs(R_lapack))) < tol
+    assert np.max(np.abs(np.abs(R_ts) - np.abs(np.triu(Fu[:k, :n])))) < tol
+    Q = H.apply_qt(F, Tg, Tt, nb, ib, elims, np.eye(m), transpose=False, ts=True)
+    assert np.max(np.abs(Q.T @ Q - np.eye(m))) < 1e-14 * m * 4
+    Rfull = np.zeros((m, n))
+    Rfull[:k] = R_ts
+    assert np.linalg.norm(A - Q @ Rfull) / scale < 1e-14 * max(m, n)
+    QtA = H.apply_qt(F, Tg, Tt, nb, ib, elims, A, ts=True)
+    assert np.max(np.abs(QtA - Rfull)) < tol
+
+
+@pytest.mark.parametrize("nb,ib,mb", [(6, 2, 6), (6, 4, 6), (5, 5, 5), (7, 3, 7), (6, 4, 3)])
+def test_tsqrt_t_identity_and_definition(nb, ib, mb):
+    """TSQRT's T: I - V T_b V^T equals the product of its block's reflectors, each formed
+    explicitly from [e_c; A2[:, c]] and tau; the reflectors map [R1; A2] to [R; 0] with
+    |R| the R of the stacked matrix (mb < nb: a ragged bottom tile)."""
+    rng = np.random.default_rng(nb * 100 + ib * 10 + mb)
+    R1 = np.triu(rng.standard_normal((nb, nb)))
+    A2 = rng.standard_normal((mb, nb))
+    S = np.vstack([R1, A2])
+    R1w, A2w = R1.copy(), A2.copy()
+    T = H.tsqrt(R1w, A2w, ib)
+    V = np.vstack([np.eye(nb), A2w])
+    full = np.eye(nb + mb)
+    for b0 in range(0, nb, ib):
+        b1 = min(b0 + ib, nb)
+        Tb = T[:b1 - b0, b0:b1]
+        assert np.allclose(np.tril(Tb, -1), 0)
+        prod = np.eye(nb + mb)
+        for c in range(b0, b1):
+            prod = prod @ _explicit_reflector(V[:, c], T[c - b0, c])
+        assert np.max(np.abs(np.eye(nb + mb) - V[:, b0:b1] @ Tb @ V[:, b0:b1].T - prod)) < 1e-14 * nb * 4
+        full = full @ prod
+    out = full.T @ S
+    assert np.max(np.abs(out[nb:])) < 1e-13
+    assert np.max(np.abs(out[:nb] - np.triu(R1w))) < 1e-13
+    assert np.max(np.abs(np.abs(np.triu(R1w)) - np.abs(np.linalg.qr(S, mode="r")))) < 1e-13
+    # TSMQR applies the same transformation to any pair of blocks
+    C1 = rng.standard_normal((nb, 3))
+    C2 = rng.standard_normal((mb, 3))
+    want = full.T @ np.vstack([C1, C2])
+    H.tsmqr(A2w, T, C1, C2, ib)
+    assert np.max(np.abs(np.vstack([C1, C2]) - want)) < 1e-13
+
+
+def test_ts_splits_into_two_tt_kernels():
+    """A TS elimination can be replaced by GEQRT of the square tile followed by TTQRT
+    (Section 3.1.1): the TS form and the TT form of one list give the same |R|."""
+    for tree in TS_TREES:
+        for (m, n, nb) in [(40, 24, 8), (33, 17, 6)]:
+            A = synthetic.gaussian(m, n, seed=tree + m)
+            p, q = H.tile_grid(m, n, nb)
+            elims = E.elimination_list(p, q, tree, bs=2)
+            F_ts, _, _ = H.tiled_qr(A, nb, 3, elims, ts=True)
+            F_tt, _, _ = H.tiled_qr(A, nb, 3, elims)
+            k = min(m, n)
+            d = np.abs(np.abs(np.triu(F_ts[:k, :n])) - np.abs(np.triu(F_tt[:k, :n])))
+            assert np.max(d) < 1e-13 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("tree", TS_TREES)
+def test_ts_lstsq(tree):
+    m, n = 60, 20
+    A, X, B = synthetic.least_squares_problem(m, n, 1e2, 1e-3, 2, seed=55)
+    p, q = H.tile_grid(m, n, 8)
+    elims = E.elimination_list(p, q, tree, bs=3)
+    Xo = H.lstsq(A, B, 8, 4, elims, ts=True)
+    Xl = np.linalg.lstsq(A, B, rcond=None)[0]
+    assert refine.rel_error(Xo, Xl) < 1e-12
