@@ -44,6 +44,17 @@ typedef enum {
   TQR_GREEDY = 4, TQR_GRASAP = 5, TQR_ASAP = 6
 } tqr_tree;
 
+/* Flag OR-ed into any tree argument: the TS form of the tree's list (Section 3.1.1,
+ * Algorithm "elimSQ", Table "Kernels for tiled QR").  A TS elimination zeroes a square
+ * tile with TSQRT(i,piv,k) (weight 6) and updates its row pair with TSMQR(i,piv,k,j)
+ * (weight 12); its row must not have been triangularized, so the TS form zeroes with TS
+ * kernels every row that is never a pivot in that column and keeps the TT kernels for
+ * the rows that pivot before they are zeroed (those rows get GEQRT/UNMQR as before).
+ * TQR_FLAT | TQR_TS is Sameh-Kuck with TS kernels; TQR_PLASMA | TQR_TS is the PLASMA
+ * algorithm (TS inside each domain, TT between the domain heads).  A TSQRT stores its
+ * reflectors in the whole zeroed tile and its T in the tile's TTQRT slot. */
+enum { TQR_TS = 16 };
+
 /* Arithmetic of the factorization.
  *   TQR_FP64   : everything in FP64 (matrix in double).
  *   TQR_FP32   : matrix in float; Householder norms and tau in FP64; updates in FP32.
@@ -71,7 +82,8 @@ enum {
  *   len      : in = capacity of list in triples; out = E = number of eliminations.
  *   cp_units : out (may be NULL), the weighted critical path with unbounded
  *              processors in units of nb^3/3 flops, kernel weights GEQRT 4, TTQRT 2,
- *              UNMQR 6, TTMQR 6 (Table "Kernels for tiled QR", Section 3.1.3).
+ *              UNMQR 6, TTMQR 6, TSQRT 6, TSMQR 12 (Table "Kernels for tiled QR",
+ *              Section 3.1.3); with TQR_TS in tree, of the TS form.
  *   bs       : PlasmaTree domain size (>= 1), ignored by the other trees.
  * Host only; no device work.  Errors: -1/-2 p or q < 1, -3 unknown tree, -4 bs < 1
  * for PlasmaTree, -6 len NULL or capacity too small while list != NULL. */
@@ -84,7 +96,8 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len,
  * of tqr_elimlist (p x q tiles, tree, bs).
  *   nproc      : number of processors, >= 1.
  *   weights    : 4 int64 kernel weights (GEQRT, TTQRT, UNMQR, TTMQR), each >= 1; NULL =
- *                the thesis's 4, 2, 6, 6.
+ *                the thesis's 4, 2, 6, 6.  The TS kernels of a TQR_TS tree weigh 3 x TTQRT
+ *                (TSQRT) and 2 x TTMQR (TSMQR), the thesis's ratios 6/2 and 12/6.
  *   makespan   : out (may be NULL), the length of the "CP Method" list schedule: every
  *                task gets its Backflow priority (its weight plus the largest priority
  *                of a successor) and at every moment the free processors take the ready
@@ -107,7 +120,8 @@ int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weigh
  *   mode 1: the start order of tqr_schedule's CP-method list schedule on as many
  *           processors as the executor keeps resident CTAs, with the given per-kind
  *           weights (GEQRT, TTQRT, UNMQR, TTMQR; each >= 1; NULL = 4, 2, 6, 6), e.g.
- *           measured task durations of the chosen precision.
+ *           measured task durations of the chosen precision (TS kernels: 3 x TTQRT and
+ *           2 x TTMQR).
  *   mode 2 (default): mode 1 with built-in weights from task durations in
  *           microseconds measured on GB300 - the tensor-core precisions 330, 360, 20, 32
  *           (nb 128, panel weights tuned on a 32768 x 4096 factorization), TQR_FP64 5146,
@@ -131,6 +145,8 @@ int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T
  *   T   : device, tqr_workspace_size() bytes, written.
  *   nb  : tile size, 1..256 for TQR_FP64 and TQR_FP32, exactly 128 for the tensor-core
  *         precisions; ib: inner block, 1 <= ib <= min(nb, 32).
+ *   tree: a tqr_tree, optionally | TQR_TS (the TS form: the upper triangle of a tile
+ *         zeroed by TSQRT is not R - the whole tile holds its reflectors).
  * Errors: -1..-4 sizes, -5 tree, -6 bs, -7 prec, -8 A NULL, -9 lda < m, -10 T NULL;
  *         TQR_ETIMEOUT, TQR_ECUDA, TQR_ENOMEM, TQR_EUNSUPPORTED. */
 int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
@@ -220,18 +236,26 @@ int tqr_factor_batched(int nbatch, const int64_t *m, const int64_t *n, void *con
                        const int64_t *lda, const int *params, int prec, void *const *T,
                        void *stream);
 
-/* Apply Q^T (trans = 0) or Q (trans = 1) of a tqr_factor result to B (m x nrhs,
+/* Chapter 3's statement of the problem (its opening, before Section 3.1) motivates the
+ * QR factorization A = QR by two uses: solving a linear least-squares problem with m
+ * equations and n unknowns, and an orthonormal basis of A's column span (the Q factor).
+ * tqr_apply_qt, tqr_trsm and tqr_lstsq are those uses, built on tqr_factor.
+ *
+ * Apply Q^T (trans = 0) or Q (trans = 1) of a tqr_factor result to B (m x nrhs,
  * column-major, ldb >= m), in place, replaying the UNMQR/TTMQR kernels on B's tile rows
  * (in list order for Q^T, in reverse for Q).  A/T/prec/tree/nb/ib must be those of the
  * factorization.  B is double for every precision; the reflectors are read in the
  * precision A is stored in.
+ * With trans = 1 on B = the first n columns of the identity the call forms the explicit
+ * thin Q (the orthonormal basis of the column span).
  * Errors: -1..-6 sizes/tree/bs, -7 prec, -8 trans, -9 A, -10 lda, -11 T, -12 B,
  *         -13 ldb, -14 nrhs < 0. */
 int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec, int trans,
                  const void *A, int64_t lda, const void *T, double *B, int64_t ldb,
                  int64_t nrhs, void *stream);
 
-/* Solve R X = B for the n x n upper-triangular R held in the top rows of a factored A
+/* Solve R X = B (the triangular solve of the least-squares use of A = QR, Chapter 3's
+ * statement of the problem) for the n x n upper-triangular R held in the top rows of a factored A
  * (double for TQR_FP64, float otherwise), X overwriting B (n x nrhs double, ldb >= n).
  * Errors: -1 n, -2 prec, -3 A, -4 lda, -5 B, -6 ldb, -7 nrhs. */
 int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb,
@@ -249,12 +273,16 @@ int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t
  *   tqr_last_error().  Arguments, layout and the other errors are those of tqr_trsm.
  *   The first call on a device looks up the device address of the array (once per
  *   device, with that device current); make that first call before any stream capture.
+ *   The address is cached for the life of the device's primary context: after a
+ *   cudaDeviceReset, call tqr_finalize() (which forgets it) before the next call.
  *   Every call uses the same array and resets the parts that must start at zero, so
  *   calls that overlap on the GPU (e.g. on two streams at once) race: serialize them. */
 int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb,
                     int64_t nrhs, void *stream);
 
-/* Least squares min ||A X - B||_2 (m >= n, A of full column rank), all operands double.
+/* Least squares min ||A X - B||_2 (m >= n, A of full column rank), all operands double:
+ * the linear least-squares problem Chapter 3's statement of the problem names as the
+ * first use of the QR factorization (X = R^{-1} (Q^T B)(0:n)).
  *   prec == TQR_FP64 : X = R^{-1} (Q^T B)(0:n) from an FP64 tiled QR.
  *   otherwise        : the tiled QR runs in "prec" on a float copy of A; X is then
  *                      computed by FP64 iterative refinement from X = 0: each step
@@ -319,7 +347,7 @@ int64_t tqr_trace_fetch(int64_t *out, int64_t cap);
 
 const char *tqr_strerror(int status);
 const char *tqr_last_error(void);      /* detail of the last TQR_ECUDA / internal error */
-void tqr_finalize(void);               /* free every cached plan                         */
+void tqr_finalize(void);               /* free every cached plan and cached scratch address */
 
 /* ---- test hooks (host logic only; no numerics) ----
  * tqr_plan_stats: task and edge counts of the task graph the executor runs for a
@@ -332,12 +360,16 @@ void tqr_finalize(void);               /* free every cached plan                
  *   p x q tile matrix, built as a plan is: mode 0 = earliest start on unbounded
  *   processors, mode 1 = start order of the CP-method list schedule on nproc processors
  *   with the four kernel weights (NULL = 4, 2, 6, 6; see tqr_set_claim_order).  tasks
- *   receives 5 int32 per task in claim order: kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR),
+ *   receives 5 int32 per task in claim order: kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR,
+ *   6 TSQRT, 7 TSMQR),
  *   i, piv (-1 if none), k, j (-1 if none); NULL to query the count.  ntask: in =
  *   capacity in tasks, out = number of tasks.  Host only.  Errors: -1/-2 p or q < 1,
  *   -3 unknown tree, -4 bs < 1 for PlasmaTree, -5 mode not 0 or 1, -6 nproc < 1, -7 a
  *   weight < 1, -8 ntask NULL or capacity too small while tasks != NULL. */
 int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6]);
+/* tqr_plan_counts: as tqr_plan_stats with the TS kernels: out[0..7] = #GEQRT, #TTQRT,
+ *   #UNMQR, #TTMQR, #TSQRT, #TSMQR, #edges, critical path (tree may carry TQR_TS). */
+int tqr_plan_counts(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[8]);
 void tqr_debug_drop_edge(int64_t e);
 int tqr_debug_claim_order(int p, int q, int tree, int bs, int mode, int nproc, const int64_t *weights,
                           int32_t *tasks, int64_t *ntask);

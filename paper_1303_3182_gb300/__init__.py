@@ -21,8 +21,10 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtqr.so")
 
 FLAT, PLASMA, BINARY, FIBONACCI, GREEDY, GRASAP, ASAP = range(7)
+TS = 16  # flag: the TS form of a tree (TSQRT/TSMQR for rows that never pivot)
 TREES = {"flat": FLAT, "plasma": PLASMA, "binary": BINARY, "fibonacci": FIBONACCI,
          "greedy": GREEDY, "grasap": GRASAP, "asap": ASAP}
+TREES.update({name + "-ts": v | TS for name, v in list(TREES.items())})
 FP64, BF16, FP16, BF16X3, FP32, BF16X6 = 0, 1, 2, 3, 4, 5
 PRECS = {"fp64": FP64, "bf16": BF16, "fp16": FP16, "bf16x3": BF16X3, "fp32": FP32, "bf16x6": BF16X6}
 TQR_ETIMEOUT = 3
@@ -70,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "tqr_last_error": (ctypes.c_char_p, []),
             "tqr_finalize": (None, []),
             "tqr_plan_stats": (i32, [i64, i64, i32, i32, i32, c_i64p]),
+            "tqr_plan_counts": (i32, [i64, i64, i32, i32, i32, c_i64p]),
             "tqr_debug_drop_edge": (None, [i64]),
             "tqr_set_timing": (i32, [i32]),
             "tqr_set_trace": (i32, [i32]),
@@ -201,6 +204,15 @@ def plan_stats(m: int, n: int, nb: int, tree="greedy", bs: int = 1):
     _check("tqr_plan_stats", lib().tqr_plan_stats(m, n, nb, _tree(tree), bs, out))
     return {"GEQRT": out[0], "TTQRT": out[1], "UNMQR": out[2], "TTMQR": out[3],
             "edges": out[4], "cp": out[5]}
+
+
+def plan_counts(m: int, n: int, nb: int, tree="greedy", bs: int = 1):
+    """Task counts of a factorization graph including the TS kernels (tree may be a TS
+    form, e.g. "plasma-ts")."""
+    out = (ctypes.c_int64 * 8)()
+    _check("tqr_plan_counts", lib().tqr_plan_counts(m, n, nb, _tree(tree), bs, out))
+    return {"GEQRT": out[0], "TTQRT": out[1], "UNMQR": out[2], "TTMQR": out[3],
+            "TSQRT": out[4], "TSMQR": out[5], "edges": out[6], "cp": out[7]}
 
 
 def workspace_size(m: int, n: int, nb: int, ib: int, prec="fp64") -> int:

@@ -33,10 +33,29 @@ int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
 //   factorization takes 1488 ms instead of 1635 ms with the unbounded order (its ALAP
 //   Derived bound is 1468 ms), Greedy's 1448 ms against 1443 ms (bound 1424 ms).
 int g_order_mode = 2;
-int64_t g_order_w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+int64_t g_order_w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr};
 int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
-constexpr int64_t kTensorOrderWeights[4] = {330, 360, 20, 32};
-constexpr int64_t kFp64OrderWeights[4] = {5146, 4249, 6394, 6369};
+// per TaskKind: GEQRT, TTQRT, UNMQR, TTMQR, (apply-Q kinds, unused), TSQRT, TSMQR
+constexpr int64_t kTensorOrderWeights[kNumKinds] = {330, 360, 20, 32, 20, 32, 400, 32, 32};
+constexpr int64_t kFp64OrderWeights[kNumKinds] = {5146, 4249, 6394, 6369, 6394, 6369, 7700, 12800, 12800};
+
+// Per-kind weights from the four TT-kernel weights of the ABI (GEQRT, TTQRT, UNMQR,
+// TTMQR): the TS kernels take the thesis's ratios to their TT counterparts, TSQRT = 3
+// TTQRT (6 against 2) and TSMQR = 2 TTMQR (12 against 6).
+void expand_weights(const int64_t w4[4], int64_t out[kNumKinds]) {
+  out[kGeqrt] = w4[0];
+  out[kTtqrt] = w4[1];
+  out[kUnmqr] = out[kUnmqrB] = w4[2];
+  out[kTtmqr] = out[kTtmqrB] = w4[3];
+  out[kTsqrt] = 3 * w4[1];
+  out[kTsmqr] = out[kTsmqrB] = 2 * w4[3];
+}
+
+bool valid_tree(int tree) {
+  if (tree & ~(kTreeTS | 15)) return false;
+  const int b = tree_base(tree);
+  return b >= TQR_FLAT && b <= TQR_ASAP;
+}
 
 OrderSpec effective_order(int prec) {
   OrderSpec spec;
@@ -53,7 +72,7 @@ OrderSpec effective_order(int prec) {
   }
   if (w) {
     spec.mode = 1;
-    for (int c = 0; c < 4; ++c) spec.w[c] = w[c];
+    for (int c = 0; c < kNumKinds; ++c) spec.w[c] = w[c];
   }
   return spec;
 }
@@ -163,20 +182,20 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   // built-in weight set a negative key of its own) is part of the key; a plan built with
   // the test hook is never reused: it gets a key of its own
   const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : kind, P, Q, tree,
-                    tree == TQR_PLASMA ? bs : 0, bounded ? spec.id : 0, bounded ? spec.nproc : 0};
+                    tree_base(tree) == TQR_PLASMA ? bs : 0, bounded ? spec.id : 0, bounded ? spec.nproc : 0};
   auto it = g_plans.find(key);
   if (it != g_plans.end()) {
     *out = it->second.get();
     return TQR_OK;
   }
   std::vector<Elim> elims;
-  if (!elimination_list(P, Q, tree, bs, elims)) return -5;
+  if (!elimination_list(P, Q, tree_base(tree), bs, elims)) return -5;
   auto plan = std::make_unique<Plan>();
   plan->device = dev;
   if (kind == 0)
-    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr);
+    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree));
   else
-    build_applyq_graph(P, Q, elims, kind == 2, plan->g);
+    build_applyq_graph(P, Q, elims, kind == 2, plan->g, tree_ts(tree));
   if (drop >= 0) g_drop_edge = -1;  // the test hook applies to one plan only
   const Graph &g = plan->g;
   if ((e = upload(&plan->d_tasks, g.tasks)) != cudaSuccess ||
@@ -282,8 +301,8 @@ int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec
   if (nb < 1 || nb > 256) return -3;
   if (is_tensor_prec(prec) && nb != kMixedNB) return -3;
   if (ib < 1 || ib > nb || ib > 32) return -4;
-  if (tree < TQR_FLAT || tree > TQR_ASAP) return -5;
-  if (tree == TQR_PLASMA && bs < 1) return -6;
+  if (!valid_tree(tree)) return -5;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -6;
   if (prec < TQR_FP64 || prec > TQR_BF16X6) return -7;
   if (ceil_div(m, nb) > 32767 || ceil_div(n, nb) > 32767) return -3;
   return 0;
@@ -318,12 +337,12 @@ extern "C" {
 int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len, int64_t *cp_units) {
   if (p < 1) return -1;
   if (q < 1) return -2;
-  if (tree < TQR_FLAT || tree > TQR_ASAP) return -3;
-  if (tree == TQR_PLASMA && bs < 1) return -4;
+  if (!valid_tree(tree)) return -3;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -4;
   if (!len) return -6;
   std::vector<Elim> elims;
   try {
-    elimination_list(p, q, tree, bs, elims);
+    elimination_list(p, q, tree_base(tree), bs, elims);
     const int64_t E = static_cast<int64_t>(elims.size());
     if (list) {
       if (*len < E) return -6;
@@ -336,7 +355,7 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len, in
     *len = E;
     if (cp_units) {
       Graph g;
-      build_factor_graph(p, q, elims, g);
+      build_factor_graph(p, q, elims, g, -1, nullptr, tree_ts(tree));
       *cp_units = g.critical_path;
     }
   } catch (const std::bad_alloc &) {
@@ -352,20 +371,21 @@ int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weigh
                  int64_t *alap_bound, int64_t *lost_area) {
   if (p < 1) return -1;
   if (q < 1) return -2;
-  if (tree < TQR_FLAT || tree > TQR_ASAP) return -3;
-  if (tree == TQR_PLASMA && bs < 1) return -4;
+  if (!valid_tree(tree)) return -3;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -4;
   if (nproc < 1) return -5;
-  int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+  int64_t w4[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr}, w[kNumKinds];
   if (weights)
     for (int c = 0; c < 4; ++c) {
       if (weights[c] < 1) return -6;
-      w[c] = weights[c];
+      w4[c] = weights[c];
     }
+  expand_weights(w4, w);
   try {
     std::vector<Elim> elims;
-    elimination_list(p, q, tree, bs, elims);
+    elimination_list(p, q, tree_base(tree), bs, elims);
     GraphBuilder b(p * q * 2);
-    add_factor_program(b, p, q, elims);
+    add_factor_program(b, p, q, elims, tree_ts(tree));
     const int n = static_cast<int>(b.tasks.size());
     std::vector<std::vector<int32_t>> succ(n);
     std::vector<int32_t> npred(n);
@@ -392,15 +412,16 @@ int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weigh
 
 int tqr_set_claim_order(int mode, const int64_t *weights) {
   if (mode < 0 || mode > 2) return -1;
-  int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+  int64_t w4[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr}, w[kNumKinds];
   if (weights && mode == 1)
     for (int c = 0; c < 4; ++c) {
       if (weights[c] < 1) return -2;
-      w[c] = weights[c];
+      w4[c] = weights[c];
     }
+  expand_weights(w4, w);
   std::lock_guard<std::mutex> lock(g_mu);
   g_order_mode = mode;
-  for (int c = 0; c < 4; ++c) g_order_w[c] = w[c];
+  for (int c = 0; c < kNumKinds; ++c) g_order_w[c] = w[c];
   ++g_order_gen;
   return TQR_OK;
 }
@@ -680,6 +701,7 @@ const char *tqr_strerror(int status) {
 const char *tqr_last_error(void) { return g_last_error.c_str(); }
 
 void tqr_finalize(void) {
+  reset_static_scratch();
   std::lock_guard<std::mutex> lock(g_mu);
   g_plans.clear();
   for (auto &kv : g_scratch) cudaFree(kv.second.flags);
@@ -691,20 +713,32 @@ void tqr_finalize(void) {
 }
 
 int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6]) {
+  int64_t all[8];
+  const int rc = tqr_plan_counts(m, n, nb, tree, bs, out ? all : nullptr);
+  if (rc) return rc;
+  for (int c = 0; c < 4; ++c) out[c] = all[c];
+  out[4] = all[6];
+  out[5] = all[7];
+  return TQR_OK;
+}
+
+int tqr_plan_counts(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[8]) {
   if (m < 1) return -1;
   if (n < 1) return -2;
   if (nb < 1) return -3;
-  if (tree < TQR_FLAT || tree > TQR_ASAP) return -4;
-  if (tree == TQR_PLASMA && bs < 1) return -5;
+  if (!valid_tree(tree)) return -4;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -5;
   if (!out) return -6;
   const int P = static_cast<int>(ceil_div(m, nb)), Q = static_cast<int>(ceil_div(n, nb));
   std::vector<Elim> elims;
-  elimination_list(P, Q, tree, bs, elims);
+  elimination_list(P, Q, tree_base(tree), bs, elims);
   Graph g;
-  build_factor_graph(P, Q, elims, g);
+  build_factor_graph(P, Q, elims, g, -1, nullptr, tree_ts(tree));
   for (int c = 0; c < 4; ++c) out[c] = g.counts[c];
-  out[4] = static_cast<int64_t>(g.succ_idx.size());
-  out[5] = g.critical_path;
+  out[4] = g.counts[kTsqrt];
+  out[5] = g.counts[kTsmqr];
+  out[6] = static_cast<int64_t>(g.succ_idx.size());
+  out[7] = g.critical_path;
   return TQR_OK;
 }
 
@@ -766,24 +800,27 @@ int tqr_debug_claim_order(int p, int q, int tree, int bs, int mode, int nproc, c
                           int32_t *tasks, int64_t *ntask) {
   if (p < 1) return -1;
   if (q < 1) return -2;
-  if (tree < TQR_FLAT || tree > TQR_ASAP) return -3;
-  if (tree == TQR_PLASMA && bs < 1) return -4;
+  if (!valid_tree(tree)) return -3;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -4;
   if (mode != 0 && mode != 1) return -5;
   if (nproc < 1) return -6;
   if (!ntask) return -8;
   OrderSpec spec;
   spec.mode = mode;
   spec.nproc = nproc;
-  if (weights)
+  if (weights) {
+    int64_t w4[4];
     for (int c = 0; c < 4; ++c) {
       if (weights[c] < 1) return -7;
-      spec.w[c] = weights[c];
+      w4[c] = weights[c];
     }
+    expand_weights(w4, spec.w);
+  }
   try {
     std::vector<Elim> elims;
-    elimination_list(p, q, tree, bs, elims);
+    elimination_list(p, q, tree_base(tree), bs, elims);
     Graph g;
-    build_factor_graph(p, q, elims, g, -1, mode == 1 ? &spec : nullptr);
+    build_factor_graph(p, q, elims, g, -1, mode == 1 ? &spec : nullptr, tree_ts(tree));
     const int64_t n = static_cast<int64_t>(g.tasks.size());
     if (tasks) {
       if (*ntask < n) return -8;

@@ -136,13 +136,13 @@ int merge_batch(int nbatch, const int64_t *m, const int64_t *n, const int *prm, 
   for (int b = 0; b < nbatch; ++b) {
     const int *o = prm + 4 * b;
     const int P = static_cast<int>(cdiv(m[b], o[0])), Q = static_cast<int>(cdiv(n[b], o[0]));
-    const Key key{P, Q, o[2], o[2] == TQR_PLASMA ? o[3] : 0};
+    const Key key{P, Q, o[2], tree_base(o[2]) == TQR_PLASMA ? o[3] : 0};
     auto it = graphs.find(key);
     if (it == graphs.end()) {
       std::vector<Elim> elims;
-      if (!elimination_list(P, Q, o[2], o[3], elims)) return fail(-5, "elimination list");
+      if (!elimination_list(P, Q, tree_base(o[2]), o[3], elims)) return fail(-5, "elimination list");
       auto g = std::make_unique<Graph>();
-      build_factor_graph(P, Q, elims, *g);
+      build_factor_graph(P, Q, elims, *g, -1, nullptr, tree_ts(o[2]));
       it = graphs.emplace(key, std::move(g)).first;
     }
     gof[b] = it->second.get();

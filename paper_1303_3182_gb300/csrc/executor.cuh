@@ -514,8 +514,10 @@ __device__ __forceinline__ bool reflector_f32(float alpha, DFloat xx, float *bet
 }
 
 // Householder factorization of one panel block (kb columns) held in shared memory.
+// kPanel selects the kernel: 0 GEQRT, 1 TTQRT, 2 TSQRT.
 //   GEQRT: column c of s.V; head = V(c, c), tail = V(c+1 .. rows-1, c)
 //   TT:    head = P1(c, c) (row c of R(piv)), tail = V(0 .. min(c0+c+1, mb)-1, c)
+//   TS:    head = P1(c, c), tail = V(0 .. rows-1, c) (the whole square tile's column)
 // Reflector c updates every later column cc of the block:
 //   w = head(c, cc) + v . tail(cc);  head(c, cc) -= tau w;  tail(cc) -= tau v w,
 // with v = tail(c) * scal.  Warp 0 updates column c+1 first and, in the same pass over
@@ -527,12 +529,13 @@ __device__ __forceinline__ bool reflector_f32(float alpha, DFloat xx, float *bet
 // scalars in FP32 from the FP64-accurate sum of squares (reflector_f32).
 // kR bounds the rows per lane (rows of the block <= 32 kR): the row loops are unrolled
 // and each lane issues all its shared-memory loads of a pass at once.
-template <typename S, bool kTT, int kR>
+template <typename S, int kPanel, int kR>
 __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr bool kTT = kPanel != 0;  // TT and TS: the head is a row of R(piv)
   auto head = [&](int c, int cc) -> S & { return kTT ? s.P1[c + cc * s.ldt] : s.V[c + cc * s.ldv]; };
   auto tlo = [&](int c) { return kTT ? 0 : c + 1; };
-  auto thi = [&](int c) { return kTT ? min(c0 + c + 1, mb) : rows; };
+  auto thi = [&](int c) { return kPanel == 1 ? min(c0 + c + 1, mb) : rows; };
   auto col = [&](int c) -> S * { return s.V + c * s.ldv; };
   constexpr bool kF32 = sizeof(S) == sizeof(float);
   // Sum of squares accumulated per lane: double-float for FP32 storage (FP64-accurate
@@ -698,17 +701,17 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
 }
 
 // panel_factor with the tight rows-per-lane bound ceil(rows / 32) (rows <= 256).
-template <typename S, bool kTT>
+template <typename S, int kPanel>
 __device__ void panel_factor_dispatch(Smem<S> &s, int kb, int rows, int c0, int mb) {
   switch ((rows + 31) / 32) {
-    case 1: panel_factor<S, kTT, 1>(s, kb, rows, c0, mb); break;
-    case 2: panel_factor<S, kTT, 2>(s, kb, rows, c0, mb); break;
-    case 3: panel_factor<S, kTT, 3>(s, kb, rows, c0, mb); break;
-    case 4: panel_factor<S, kTT, 4>(s, kb, rows, c0, mb); break;
-    case 5: panel_factor<S, kTT, 5>(s, kb, rows, c0, mb); break;
-    case 6: panel_factor<S, kTT, 6>(s, kb, rows, c0, mb); break;
-    case 7: panel_factor<S, kTT, 7>(s, kb, rows, c0, mb); break;
-    default: panel_factor<S, kTT, 8>(s, kb, rows, c0, mb); break;
+    case 1: panel_factor<S, kPanel, 1>(s, kb, rows, c0, mb); break;
+    case 2: panel_factor<S, kPanel, 2>(s, kb, rows, c0, mb); break;
+    case 3: panel_factor<S, kPanel, 3>(s, kb, rows, c0, mb); break;
+    case 4: panel_factor<S, kPanel, 4>(s, kb, rows, c0, mb); break;
+    case 5: panel_factor<S, kPanel, 5>(s, kb, rows, c0, mb); break;
+    case 6: panel_factor<S, kPanel, 6>(s, kb, rows, c0, mb); break;
+    case 7: panel_factor<S, kPanel, 7>(s, kb, rows, c0, mb); break;
+    default: panel_factor<S, kPanel, 8>(s, kb, rows, c0, mb); break;
   }
 }
 
@@ -828,7 +831,7 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
     Real *blk = tile + c0 + static_cast<int64_t>(c0) * p.lda;
     load_block(s.V, s.ldv, blk, p.lda, rows, kb);
     __syncthreads();
-    panel_factor_dispatch<S, false>(s, kb, rows, c0, mb);
+    panel_factor_dispatch<S, 0>(s, kb, rows, c0, mb);
     phase_mark(s.ph, 0);
     store_block(blk, p.lda, s.V, s.ldv, rows, kb);
     __syncthreads();
@@ -862,7 +865,10 @@ __device__ void task_geqrt(const ExecParams &p, Smem<S> &s, int i, int k) {
 // TTQRT(i,piv,k): QR of the upper triangle of tile (piv,k) stacked on the upper
 // triangle of tile (i,k); reflector c acts on row c of (piv,k) and rows 0..c of (i,k),
 // its tail is stored in column c of (i,k)'s upper triangle.
-template <typename Real, typename S>
+// TSQRT(i,piv,k) (kTS): the same with the whole square tile (i,k) below the triangle
+// (Algorithm "elimSQ"): reflector c acts on row c of (piv,k) and every row of (i,k), its
+// tail overwrites column c of (i,k).
+template <typename Real, typename S, bool kTS>
 __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int k) {
   const TileGeom geo{p.m, p.n, p.nb};
   const int nb = p.nb, ib = p.ib;
@@ -879,22 +885,22 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
       store_t(Tt, ib, c0, width, s, 0);
       continue;
     }
-    const int rb = min(c0 + kb, mb);  // rows of tile i touched by this block
-    // P2 = upper part of tile i, rows 0..rb-1, columns c0..c0+kb-1
+    const int rb = kTS ? mb : min(c0 + kb, mb);  // rows of tile i touched by this block
+    // P2 = tile i, rows 0..rb-1 (TT: its upper part only), columns c0..c0+kb-1
     load_block_mode(s.V, s.ldv, t2 + static_cast<int64_t>(c0) * p.lda, p.lda, rb, kb,
-                    [c0](int r, int c) { return r <= c0 + c ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
+                    [c0](int r, int c) { return (kTS || r <= c0 + c) ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
     // P1 = upper part of the diagonal block of R(piv)
     load_block_mode(s.P1, s.ldt, t1 + c0 + static_cast<int64_t>(c0) * p.lda, p.lda, kb, kb,
                     [](int r, int c) { return r <= c ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
     __syncthreads();
-    panel_factor_dispatch<S, true>(s, kb, rb, c0, mb);
+    panel_factor_dispatch<S, kTS ? 2 : 1>(s, kb, rb, c0, mb);
     phase_mark(s.ph, 0);
     panel_gram(s, kb, rb);
     build_t(s, kb);
-    // write back the upper parts only (the lower parts hold GEQRT reflectors)
+    // write back (TT: the upper parts only, the lower parts hold GEQRT reflectors)
     for (int c = warp; c < kb; c += kWarps)
       for (int r = lane; r < rb; r += 32)
-        if (r <= c0 + c) t2[r + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.V[r + c * s.ldv]);
+        if (kTS || r <= c0 + c) t2[r + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.V[r + c * s.ldv]);
     for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
       const int c = idx / kb, r = idx - c * kb;
       if (r <= c) t1[(c0 + r) + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.P1[r + c * s.ldt]);
@@ -955,10 +961,11 @@ __device__ void task_unmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *cp
 }
 
 // TTMQR: [C1; C2] <- Q^T [C1; C2] (or Q [C1; C2]) with the reflectors of the TTQRT that
-// zeroed tile (i,k).  C1 is the pivot row's tile (nb rows), C2 row i's tile (mb rows).
+// zeroed tile (i,k) (ts: of the TSQRT, whose reflectors fill the whole tile).  C1 is the
+// pivot row's tile (nb rows), C2 row i's tile (mb rows).
 template <typename Real, typename S, typename CT>
 __device__ void task_ttmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *c1ptr, CT *c2ptr,
-                           int64_t ldc, int ncols, bool transpose_q) {
+                           int64_t ldc, int ncols, bool transpose_q, bool ts = false) {
   const TileGeom geo{p.m, p.n, p.nb};
   const int nb = p.nb, ib = p.ib;
   const Real *vt = tile_ptr(static_cast<Real *>(p.A), p.lda, nb, i, k);
@@ -974,9 +981,9 @@ __device__ void task_ttmqr(const ExecParams &p, Smem<S> &s, int i, int k, CT *c1
     load_block(s.C, s.ldv, b2, ldc, mb, w);
     for (int bb = 0; bb < nblk; ++bb) {
       const int b = transpose_q ? nblk - 1 - bb : bb;
-      const int c0 = b * ib, kb = min(ib, K - c0), rb = min(c0 + kb, mb);
-      load_block_mode(s.V, s.ldv, vt + static_cast<int64_t>(c0) * p.lda, p.lda, rb, kb, [c0](int r, int c) {
-        return r <= c0 + c ? static_cast<int>(kLoad) : static_cast<int>(kZero);
+      const int c0 = b * ib, kb = min(ib, K - c0), rb = ts ? mb : min(c0 + kb, mb);
+      load_block_mode(s.V, s.ldv, vt + static_cast<int64_t>(c0) * p.lda, p.lda, rb, kb, [c0, ts](int r, int c) {
+        return (ts || r <= c0 + c) ? static_cast<int>(kLoad) : static_cast<int>(kZero);
       });
       load_t(s.T, s.ldt, Tt, ib, c0, kb);
       __syncthreads();
@@ -1036,9 +1043,9 @@ __device__ void prefetch_task_tiles(const ExecParams &p, int ta) {
   int tcol = task.k, nt = 0;  // tile column; tile rows task.i and (second tile) task.piv
   switch (task.kind) {
     case kGeqrt: nt = 1; break;
-    case kTtqrt: nt = 2; break;
+    case kTtqrt: case kTsqrt: nt = 2; break;
     case kUnmqr: tcol = task.j; nt = 1; break;
-    case kTtmqr: tcol = task.j; nt = 2; break;
+    case kTtmqr: case kTsmqr: tcol = task.j; nt = 2; break;
     default: return;
   }
   for (int w = threadIdx.x; w < nt * nb; w += kThreads) {
@@ -1058,6 +1065,7 @@ template <typename Real, typename S, bool kMixed>
 __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_task, s_stop, s_ahead;
+  __shared__ int s_fail;  // a bounded tensor-core wait of this block gave up
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ uint32_t s_tmem;
   __shared__ uint64_t s_ph[5];
@@ -1066,6 +1074,9 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   s0.ph = p.trace ? s_ph : nullptr;
   MixedState ms{};
   ms.ph = s0.ph;
+  ms.fail = &s_fail;
+  ms.ld_pending = false;
+  if (threadIdx.x == 0) s_fail = 0;
   if (kMixed) {
     if (threadIdx.x == 0) {
       umma::mbar_init(&s_bar[0], 1);
@@ -1091,7 +1102,8 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
   for (;;) {
     if (threadIdx.x == 0) {
       const int t = atomicAdd(p.next, 1);
-      int stop = t >= p.ntask;
+      // a wait that gave up anywhere stops every CTA at its next claim
+      int stop = t >= p.ntask || ld_relaxed_gpu(p.status) != 0;
       s_ahead = t + static_cast<int>(gridDim.x) < p.ntask ? t + static_cast<int>(gridDim.x) : -1;
       const uint64_t t_claim = p.trace ? globaltimer_ns() : 0;
       if (!stop && !wait_ready(p, t)) stop = 1;
@@ -1148,11 +1160,20 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
         }
         break;
       case kTtqrt:
-        task_ttqrt<Real, S>(q, s, task.i, task.piv, task.k);
+        task_ttqrt<Real, S, false>(q, s, task.i, task.piv, task.k);
         if (kMixed) {
           __syncthreads();
           phase_mark(s.ph, 2);
-          prep_ttqrt_ops(q, smem_raw, task.i, task.k);
+          prep_ttqrt_ops(q, smem_raw, task.i, task.k, false);
+          phase_mark(s.ph, 3);
+        }
+        break;
+      case kTsqrt:
+        task_ttqrt<Real, S, true>(q, s, task.i, task.piv, task.k);
+        if (kMixed) {
+          __syncthreads();
+          phase_mark(s.ph, 2);
+          prep_ttqrt_ops(q, smem_raw, task.i, task.k, true);
           phase_mark(s.ph, 3);
         }
         break;
@@ -1167,15 +1188,18 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
                                   ncols, false);
         break;
       }
-      case kTtmqr: {
+      case kTtmqr:
+      case kTsmqr: {
         if (kMixed) {
+          // the TSQRT operand images are dense, the TTQRT ones upper triangular: one kernel
           task_ttmqr_umma(q, smem_raw, ms, task.i, task.piv, task.k, task.j);
           break;
         }
         Real *A = static_cast<Real *>(q.A);
         const int ncols = static_cast<int>(lmin(nb, q.n - int64_t(task.j) * nb));
         task_ttmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.piv, task.j),
-                                  tile_ptr(A, q.lda, nb, task.i, task.j), q.lda, ncols, false);
+                                  tile_ptr(A, q.lda, nb, task.i, task.j), q.lda, ncols, false,
+                                  task.kind == kTsmqr);
         break;
       }
       case kUnmqrB:
@@ -1183,15 +1207,18 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
                                     static_cast<int>(q.nrhs), q.trans != 0);
         break;
       case kTtmqrB:
+      case kTsmqrB:
         task_ttmqr<Real, S, double>(q, s, task.i, task.k, q.B + static_cast<int64_t>(task.piv) * nb,
                                     q.B + static_cast<int64_t>(task.i) * nb, q.ldb,
-                                    static_cast<int>(q.nrhs), q.trans != 0);
+                                    static_cast<int>(q.nrhs), q.trans != 0, task.kind == kTsmqrB);
         break;
       default:
         break;
     }
     __threadfence();
     __syncthreads();
+    // an abandoned task (a tensor-core wait gave up) releases no successor: stop here
+    if (kMixed && s_fail) break;
     if (threadIdx.x == 0) {
       if (p.trace) {
         p.trace[8 * static_cast<int64_t>(t) + 2] = static_cast<int64_t>(globaltimer_ns());
@@ -1202,6 +1229,15 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     }
   }
   if (kMixed) {
+    if (s_fail && threadIdx.x == 0) {
+      // drain the tensor-core work this thread issued (bounded) before tensor memory is
+      // freed: one more commit tracks every MMA issued so far, and a pending operand copy
+      // completes its own load phase
+      constexpr uint64_t kDrainNs = 10ull * 1000 * 1000;
+      umma::commit(ms.bar_mma);
+      umma::mbar_wait(ms.bar_mma, ms.mma_phase, kDrainNs);
+      if (ms.ld_pending) umma::mbar_wait(ms.bar_ld, ms.ld_phase, kDrainNs);
+    }
     umma::fence_before();
     __syncthreads();
     if (threadIdx.x < 32) umma::tmem_dealloc(s_tmem, 512);

@@ -49,9 +49,13 @@ int GraphBuilder::add(const Task &t, int w, const int *reads, int nr, const int 
   return id;
 }
 
-std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k) {
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square) {
   std::vector<int> geqrt_ids;
   for (int i = k; i < p; ++i) {
+    if (square && square[i]) {
+      geqrt_ids.push_back(-1);
+      continue;
+    }
     const int rw[2] = {region_L(q, i, k), region_U(q, i, k)};
     geqrt_ids.push_back(b.add(Task{kGeqrt, i, -1, (int16_t)k, -1}, kWGeqrt, nullptr, 0, rw, 2));
     for (int j = k + 1; j < q; ++j) {
@@ -63,8 +67,20 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k) {
   return geqrt_ids;
 }
 
-void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col) {
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square) {
   for (const Elim &e : col) {
+    if (square && square[e.i]) {
+      // TSQRT overwrites the whole square tile (i,k) with its reflectors; TSMQR reads it
+      const int wr3[3] = {region_U(q, e.piv, k), region_L(q, e.i, k), region_U(q, e.i, k)};
+      b.add(Task{kTsqrt, e.i, e.piv, (int16_t)k, -1}, kWTsqrt, nullptr, 0, wr3, 3);
+      for (int j = k + 1; j < q; ++j) {
+        const int rd[2] = {region_L(q, e.i, k), region_U(q, e.i, k)};
+        const int w4[4] = {region_L(q, e.piv, j), region_U(q, e.piv, j), region_L(q, e.i, j),
+                           region_U(q, e.i, j)};
+        b.add(Task{kTsmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, kWTsmqr, rd, 2, w4, 4);
+      }
+      continue;
+    }
     const int wr[2] = {region_U(q, e.piv, k), region_U(q, e.i, k)};
     b.add(Task{kTtqrt, e.i, e.piv, (int16_t)k, -1}, kWTtqrt, nullptr, 0, wr, 2);
     for (int j = k + 1; j < q; ++j) {
@@ -219,7 +235,7 @@ void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge, const OrderSpe
     g.indeg[r] = static_cast<int32_t>(b.preds[t].size());
     g.critical_path = std::max<int64_t>(g.critical_path, b.finish[t]);
     const int kind = b.tasks[t].kind;
-    if (kind >= kGeqrt && kind <= kTtmqr) g.counts[kind]++;
+    if (kind >= 0 && kind < kNumKinds) g.counts[kind]++;
   }
   int64_t edge = 0;
   for (int r = 0; r < n; ++r) {
@@ -236,32 +252,48 @@ void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge, const OrderSpe
   }
 }
 
-void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims) {
+std::vector<std::vector<char>> ts_square_rows(int p, int q, const std::vector<Elim> &elims) {
+  const int kmax = std::min(p, q);
+  std::vector<std::vector<char>> pivot(kmax, std::vector<char>(p, 0)), square(kmax, std::vector<char>(p, 0));
+  for (const Elim &e : elims) pivot[e.k][e.piv] = 1;
+  for (const Elim &e : elims)
+    if (!pivot[e.k][e.i]) square[e.k][e.i] = 1;
+  return square;
+}
+
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts) {
   const int kmax = std::min(p, q);
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : elims) by_col[e.k].push_back(e);
+  std::vector<std::vector<char>> square;
+  if (ts) square = ts_square_rows(p, q, elims);
   for (int k = 0; k < kmax; ++k) {
-    add_panel_tasks(b, p, q, k);
-    add_elim_tasks(b, q, k, by_col[k]);
+    const char *sq = ts ? square[k].data() : nullptr;
+    add_panel_tasks(b, p, q, k, sq);
+    add_elim_tasks(b, q, k, by_col[k], sq);
   }
 }
 
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge,
-                        const OrderSpec *order) {
+                        const OrderSpec *order, bool ts) {
   GraphBuilder b(p * q * 2);
-  add_factor_program(b, p, q, elims);
+  add_factor_program(b, p, q, elims, ts);
   finalize_graph(b, g, drop_edge, order);
 }
 
-void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g) {
+void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g, bool ts) {
   // Regions are the tile rows of the right-hand-side block; the factors are read-only.
   const int kmax = std::min(p, q);
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : elims) by_col[e.k].push_back(e);
+  std::vector<std::vector<char>> square;
+  if (ts) square = ts_square_rows(p, q, elims);
   std::vector<Task> ops;
   for (int k = 0; k < kmax; ++k) {
-    for (int i = k; i < p; ++i) ops.push_back(Task{kUnmqrB, i, -1, (int16_t)k, -1});
-    for (const Elim &e : by_col[k]) ops.push_back(Task{kTtmqrB, e.i, e.piv, (int16_t)k, -1});
+    for (int i = k; i < p; ++i)
+      if (!ts || !square[k][i]) ops.push_back(Task{kUnmqrB, i, -1, (int16_t)k, -1});
+    for (const Elim &e : by_col[k])
+      ops.push_back(Task{ts && square[k][e.i] ? kTsmqrB : kTtmqrB, e.i, e.piv, (int16_t)k, -1});
   }
   if (reverse) std::reverse(ops.begin(), ops.end());
   GraphBuilder b(p);
@@ -271,7 +303,7 @@ void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool rever
       b.add(t, kWUnmqr, nullptr, 0, wr, 1);
     } else {
       const int wr[2] = {t.piv, t.i};
-      b.add(t, kWTtmqr, nullptr, 0, wr, 2);
+      b.add(t, t.kind == kTsmqrB ? kWTsmqr : kWTtmqr, nullptr, 0, wr, 2);
     }
   }
   finalize_graph(b, g);

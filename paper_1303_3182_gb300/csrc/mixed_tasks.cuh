@@ -49,7 +49,9 @@ struct MixedState {
   uint64_t *bar_ld, *bar_mma;
   uint32_t tmem;
   uint32_t ld_phase, mma_phase;
-  uint64_t *ph;  // phase clock of the execution trace, or null
+  uint64_t *ph;      // phase clock of the execution trace, or null
+  volatile int *fail;  // shared: a bounded wait of this block gave up (the task is abandoned)
+  bool ld_pending;   // thread 0: a bulk copy was issued whose completion was not yet seen
 };
 
 __device__ __forceinline__ unsigned char *ops_slot(const ExecParams &p, int i, int k, int which) {
@@ -323,7 +325,8 @@ __device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
 }
 
 // Operand images of TTQRT(i,piv,k): V2 (upper part of tile i), Z2 = V2 T_full^T, T_full^T.
-__device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, int k) {
+// ts: of TSQRT(i,piv,k), whose V2 is the whole tile i (Algorithm "elimSQ").
+__device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, int k, bool ts) {
   const TileGeom geo{p.m, p.n, kMNB};
   float *Vs = reinterpret_cast<float *>(raw);
   float *Ts = Vs + kMNB * kMLD;
@@ -331,16 +334,20 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   const float *tile = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, k);
   const float *Tt = t_ptr(static_cast<float *>(p.T), p.P, p.ib, kMNB, i, k, 1);
   const int mb = geo.rows(i), K = geo.cols(k);
-  load_block_mode(Vs, kMLD, tile, p.lda, kMNB, kMNB, [K, mb](int r, int c) {
-    return (c < K && r < mb && r <= c) ? static_cast<int>(kLoad) : static_cast<int>(kZero);
+  load_block_mode(Vs, kMLD, tile, p.lda, kMNB, kMNB, [K, mb, ts](int r, int c) {
+    return (c < K && r < mb && (ts || r <= c)) ? static_cast<int>(kLoad) : static_cast<int>(kZero);
   });
   load_t_blocks(Ts, Tt, p.ib);
   __syncthreads();
-  // G(a, c) = v_a . v_c over rows r <= a (the tails live in the upper triangle)
-  gram_upper(Gs, Vs, [](int c_lo, int &r0, int &r1) { r0 = 0; r1 = min(c_lo + 16, kMNB); });
+  // G(a, c) = v_a . v_c over the rows the tails occupy (TT: r <= a, within the upper
+  // triangle; TS: every row)
+  if (ts)
+    gram_upper(Gs, Vs, [](int, int &r0, int &r1) { r0 = 0; r1 = kMNB; });
+  else
+    gram_upper(Gs, Vs, [](int c_lo, int &r0, int &r1) { r0 = 0; r1 = min(c_lo + 16, kMNB); });
   __syncthreads();
   assemble_t(Ts, Gs, p.ib);
-  // Z2(r, a) = sum_{b >= max(a, r)} V2(r, b) T(a, b)
+  // Z2(r, a) = sum_{b >= a} V2(r, b) T(a, b)
   v_times_tt(Gs, Vs, Ts, [](int a_lo, int &b0, int &b1) { b0 = a_lo; b1 = kMNB; });
   __syncthreads();
   unsigned char *slot = ops_slot(p, i, k, 1);
@@ -479,10 +486,35 @@ __device__ __forceinline__ void sync_all_tc() {
   umma::fence_after();
 }
 
-// Records a failed bounded wait in the status word.
-__device__ __forceinline__ void wait_or_flag(const ExecParams &p, uint64_t *bar, uint32_t parity) {
-  if (!umma::mbar_wait(bar, parity, 1ull << 26)) atomicCAS(p.status, 0, kStatusTimeout | (0x7fffff << 8));
+// Bounded wait on an mbarrier phase.  On expiry (or when another thread of the block
+// already gave up) it records kStatusTimeout in the status word, raises the block's
+// failure flag and returns false; the task then stops issuing work at its next block
+// barrier (task_failed), its successors are never released and the executor drains the
+// tensor-core work in flight before it frees tensor memory.
+__device__ __forceinline__ bool wait_or_flag(const ExecParams &p, MixedState &ms, uint64_t *bar,
+                                             uint32_t parity) {
+  if (*ms.fail) return false;
+  if (umma::mbar_wait(bar, parity, static_cast<uint64_t>(p.wait_limit_ns), ms.fail)) return true;
+  atomicCAS(p.status, 0, kStatusTimeout | (0x7fffff << 8));
+  *ms.fail = 1;
+  return false;
 }
+
+// Thread 0 waits for the operand copies it issued.
+__device__ __forceinline__ bool wait_loads(const ExecParams &p, MixedState &ms) {
+  const bool ok = wait_or_flag(p, ms, ms.bar_ld, ms.ld_phase);
+  if (ok) ms.ld_pending = false;
+  return ok;
+}
+
+// Thread 0 issues bulk copies of "bytes" in total on the load barrier.
+__device__ __forceinline__ void expect_loads(MixedState &ms, uint32_t bytes) {
+  umma::mbar_expect_tx(ms.bar_ld, bytes);
+  ms.ld_pending = true;
+}
+
+// After a block barrier every thread reads the same failure flag.
+__device__ __forceinline__ bool task_failed(const MixedState &ms) { return *ms.fail != 0; }
 
 // Shared-memory operand buffers: X and Y always; a third buffer Zb when the parts of
 // three operands fit (nparts <= 2), which lets the second operand load early.
@@ -511,7 +543,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   const unsigned char *imgV = slot, *imgZ = slot + b.bytes;
   unsigned char *bufZ = b.Zb ? b.Zb : b.Y;
   if (threadIdx.x == 0) {
-    umma::mbar_expect_tx(ms.bar_ld, b.Zb ? 2 * b.bytes : b.bytes);
+    expect_loads(ms, b.Zb ? 2 * b.bytes : b.bytes);
     umma::bulk_g2s(b.Y, imgV, b.bytes, ms.bar_ld);
     if (b.Zb) umma::bulk_g2s(b.Zb, imgZ, b.bytes, ms.bar_ld);
   }
@@ -522,22 +554,23 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
     umma::fence_proxy_async();
     sync_all_tc();
+    if (task_failed(ms)) return;
     if (threadIdx.x == 0) {
-      if (h == 0) {
-        wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+      const bool ok = h != 0 || wait_loads(p, ms);
+      if (ok) {
         umma::fence_after();
+        issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 0, 4 * h, 4 * h + 4);
+        if (h == 1) umma::commit(ms.bar_mma);
       }
-      issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 0, 4 * h, 4 * h + 4);
-      if (h == 1) umma::commit(ms.bar_mma);
     }
   }
   ms.ld_phase ^= 1;
   phase_mark(ms.ph, 0);
-  wait_or_flag(p, ms.bar_mma, ms.mma_phase);
+  wait_or_flag(p, ms, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
-  if (!b.Zb && threadIdx.x == 0) {  // Y is free again: fetch Z into it
-    umma::mbar_expect_tx(ms.bar_ld, b.bytes);
+  if (!b.Zb && threadIdx.x == 0 && !*ms.fail) {  // Y is free again: fetch Z into it
+    expect_loads(ms, b.bytes);
     umma::bulk_g2s(b.Y, imgZ, b.bytes, ms.bar_ld);
   }
   phase_mark(ms.ph, 1);
@@ -545,20 +578,23 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h);
     umma::fence_proxy_async();
     sync_all_tc();
+    if (task_failed(ms)) return;
     if (threadIdx.x == 0) {
-      if (h == 0 && !b.Zb) {
-        wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+      const bool ok = !(h == 0 && !b.Zb) || wait_loads(p, ms);
+      if (ok) {
         umma::fence_after();
+        issue_gemm(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
+        if (h == 1) umma::commit(ms.bar_mma);
       }
-      issue_gemm(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
-      if (h == 1) umma::commit(ms.bar_mma);
     }
   }
   if (!b.Zb) ms.ld_phase ^= 1;
   phase_mark(ms.ph, 2);
-  wait_or_flag(p, ms.bar_mma, ms.mma_phase);
+  wait_or_flag(p, ms, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
+  sync_all_tc();
+  if (task_failed(ms)) return;
   tmem_to_tile(C, p.lda, mb, ncols, ms.tmem + 128);
   sync_all_tc();
   phase_mark(ms.ph, 3);
@@ -574,7 +610,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   const unsigned char *slot = ops_slot(p, i, k, 1);
   const unsigned char *imgV = slot, *imgZ = slot + b.bytes, *imgT = slot + 2 * b.bytes;
   if (threadIdx.x == 0) {
-    umma::mbar_expect_tx(ms.bar_ld, b.Zb ? 2 * b.bytes : b.bytes);
+    expect_loads(ms, b.Zb ? 2 * b.bytes : b.bytes);
     umma::bulk_g2s(b.Y, imgV, b.bytes, ms.bar_ld);
     if (b.Zb) umma::bulk_g2s(b.Zb, imgZ, b.bytes, ms.bar_ld);
   }
@@ -610,22 +646,23 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
     umma::fence_proxy_async();
     sync_all_tc();
+    if (task_failed(ms)) return;
     if (threadIdx.x == 0) {
-      if (h == 0) {
-        wait_or_flag(p, ms.bar_ld, ms.ld_phase);
+      const bool ok = h != 0 || wait_loads(p, ms);
+      if (ok) {
         umma::fence_after();
+        issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 1, 4 * h, 4 * h + 4);
+        if (h == 1) umma::commit(ms.bar_mma);
       }
-      issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 1, 4 * h, 4 * h + 4);
-      if (h == 1) umma::commit(ms.bar_mma);
     }
   }
   ms.ld_phase ^= 1;
   phase_mark(ms.ph, 0);
-  wait_or_flag(p, ms.bar_mma, ms.mma_phase);
+  wait_or_flag(p, ms, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
-  if (threadIdx.x == 0) {  // Y is free: the next operand (Z2, or T^T when Z2 is resident)
-    umma::mbar_expect_tx(ms.bar_ld, b.bytes);
+  if (threadIdx.x == 0 && !*ms.fail) {  // Y is free: the next operand (Z2, or T^T when Z2 is resident)
+    expect_loads(ms, b.bytes);
     umma::bulk_g2s(b.Y, b.Zb ? imgT : imgZ, b.bytes, ms.bar_ld);
   }
   phase_mark(ms.ph, 1);
@@ -633,22 +670,22 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h);
     umma::fence_proxy_async();
     sync_all_tc();
+    if (task_failed(ms)) return;
     if (threadIdx.x == 0) {
       if (b.Zb) {
         issue_gemm(ms.tmem + 128, b.Zb, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);  // C2 -= Z2 W
-        if (h == 1) {
-          wait_or_flag(p, ms.bar_ld, ms.ld_phase);                                       // T^T in Y
+        if (h == 1 && wait_loads(p, ms)) {                                             // T^T in Y
           umma::fence_after();
           issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);                    // C1 -= T^T W
           umma::commit(ms.bar_mma);
         }
       } else {
-        if (h == 0) {
-          wait_or_flag(p, ms.bar_ld, ms.ld_phase);                                       // Z2 in Y
+        const bool ok = h != 0 || wait_loads(p, ms);                                   // Z2 in Y
+        if (ok) {
           umma::fence_after();
+          issue_gemm(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
+          if (h == 1) umma::commit(ms.bar_mma);
         }
-        issue_gemm(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
-        if (h == 1) umma::commit(ms.bar_mma);
       }
     }
   }
@@ -656,22 +693,27 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   phase_mark(ms.ph, 2);
   if (!b.Zb) {
     // Y held Z2: wait for that product, then bring T^T into Y
-    wait_or_flag(p, ms.bar_mma, ms.mma_phase);
+    wait_or_flag(p, ms, ms.bar_mma, ms.mma_phase);
     ms.mma_phase ^= 1;
     umma::fence_after();
+    sync_all_tc();
+    if (task_failed(ms)) return;
     if (threadIdx.x == 0) {
-      umma::mbar_expect_tx(ms.bar_ld, b.bytes);
+      expect_loads(ms, b.bytes);
       umma::bulk_g2s(b.Y, imgT, b.bytes, ms.bar_ld);
-      wait_or_flag(p, ms.bar_ld, ms.ld_phase);
-      umma::fence_after();
-      issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);
-      umma::commit(ms.bar_mma);
+      if (wait_loads(p, ms)) {
+        umma::fence_after();
+        issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);
+        umma::commit(ms.bar_mma);
+      }
     }
     ms.ld_phase ^= 1;
   }
-  wait_or_flag(p, ms.bar_mma, ms.mma_phase);
+  wait_or_flag(p, ms, ms.bar_mma, ms.mma_phase);
   ms.mma_phase ^= 1;
   umma::fence_after();
+  sync_all_tc();
+  if (task_failed(ms)) return;
   tmem_to_tile(C2, p.lda, mb, ncols, ms.tmem + 128);
   tmem_to_tile(C1, p.lda, kMNB, ncols, ms.tmem + 256);
   sync_all_tc();

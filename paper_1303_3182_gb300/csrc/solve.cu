@@ -271,7 +271,10 @@ int32_t *g_static_ptr[kMaxDevices] = {};
 
 // Device address of the static scratch on the current device.  The host-side symbol is
 // only a stand-in, so the address is looked up once per device (with that device
-// current) and cached; this lookup is the only set-up the entry point needs.
+// current) and cached; this lookup is the only set-up the entry point needs.  The cached
+// address belongs to the device's primary context: after a cudaDeviceReset the module is
+// loaded again and the array may move, so tqr_finalize() forgets the cached addresses
+// (reset_static_scratch) and the next call looks them up again.
 int static_scratch(int32_t **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -291,6 +294,11 @@ int static_scratch(int32_t **out) {
   return TQR_OK;
 }
 }  // namespace
+
+void reset_static_scratch() {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  for (int d = 0; d < kMaxDevices; ++d) g_static_ptr[d] = nullptr;
+}
 
 }  // namespace tqr
 
@@ -336,5 +344,9 @@ extern "C" int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, 
     set_error(std::string("tqr_trsm_static: ") + cudaGetErrorString(e));
     return TQR_ECUDA;
   }
-  return h != 0 ? TQR_ETIMEOUT : TQR_OK;
+  if (h != 0) {
+    set_error("tqr_trsm_static: device wait exceeded the limit at block " + std::to_string(h >> 8));
+    return TQR_ETIMEOUT;
+  }
+  return TQR_OK;
 }

@@ -14,10 +14,22 @@ struct Elim {
 
 // Kernel weights in units of nb^3/3 flops (Table "Kernels for tiled QR").
 constexpr int kWGeqrt = 4, kWTtqrt = 2, kWUnmqr = 6, kWTtmqr = 6;
+constexpr int kWTsqrt = 6, kWTsmqr = 12;
+
+// Tree argument flag (TQR_TS in tqr.h): the TS form of the list - every row that is
+// never a pivot in a column is zeroed there by TSQRT/TSMQR (Algorithm "elimSQ") while
+// still square, the other eliminations keep the TT kernels.
+constexpr int kTreeTS = 16;
+inline int tree_base(int tree) { return tree & ~kTreeTS; }
+inline bool tree_ts(int tree) { return (tree & kTreeTS) != 0; }
 
 // Elimination list of a tree in canonical order (Section 3.2).  Returns false on an
-// unknown tree.  Host only.
+// unknown tree.  The TS flag of "tree" is ignored (the list is the same).  Host only.
 bool elimination_list(int p, int q, int tree, int bs, std::vector<Elim> &out);
+
+// Rows of each column zeroed by TS kernels in the TS form of a list: square[k][i] != 0
+// when row i is never a pivot of column k's eliminations (and is zeroed in column k).
+std::vector<std::vector<char>> ts_square_rows(int p, int q, const std::vector<Elim> &elims);
 
 // Task kinds of the tile task graph.
 enum TaskKind : int32_t {
@@ -27,7 +39,11 @@ enum TaskKind : int32_t {
   kTtmqr = 3,   // TTMQR(i,piv,k,j)
   kUnmqrB = 4,  // UNMQR(i,k) applied to tile row i of a right-hand-side block
   kTtmqrB = 5,  // TTMQR(i,piv,k) applied to tile rows (piv, i) of a right-hand-side block
+  kTsqrt = 6,   // TSQRT(i,piv,k): zeroes the square tile (i,k) under R(piv,k)
+  kTsmqr = 7,   // TSMQR(i,piv,k,j)
+  kTsmqrB = 8,  // TSMQR(i,piv,k) applied to tile rows (piv, i) of a right-hand-side block
 };
+constexpr int kNumKinds = 9;
 
 // A task as the device executor reads it (16 bytes).
 struct Task {
@@ -46,7 +62,7 @@ struct Graph {
   std::vector<int32_t> indeg;        // number of predecessors
   std::vector<int32_t> weight;       // kernel weight per task
   int64_t critical_path = 0;         // longest weighted path (unbounded processors)
-  int64_t counts[4] = {0, 0, 0, 0};  // GEQRT, TTQRT, UNMQR, TTMQR
+  int64_t counts[kNumKinds] = {};    // tasks per kind
   std::vector<int64_t> start;        // earliest start (unbounded processors), executor order
   std::vector<int64_t> bottom;       // longest weighted path to a sink, task included
 };
@@ -81,27 +97,31 @@ struct GraphBuilder {
 // (GEQRT reflectors) and an upper part (R, then TTQRT reflectors).
 inline int region_L(int q, int i, int j) { return (i * q + j) * 2; }
 inline int region_U(int q, int i, int j) { return (i * q + j) * 2 + 1; }
-// Adds GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k of panel k; returns the task
-// ids of the GEQRTs (index i - k).
-std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k);
-// Adds TTQRT(i,piv,k) and TTMQR(i,piv,k,j) for the eliminations of panel k, in order.
-void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col);
+// Adds GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k of panel k except the rows with
+// square[i] != 0 (zeroed by TS kernels); returns the task ids of the GEQRTs (index i - k,
+// -1 for a skipped row).
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square = nullptr);
+// Adds the eliminations of panel k in order: TSQRT / TSMQR(i,piv,k,j) when square[i] != 0,
+// TTQRT / TTMQR(i,piv,k,j) otherwise.
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square = nullptr);
 // Orders a built graph for the executor (earliest start, then longest remaining path)
 // and fills the successor CSR.
 // Executor (claim) order of a factorization graph.  mode 0: earliest start with
 // unbounded processors (thesis weights), then the longer remaining path first.  mode 1:
 // the bounded-processor list schedule of thesis Chapter 5 ("CP Method") on nproc
-// processors with per-kind weights w[4] (GEQRT, TTQRT, UNMQR, TTMQR), tasks ordered by
-// their start in that schedule.
+// processors with per-kind weights w[kind], tasks ordered by their start in that
+// schedule.
 struct OrderSpec {
   int mode = 0;
   int nproc = 1;
-  int64_t w[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr};
+  // per task kind (TaskKind index; the apply-Q kinds are unused)
+  int64_t w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr};
   int id = 0;  // identity of the weight set in the plan cache (built-in sets < 0)
 };
 void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1, const OrderSpec *order = nullptr);
-// Tasks of the sequential program (all panels, in column order) added to b.
-void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims);
+// Tasks of the sequential program (all panels, in column order) added to b; ts: the TS
+// form of the list.
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts = false);
 // Backflow priorities (a task's weight plus the largest priority of its successors) of
 // a graph in program order with successor lists succ and weights w.
 std::vector<int64_t> backflow_priorities(const std::vector<std::vector<int32_t>> &succ,
@@ -121,9 +141,9 @@ int64_t alap_derived_bound(const std::vector<int64_t> &w, const std::vector<int6
 // (column-by-column program of Algorithm "elimTR"; dependencies from the tile regions
 // each kernel reads and writes, Eq. ttdeps / ttdeps2).
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
-                        int64_t drop_edge = -1, const OrderSpec *order = nullptr);
+                        int64_t drop_edge = -1, const OrderSpec *order = nullptr, bool ts = false);
 // Builds the graph that applies Q^T (or Q when reverse) to a right-hand-side block.
-void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g);
+void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g, bool ts = false);
 
 void set_error(const std::string &msg);
 // Number of kernels this library has launched (tqr_launch_count).
@@ -202,6 +222,8 @@ int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, doub
                 int64_t ldb, int64_t nrhs, int32_t *flags, int32_t *status,
                 int64_t wait_limit_ns, void *stream, bool lower_transposed = false);
 int trsm_flag_count(int64_t n);
+// Forgets the cached device addresses of tqr_trsm_static's fixed scratch (tqr_finalize).
+void reset_static_scratch();
 // Inverses of the 64 x 64 diagonal blocks of an upper-triangular R (FP64, 64*64 doubles
 // per block; identity on the padding of a partial last block).
 int launch_diag_inverse(int64_t n, const void *A, int64_t lda, bool real_is_double, double *Dinv, void *stream);

@@ -118,9 +118,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false when the bound is hit.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t max_iter) {
+// Bounded wait for the phase with the given parity; false when the bound is hit: more
+// than limit_ns nanoseconds of %globaltimer (checked every 256 polls), an iteration cap
+// as a second bound, or *abort (shared memory) set by another thread of the block.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns,
+                                          const volatile int *abort = nullptr) {
   const uint32_t a = smem_u32(bar);
+  const uint64_t max_iter = (limit_ns >> 2) + (1ull << 20);
+  uint64_t t0 = 0;
   for (uint64_t it = 0; it < max_iter; ++it) {
     uint32_t ok;
     asm volatile(
@@ -130,6 +135,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 255) == 255) {
+      if (abort && *abort) return false;
+      uint64_t now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > limit_ns)
+        return false;
+    }
   }
   return false;
 }

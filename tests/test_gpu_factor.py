@@ -47,14 +47,21 @@ def gpu_t_blocks(Tbuf, P, K, ib, nb, dtype):
     return arr.reshape(K, P, 2, nb, ib)  # [k][i][which] -> (nb cols, ib rows) row-major view
 
 
+def tree_and_ts(tree):
+    """(oracle tree id, TS form?) of a tree name or id (TS forms carry tqr.TS)."""
+    t = tqr.TREES[tree] if isinstance(tree, str) else tree
+    return t & ~tqr.TS, bool(t & tqr.TS)
+
+
 def compare_factor(A, nb, ib, tree, prec="fp64", bs=2):
     m, n = A.shape
     p, q = H.tile_grid(m, n, nb)
-    elims = E.elimination_list(p, q, tqr.TREES[tree] if isinstance(tree, str) else tree, bs=bs)
+    base, ts = tree_and_ts(tree)
+    elims = E.elimination_list(p, q, base, bs=bs)
     dtype = torch.float64 if prec == "fp64" else torch.float32
     if prec != "fp64":
         A = A.astype(np.float32).astype(np.float64)  # the oracle runs on the rounded input
-    F, Tg, Tt = H.tiled_qr(A, nb, ib, elims)
+    F, Tg, Tt = H.tiled_qr(A, nb, ib, elims, ts)
     Ad = to_dev(A, dtype)
     T = tqr.factor(Ad, nb, ib, tree, bs, prec)
     torch.cuda.synchronize()
@@ -98,14 +105,32 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("m,n,nb,ib,tree", CASES)
+TS_CASES = [
+    # the TS forms (TSQRT/TSMQR for the rows that never pivot), Algorithm "elimSQ"
+    (512, 128, 64, 16, "flat-ts"),      # Sameh-Kuck with TS kernels
+    (640, 320, 64, 32, "plasma-ts"),    # the PLASMA algorithm (bs = 2)
+    (640, 320, 64, 32, "binary-ts"),
+    (1000, 300, 64, 16, "greedy-ts"),   # ragged rows and columns
+    (640, 320, 64, 32, "fibonacci-ts"),
+    (640, 320, 64, 32, "grasap-ts"),
+    (37, 21, 8, 3, "greedy-ts"),
+    (128, 300, 64, 16, "flat-ts"),      # wide (p < q)
+    (2048, 64, 64, 32, "flat-ts"),      # one tile column
+    (1024, 512, 256, 32, "greedy-ts"),  # 256 x 256 tiles
+    (1000, 520, 256, 32, "plasma-ts"),  # ragged 256 tiles (bottom tile of 232 rows)
+    (9, 5, 1, 1, "flat-ts"),            # scalar tiles
+]
+
+
+@pytest.mark.parametrize("m,n,nb,ib,tree", CASES + TS_CASES)
 def test_factor_fp64_parity(m, n, nb, ib, tree):
     A = synthetic.gaussian(m, n, seed=1303318201 + m + n)
     compare_factor(A, nb, ib, tree)
 
 
 @pytest.mark.parametrize("m,n,nb,ib,tree", [(512, 128, 64, 16, "greedy"), (1000, 300, 64, 16, "asap"),
-                                            (300, 200, 32, 8, "flat")])
+                                            (300, 200, 32, 8, "flat"), (1000, 300, 64, 16, "plasma-ts"),
+                                            (300, 200, 32, 8, "flat-ts")])
 def test_factor_fp32_parity(m, n, nb, ib, tree):
     A = synthetic.gaussian(m, n, seed=77 + m)
     compare_factor(A, nb, ib, tree, prec="fp32")
@@ -145,16 +170,18 @@ def _q_times(Ad, T, Z, nb, ib, tree, trans, prec="fp64"):
 
 
 @pytest.mark.parametrize("m,n,nb,ib,tree", [(512, 128, 64, 16, "greedy"), (1000, 300, 64, 16, "fibonacci"),
-                                            (37, 21, 8, 3, "asap")])
+                                            (37, 21, 8, 3, "asap"), (1000, 300, 64, 16, "plasma-ts"),
+                                            (37, 21, 8, 3, "flat-ts")])
 def test_apply_q_parity_and_definition(m, n, nb, ib, tree):
     A = synthetic.gaussian(m, n, seed=11 + m)
     Ad, T, F, elims = compare_factor(A, nb, ib, tree)
     p, q = H.tile_grid(m, n, nb)
-    _, Tg, Tt = H.tiled_qr(A, nb, ib, elims)
+    ts = tree_and_ts(tree)[1]
+    _, Tg, Tt = H.tiled_qr(A, nb, ib, elims, ts)
     Z = synthetic.gaussian(m, 5, seed=3)
     for trans in (0, 1):
         got = _q_times(Ad, T, Z, nb, ib, tree, trans)
-        ref = H.apply_qt(F, Tg, Tt, nb, ib, elims, Z, transpose=(trans == 0))
+        ref = H.apply_qt(F, Tg, Tt, nb, ib, elims, Z, transpose=(trans == 0), ts=ts)
         assert np.max(np.abs(got - ref)) <= 64 * m * U64 * np.max(np.abs(ref)) * 4
     # definition: Q explicit from the GPU, A = Q R and Q^T Q = I
     Q = _q_times(Ad, T, np.eye(m), nb, ib, tree, 1)
@@ -168,15 +195,17 @@ def test_apply_q_parity_and_definition(m, n, nb, ib, tree):
 @pytest.mark.parametrize("m,n,nrhs,nb,ib,tree,cond", [(512, 128, 1, 64, 16, "greedy", 1e2),
                                                       (1000, 300, 3, 64, 16, "grasap", 1e4),
                                                       (300, 300, 2, 64, 32, "fibonacci", 1e3),
-                                                      (700, 130, 40, 32, 16, "flat", 1e4)])
+                                                      (700, 130, 40, 32, 16, "flat", 1e4),
+                                                      (1000, 300, 3, 64, 16, "greedy-ts", 1e4)])
 def test_lstsq_fp64(m, n, nrhs, nb, ib, tree, cond):
     """GPU least squares vs the oracle's.  Both are backward stable, so their solutions
     differ by at most the LS perturbation bound (Golub & Van Loan, Thm 5.3.1):
     |dx|/|x| <~ c u (kappa + kappa^2 |r| / (|A| |x|)) with |A|_2 = 1 here; c = 64."""
     A, X, B = synthetic.least_squares_problem(m, n, cond, 1e-3, nrhs, seed=m + nrhs)
     p, q = H.tile_grid(m, n, nb)
-    elims = E.elimination_list(p, q, tqr.TREES[tree], bs=2)
-    Xo = H.lstsq(A, B, nb, ib, elims)
+    base, ts = tree_and_ts(tree)
+    elims = E.elimination_list(p, q, base, bs=2)
+    Xo = H.lstsq(A, B, nb, ib, elims, ts)
     Xg = to_np(tqr.lstsq(to_dev(A), to_dev(B), nb, ib, tree, 2, "fp64"))
     r = B - A @ Xo
     bound = 64 * U64 * (cond + cond ** 2 * np.linalg.norm(r) / np.linalg.norm(Xo))
@@ -215,6 +244,28 @@ def test_wait_timeout_reports_error_and_context_survives():
     finally:
         tqr.set_wait_limit_ns(old)
     compare_factor(A, 32, 8, "greedy")
+
+
+def test_wait_timeout_tensor_core_executor():
+    """The same with the tensor-core executor (split-bf16 x3): the CTAs stop at their next
+    claim, free their tensor memory and the call returns TQR_ETIMEOUT; a following mixed
+    factorization of the same input is bitwise equal to one made before."""
+    A = synthetic.gaussian(512, 384, seed=19)
+    ws = tqr.workspace_size(512, 384, 128, 32, "bf16x3")
+    ref = to_dev(A, torch.float32)
+    tqr.factor(ref, 128, 32, "greedy", 1, "bf16x3", T=torch.zeros(ws, dtype=torch.uint8, device="cuda"))
+    old = tqr.set_wait_limit_ns(200 * 10 ** 6)
+    try:
+        tqr.debug_drop_edge(7)
+        with pytest.raises(tqr.TqrError) as ei:
+            tqr.factor(to_dev(A, torch.float32), 128, 32, "greedy", 1, "bf16x3")
+        assert ei.value.status == tqr.TQR_ETIMEOUT
+    finally:
+        tqr.set_wait_limit_ns(old)
+    again = to_dev(A, torch.float32)
+    tqr.factor(again, 128, 32, "greedy", 1, "bf16x3", T=torch.zeros(ws, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(ref, again)
 
 
 def test_serialized_equals_parallel_bitwise():

@@ -87,3 +87,25 @@ def test_consistent_square_system_stops_at_backward_error(prec, cond, max_iters)
 
     assert omega(Xg) <= max(2 * omega(Xo), 1e-14), (omega(Xg), omega(Xo))
     assert 1 <= iters <= max_iters, iters
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x3", "fp32"])
+@pytest.mark.parametrize("m,n,nrhs,noise,tree", [(1024, 384, 2, 1e-3, "greedy"), (512, 512, 2, 0.0, "greedy"),
+                                                 (1024, 384, 1, 1e-3, "plasma-ts")])
+def test_refined_solution_within_1e_12(prec, m, n, nrhs, noise, tree):
+    """The 1e-12 relative accuracy of refined least-squares solutions, asserted where kappa u
+    permits it: at kappa = 1e2 the LS perturbation bound c u (kappa + kappa^2 |r| / |x|)
+    with c = 64 is below 1e-12 (checked here, for the problem itself), so every solver that
+    is backward stable to FP64 rounding - the FP64 tiled QR and each refined mixed form -
+    must agree with the FP64 oracle's solution to 1e-12."""
+    cond = 1e2
+    A, X, B = synthetic.least_squares_problem(m, n, cond, noise, nrhs, seed=m + 3 * n + nrhs)
+    p, q = H.tile_grid(m, n, 128)
+    t = tqr.TREES[tree]
+    Xo = H.lstsq(A, B, 128, 32, E.elimination_list(p, q, t & ~tqr.TS, bs=3), bool(t & tqr.TS))
+    r = B - A @ Xo
+    bound = 64 * U64 * (cond + cond ** 2 * np.linalg.norm(r) / np.linalg.norm(Xo))
+    assert bound <= 1e-12, bound
+    Xg = tqr.lstsq(to_dev(A), to_dev(B), 128, 32, tree, 3, prec, tol=1e-14, max_iter=600).cpu().numpy()
+    err = refine.rel_error(Xg, Xo)
+    assert err <= 1e-12, (prec, err)

@@ -113,3 +113,80 @@ def test_workspace_and_flops():
     assert tqr.workspace_size(512, 128, 64, 16, "fp64") == 2 * 8 * 2 * 16 * 64 * 8
     assert tqr.workspace_size(512, 128, 64, 16, "fp32") == 2 * 8 * 2 * 16 * 64 * 4
     assert tqr.nominal_flops(32768, 4096) == pytest.approx(2 * 4096 ** 2 * (32768 - 4096 / 3))
+
+
+@pytest.mark.parametrize("m,n,nb", [(512, 128, 64), (1000, 300, 64), (300, 1000, 64), (64, 64, 64), (2048, 640, 128)])
+def test_ts_plan_counts_vs_oracle(m, n, nb):
+    """TS form of each tree (tree | TQR_TS): the library's task counts and critical path
+    equal the oracle's TS-form schedule (TSQRT weight 6, TSMQR 12)."""
+    p, q = -(-m // nb), -(-n // nb)
+    for tree in ["flat", "plasma", "binary", "fibonacci", "greedy", "grasap"]:
+        st = tqr.plan_counts(m, n, nb, tree + "-ts", 3)
+        ref = E.elimination_list(p, q, tqr.TREES[tree], bs=3)
+        counts = E.kernel_counts(p, q, ref, ts=True)
+        for k in ("GEQRT", "TTQRT", "UNMQR", "TTMQR", "TSQRT", "TSMQR"):
+            assert st[k] == counts[k], (tree, k)
+        assert st["cp"] == E.critical_path(p, q, ref, ts=True), tree
+        # the TT form through the same entry point is unchanged
+        tt = tqr.plan_counts(m, n, nb, tree, 3)
+        assert tt["TSQRT"] == 0 and tt["TSMQR"] == 0
+        assert tt["cp"] == E.critical_path(p, q, ref)
+        _, cp = tqr.elimlist(p, q, tree + "-ts", 3)
+        assert cp == st["cp"]
+
+
+def test_ts_claim_order_topological():
+    """The executor order of a TS-form graph is a topological order of the oracle's
+    TS-form program (every task after the tasks it conflicts with)."""
+    for tree in ["flat-ts", "plasma-ts", "greedy-ts"]:
+        for mode in (0, 1):
+            order = tqr.claim_order(9, 4, tree, 3, mode=mode, nproc=5)
+            names = {0: "GEQRT", 1: "TTQRT", 2: "UNMQR", 3: "TTMQR", 6: "TSQRT", 7: "TSMQR"}
+            keys = []
+            for kind, i, piv, k, j in order:
+                nm = names[int(kind)]
+                if nm == "GEQRT":
+                    keys.append((nm, i, k))
+                elif nm == "UNMQR":
+                    keys.append((nm, i, k, j))
+                elif nm in ("TTQRT", "TSQRT"):
+                    keys.append((nm, i, piv, k))
+                else:
+                    keys.append((nm, i, piv, k, j))
+            base = tqr.TREES[tree] & ~tqr.TS
+            sched = E.schedule(9, 4, E.elimination_list(9, 4, base, bs=3), ts=True)
+            assert sorted(keys) == sorted(sched.finish.keys())
+            pos = {key: r for r, key in enumerate(keys)}
+            # a task starts no earlier than its earliest-start predecessors finish: in a
+            # topological order, tasks with a finish time <= another's start come first
+            for key in keys:
+                st = sched.finish[key] - {"GEQRT": 4, "TTQRT": 2, "UNMQR": 6, "TTMQR": 6,
+                                          "TSQRT": 6, "TSMQR": 12}[key[0]]
+                for other in keys:
+                    if sched.finish[other] <= st and _conflict(key, other):
+                        assert pos[other] < pos[key], (tree, mode, key, other)
+
+
+def _regions(key):
+    nm = key[0]
+    if nm == "GEQRT":
+        _, i, k = key
+        return set(), {(i, k, "L"), (i, k, "U")}
+    if nm == "UNMQR":
+        _, i, k, j = key
+        return {(i, k, "L")}, {(i, j, "L"), (i, j, "U")}
+    if nm == "TTQRT":
+        _, i, piv, k = key
+        return set(), {(piv, k, "U"), (i, k, "U")}
+    if nm == "TSQRT":
+        _, i, piv, k = key
+        return set(), {(piv, k, "U"), (i, k, "L"), (i, k, "U")}
+    _, i, piv, k, j = key
+    rd = {(i, k, "U")} if nm == "TTMQR" else {(i, k, "L"), (i, k, "U")}
+    return rd, {(piv, j, "L"), (piv, j, "U"), (i, j, "L"), (i, j, "U")}
+
+
+def _conflict(a, b):
+    ra, wa = _regions(a)
+    rb, wb = _regions(b)
+    return bool(wa & (rb | wb)) or bool(wb & ra)
