@@ -312,6 +312,13 @@ int tqr_lstsq_workspace_size(int64_t m, int64_t n, int64_t nrhs, int nb, int ib,
  * every TFLOP/s figure of this library uses (Theorem "thm.flops"). */
 double tqr_nominal_flops(int64_t m, int64_t n);
 
+/* Measured FP64 throughput of the current device (TFLOP/s): the plain FP64 FMA pipe
+ * (DFMA: independent FMA chains on every SM) and the FP64 tensor instruction (DMMA:
+ * mma.sync m8n8k4 f64, independent accumulators on every warp).  These are the
+ * denominators of the FP64 form's fraction of peak; under 0.1 s of device time, on
+ * "stream", synchronized.  Errors: -1/-2 NULL output, TQR_ECUDA, TQR_ENOMEM. */
+int tqr_fp64_peak(double *dfma_tflops, double *dmma_tflops, void *stream);
+
 /* Maximum time one device-side dependency wait may spin before the kernel gives up
  * with TQR_ETIMEOUT (nanoseconds; default 20 s).  Returns the previous value. */
 int64_t tqr_set_wait_limit_ns(int64_t ns);

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
             "tqr_lstsq_workspace_size": (i32, [i64, i64, i64, i32, i32, i32,
                                                ctypes.POINTER(ctypes.c_size_t)]),
             "tqr_nominal_flops": (dbl, [i64, i64]),
+            "tqr_fp64_peak": (i32, [ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]),
             "tqr_set_wait_limit_ns": (i64, [i64]),
             "tqr_set_sync": (i32, [i32]),
             "tqr_sync_status": (i32, [vp]),
@@ -223,6 +224,13 @@ def workspace_size(m: int, n: int, nb: int, ib: int, prec="fp64") -> int:
 
 def nominal_flops(m: int, n: int) -> float:
     return lib().tqr_nominal_flops(m, n)
+
+
+def fp64_peak(stream=None):
+    """Measured FP64 TFLOP/s of the current GPU: {"dfma": ..., "dmma": ...}."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check("tqr_fp64_peak", lib().tqr_fp64_peak(ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return {"dfma": a.value, "dmma": b.value}
 
 
 def set_wait_limit_ns(ns: int) -> int:
