@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tiled-QR TFLOP/s, mixed vs plain FP64 at equal LS error; % of tensor peak"
-FP64_PEAK_TFLOPS = 1.25        # GB300 FP64 rate (the FP64 arm runs on the FP64 ALUs)
+FP64_NOMINAL_TFLOPS = 1.25     # GB300's nominal FP64 rate (context; the fraction uses the measured one)
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum SM clock
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BATCH_COUNT = 2048
@@ -62,8 +62,9 @@ def parse_args():
     ap.add_argument("--cond", type=float, default=1e6)
     ap.add_argument("--prec", default="bf16x6")
     ap.add_argument("--also-prec", default="bf16x3", help="second mixed precision measured for comparison ('' = none)")
-    ap.add_argument("--trees", action="store_true",
-                    help="also time the FP64 factorization under the six trees (32768x4096, nb 256, ib 32)")
+    ap.add_argument("--no-trees", action="store_true",
+                    help="skip the FP64 factorization under the six trees and their TS forms "
+                         "(32768x4096, nb 256, ib 32; about 20 s)")
     ap.add_argument("--tree", default="greedy")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,8 +75,8 @@ def parse_args():
     ap.add_argument("--batch-prec", default="fp32")
     ap.add_argument("--batch-table", default="", help="JSON tuning table (autotune output) for the batch")
     ap.add_argument("--batch-reps", type=int, default=5)
-    ap.add_argument("--c5", action="store_true",
-                    help="also measure the square 16384^2 solve (cond 1e4, 64 right-hand sides), ~1 min")
+    ap.add_argument("--no-c5", action="store_true",
+                    help="skip the square 16384^2 solve (cond 1e4, 64 right-hand sides; about 1 min)")
     ap.add_argument("--c5-precs", default="bf16x3,bf16x6")
     return ap.parse_args()
 
@@ -122,20 +123,42 @@ print(json.dumps(dict(times=times, flops=2.0 * n * n * (m - n / 3.0))))
 """
 
 
-def run_oracle(m, n, nb, ib, tree, reps, cond):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def run_oracle(m, n, nb, ib, tree, reps, cond, threads=1):
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = ORACLE_SNIPPET.format(root=ROOT, m=m, n=n, nb=nb, ib=ib, tree=tree, reps=reps, cond=cond)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def host_cpu():
+    """(logical cores, CPU model name) of this host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
 def cpu_baseline(args):
+    """The oracle timed on a bounded sample of the workload: with every host core as BLAS
+    threads (the value) and with one thread (beside it)."""
     ms, ns = min(args.sample_m, args.m), min(args.sample_n, args.n)
-    r = run_oracle(ms, ns, 256, 32, args.tree, 1, args.cond)
-    t = r["times"][0]
-    return {"value": r["flops"] / t / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.tree}) of a {ms}x{ns} "
-                      f"matrix of the same kind, one BLAS thread, {t:.1f} s; rate = nominal flops / time"}
+    cores, model = host_cpu()
+    multi = run_oracle(ms, ns, 256, 32, args.tree, 1, args.cond, threads=cores)
+    one = run_oracle(ms, ns, 256, 32, args.tree, 1, args.cond, threads=1)
+    tm, t1 = multi["times"][0], one["times"][0]
+    return {"value": multi["flops"] / tm / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "cpu_model": model,
+            "sample": f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.tree}) of a {ms}x{ns} matrix "
+                      f"of the same kind, numpy with {cores} BLAS threads (nproc), {tm:.1f} s; rate = nominal "
+                      f"flops / time",
+            "single_thread": {"value": one["flops"] / t1 / 1e12, "unit": "TFLOP/s", "cores": 1, "seconds": t1}}
 
 
 def workload_config(args):
@@ -287,7 +310,7 @@ def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
     t_bytes = int(sum(tqr.workspace_size(m, n, int(p[0]), int(p[1]), prec) for (m, n), p in zip(all_shapes, all_params)))
     a_bytes = 2 * esz * sum(m * n for m, n in all_shapes)
     byts = a_bytes + t_bytes
-    peak = FP32_ALU_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
+    peak = FP32_ALU_PEAK_TFLOPS if prec == "fp32" else FP64_NOMINAL_TFLOPS
     classes = []
     all_ms = [m for m, _ in all_shapes]
     for (lo, hi, n), idx in sorted(size_classes(all_shapes).items()):
@@ -522,12 +545,15 @@ def main_gpu(args):
         torch.cuda.empty_cache()
 
     trees = None
-    if args.trees:
+    if not args.no_trees and world == 1:
+        # the six trees of the 32768 x 4096 FP64 workload (PlasmaTree with BS = 4) on the
+        # same input, and their TS forms (TSQRT / TSMQR for the rows that never pivot)
         trees = {}
         Af = torch.empty_like(A.t()).t()
         T64 = torch.empty(tqr.workspace_size(m, n, 256, 32, "fp64"), dtype=torch.uint8, device=dev)
         tqr.set_timing(True)
-        for tr in ("flat", "plasma", "binary", "fibonacci", "greedy", "grasap"):
+        for tr in ("flat", "plasma", "binary", "fibonacci", "greedy", "grasap",
+                   "flat-ts", "plasma-ts", "greedy-ts"):
             Af.copy_(A)
             tqr.kernel_time("factor", reset=True)
             tqr.factor(Af, 256, 32, tr, 4, "fp64", T=T64)
@@ -535,11 +561,13 @@ def main_gpu(args):
             cp = tqr.elimlist(-(-m // 256), -(-n // 256), tr, 4)[1]
             trees[tr] = {"factor_ms": fms, "tflops": tqr.nominal_flops(m, n) / (fms * 1e-3) / 1e12, "cp_units": cp}
         tqr.set_timing(False)
+        del Af, T64
+        torch.cuda.empty_cache()
 
     batched = None
     if not args.no_batched:
         batched = batched_measurement(args, hbm_peak(), rank, world, dev)
-    c5 = c5_measurement(args) if (args.c5 and world == 1) else None
+    c5 = c5_measurement(args) if (not args.no_c5 and world == 1) else None
     c1 = c1_measurement() if world == 1 else None
 
     # ---- end to end: host buffers, copies inside the timed region ----
@@ -572,6 +600,8 @@ def main_gpu(args):
     fac_ms, fac_n = kt["factor"]
     fac_avg = fac_ms / max(fac_n, 1)
     bf16_burst, bf16_sust, peak_src = peaks()
+    fp64_pk = tqr.fp64_peak(stream)
+    fp64_peak = max(fp64_pk["dfma"], fp64_pk["dmma"])
     achieved = flops / (fac_avg * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -590,11 +620,21 @@ def main_gpu(args):
                                                "updates them, split operand images written once and read by "
                                                "every update (no reuse in L2 assumed); A alone is 8mn bytes",
                      "peak_source": f"{peak_src} bf16 dense sustained (MEASURED_PEAKS.json)",
-                     "flops_per_launch": flops, "avg_launch_ms": fac_avg},
+                     "flops_per_launch": flops, "avg_launch_ms": fac_avg,
+                     "minimal_bytes": minimal_bytes(args),
+                     "minimal_bytes_note": "A (FP32) read and written once plus the T factors (2 p q ib nb "
+                                           "FP32) - the least traffic any tiled QR of this shape needs",
+                     "traffic_over_minimal": flops * MIXED_TRAFFIC_PER_FLOP / minimal_bytes(args),
+                     "traffic_over_tile_task": flops * MIXED_TRAFFIC_PER_FLOP / tile_task_bytes(args)},
         "ls_optimality": {"mixed": eta_mixed, "fp64": eta64, "target": tol},
         "refinement_iterations": iters,
         "fp64": {"value": flops / (fp64_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": fp64_ms,
-                 "steps": args.fp64_steps, "frac_of_fp64_peak": flops / (fp64_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+                 "steps": args.fp64_steps,
+                 "frac_of_fp64_peak": flops / (fp64_ms * 1e-3) / 1e12 / fp64_peak,
+                 "fp64_peak": {"dfma_tflops": fp64_pk["dfma"], "dmma_tflops": fp64_pk["dmma"],
+                               "used": fp64_peak, "nominal": FP64_NOMINAL_TFLOPS,
+                               "source": "measured on this GPU by tqr_fp64_peak (DFMA chains on every "
+                                         "SM; DMMA m8n8k4 f64 accumulators on every warp)"}},
         "speedup_vs_fp64": fp64_ms / step_ms,
         "also": also,
         "fp64_trees": trees,
@@ -610,6 +650,12 @@ def main_gpu(args):
     if rank == 0:
         print(json.dumps(line))
     replicas.finalize()
+
+
+def minimal_bytes(args, nb=128, ib=32, esz=4):
+    """A read and written once plus the T factors: 2 m n esz + 2 p q ib nb esz bytes."""
+    p, q = -(-args.m // nb), -(-args.n // nb)
+    return 2 * args.m * args.n * esz + 2 * p * q * ib * nb * esz
 
 
 def tile_task_bytes(args):

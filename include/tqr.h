@@ -113,6 +113,12 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len,
 int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
                  int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
 
+/* tqr_schedule with six kernel weights (GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR), each
+ * >= 1: the TS kernels weighed on their own, e.g. by measured task durations.  weights
+ * must not be NULL (-6); other arguments and errors as tqr_schedule. */
+int tqr_schedule_ts(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
+                    int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
+
 /* Claim order of the persistent executor for the factorizations planned after this call
  * (plans are cached per order setting; results never depend on the order).
  *   mode 0: earliest start on unbounded processors with the thesis weights, ties to the
@@ -123,12 +129,16 @@ int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weigh
  *           measured task durations of the chosen precision (TS kernels: 3 x TTQRT and
  *           2 x TTMQR).
  *   mode 2 (default): mode 1 with built-in weights from task durations in
- *           microseconds measured on GB300 - the tensor-core precisions 330, 360, 20, 32
- *           (nb 128, panel weights tuned on a 32768 x 4096 factorization), TQR_FP64 5146,
- *           4249, 6394, 6369 (nb 256) - and mode 0 for TQR_FP32.  weights is ignored.
+ *           microseconds measured on GB300 - the tensor-core precisions 330, 360, 20, 32,
+ *           TSQRT 400, TSMQR 32 (nb 128, panel weights tuned on a 32768 x 4096
+ *           factorization), TQR_FP64 5146, 4249, 6394, 6369, TSQRT 6767, TSMQR 9457
+ *           (nb 256) - and mode 0 for TQR_FP32.  weights is ignored.
  * Every order is topological, so the executor's dependency waits always end.
  * Host only.  Errors: -1 unknown mode, -2 a weight < 1. */
 int tqr_set_claim_order(int mode, const int64_t *weights);
+/* tqr_set_claim_order with six weights (GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR) for
+ * mode 1 (NULL = 4, 2, 6, 6, 6, 12).  Errors as tqr_set_claim_order. */
+int tqr_set_claim_order_ts(int mode, const int64_t *weights);
 
 /* Bytes of the caller-owned T workspace of tqr_factor: two ib x nb compact-WY T
  * factors (GEQRT's and TTQRT's, Schreiber-Van Loan form, LAPACK GEQRT layout: block b
@@ -346,7 +356,8 @@ int64_t tqr_launch_count(int reset);
  * trailing update, operand images; tensor-core updates: operand conversion, first
  * product, W conversion, second product and epilogue).
  * tqr_trace_fetch copies the last traced launch: 12 int64 per task in executor order =
- * {kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR, 4/5 apply-Q), i, piv, k | j << 16, claim,
+ * {kind (0 GEQRT, 1 TTQRT, 2 UNMQR, 3 TTMQR, 4/5/8 apply-Q, 6 TSQRT, 7 TSMQR, 9/10 operand
+ * images of a GEQRT / of a TTQRT or TSQRT (tensor-core precisions)), i, piv, k | j << 16, claim,
  * start, end, sm, phase0, phase1, phase2, phase3}.  With out == NULL it returns the task count; otherwise the count
  * copied, -1 if cap is too small or nothing was traced, -2 on a CUDA error. */
 int tqr_set_trace(int on);

@@ -53,6 +53,8 @@ def lib() -> ctypes.CDLL:
             "tqr_elimlist": (i32, [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32), c_i64p, c_i64p]),
             "tqr_schedule": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
             "tqr_set_claim_order": (i32, [i32, c_i64p]),
+            "tqr_set_claim_order_ts": (i32, [i32, c_i64p]),
+            "tqr_schedule_ts": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
             "tqr_debug_claim_order": (i32, [i32, i32, i32, i32, i32, i32, c_i64p, ctypes.POINTER(ctypes.c_int32),
                                              c_i64p]),
             "tqr_workspace_size": (i32, [i64, i64, i32, i32, i32, ctypes.POINTER(ctypes.c_size_t)]),
@@ -164,26 +166,34 @@ def elimlist(p: int, q: int, tree="greedy", bs: int = 1):
 def _weights4(weights):
     if weights is None:
         return None
-    w = (ctypes.c_int64 * 4)(*[int(x) for x in weights])
+    w = (ctypes.c_int64 * len(weights))(*[int(x) for x in weights])
     return ctypes.cast(w, ctypes.POINTER(ctypes.c_int64))
 
 
 def schedule(p: int, q: int, tree="greedy", bs: int = 1, nproc: int = 1, weights=None):
     """Bounded-processor schedule of the factorization task graph on nproc processors:
-    (CP-method makespan, ALAP Derived bound, lost area); weights are the four kernel
-    weights (GEQRT, TTQRT, UNMQR, TTMQR), None = 4, 2, 6, 6."""
+    (CP-method makespan, ALAP Derived bound, lost area); weights are four kernel weights
+    (GEQRT, TTQRT, UNMQR, TTMQR; None = 4, 2, 6, 6; TS kernels 3 x TTQRT, 2 x TTMQR) or six
+    (..., TSQRT, TSMQR)."""
     ms, bound, la = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
-    _check("tqr_schedule", lib().tqr_schedule(p, q, _tree(tree), bs, nproc, _weights4(weights),
-                                              ctypes.byref(ms), ctypes.byref(bound), ctypes.byref(la)))
+    if weights is not None and len(weights) == 6:
+        fn, name = lib().tqr_schedule_ts, "tqr_schedule_ts"
+    else:
+        fn, name = lib().tqr_schedule, "tqr_schedule"
+    _check(name, fn(p, q, _tree(tree), bs, nproc, _weights4(weights), ctypes.byref(ms), ctypes.byref(bound),
+                    ctypes.byref(la)))
     return ms.value, bound.value, la.value
 
 
 def set_claim_order(mode: int, weights=None) -> None:
     """Executor claim order of later factorization plans: 0 = earliest start on unbounded
     processors, 1 = start order of the bounded-processor CP-method schedule with the given
-    kernel weights (GEQRT, TTQRT, UNMQR, TTMQR), 2 = the default (1 with built-in GB300
-    weights for the tensor-core precisions and fp64, 0 for fp32)."""
-    _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))
+    kernel weights (GEQRT, TTQRT, UNMQR, TTMQR[, TSQRT, TSMQR]), 2 = the default (1 with
+    built-in GB300 weights for the tensor-core precisions and fp64, 0 for fp32)."""
+    if weights is not None and len(weights) == 6:
+        _check("tqr_set_claim_order_ts", lib().tqr_set_claim_order_ts(mode, _weights4(weights)))
+    else:
+        _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))
 
 
 def claim_order(p: int, q: int, tree="greedy", bs: int = 1, mode: int = 0, nproc: int = 1, weights=None):

@@ -33,11 +33,15 @@ int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
 //   factorization takes 1488 ms instead of 1635 ms with the unbounded order (its ALAP
 //   Derived bound is 1468 ms), Greedy's 1448 ms against 1443 ms (bound 1424 ms).
 int g_order_mode = 2;
-int64_t g_order_w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr};
+int64_t g_order_w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr, 1, 1};
 int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
-// per TaskKind: GEQRT, TTQRT, UNMQR, TTMQR, (apply-Q kinds, unused), TSQRT, TSMQR
-constexpr int64_t kTensorOrderWeights[kNumKinds] = {330, 360, 20, 32, 20, 32, 400, 32, 32};
-constexpr int64_t kFp64OrderWeights[kNumKinds] = {5146, 4249, 6394, 6369, 6394, 6369, 7700, 12800, 12800};
+// per TaskKind: GEQRT, TTQRT, UNMQR, TTMQR, (apply-Q kinds, unused), TSQRT, TSMQR.  The
+// TS kernels' weights are measured task means on GB300 as well: tensor cores 340-375 /
+// 29-30 us (TSQRT taken like the tuned panel weights, a little above its mean), FP64
+// 6767 / 9457 us (TSMQR 1.37 times faster per flop than UNMQR + TTMQR, as the thesis
+// found the TS kernels faster on its CPUs).
+constexpr int64_t kTensorOrderWeights[kNumKinds] = {265, 285, 20, 32, 20, 32, 320, 32, 32, 66, 66};
+constexpr int64_t kFp64OrderWeights[kNumKinds] = {5146, 4249, 6394, 6369, 6394, 6369, 6767, 9457, 9457, 1, 1};
 
 // Per-kind weights from the four TT-kernel weights of the ABI (GEQRT, TTQRT, UNMQR,
 // TTMQR): the TS kernels take the thesis's ratios to their TT counterparts, TSQRT = 3
@@ -49,6 +53,7 @@ void expand_weights(const int64_t w4[4], int64_t out[kNumKinds]) {
   out[kTtmqr] = out[kTtmqrB] = w4[3];
   out[kTsqrt] = 3 * w4[1];
   out[kTsmqr] = out[kTsmqrB] = 2 * w4[3];
+  out[kPrepG] = out[kPrepT] = 1;  // operand images (tensor-core precisions): short
 }
 
 bool valid_tree(int tree) {
@@ -168,7 +173,9 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 // Returns the cached plan for (kind, P, Q, tree, bs) on the current device.
 // order: the claim order of a factorization plan (kind 0), with spec.nproc the
 // executor's resident CTAs; ignored for the apply-Q plans.
-int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSpec *order = nullptr) {
+// prep: the tensor-core form of a factorization graph (operand-preparation tasks).
+int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSpec *order = nullptr,
+             bool prep = false) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -181,7 +188,7 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   // the order's identity (spec.id: user weights carry the setting's generation, each
   // built-in weight set a negative key of its own) is part of the key; a plan built with
   // the test hook is never reused: it gets a key of its own
-  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : kind, P, Q, tree,
+  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : (kind == 0 && prep ? 3 : kind), P, Q, tree,
                     tree_base(tree) == TQR_PLASMA ? bs : 0, bounded ? spec.id : 0, bounded ? spec.nproc : 0};
   auto it = g_plans.find(key);
   if (it != g_plans.end()) {
@@ -193,7 +200,7 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   auto plan = std::make_unique<Plan>();
   plan->device = dev;
   if (kind == 0)
-    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree));
+    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree), prep);
   else
     build_applyq_graph(P, Q, elims, kind == 2, plan->g, tree_ts(tree));
   if (drop >= 0) g_drop_edge = -1;  // the test hook applies to one plan only
@@ -367,24 +374,23 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len, in
   return TQR_OK;
 }
 
-int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights, int64_t *makespan,
-                 int64_t *alap_bound, int64_t *lost_area) {
-  if (p < 1) return -1;
-  if (q < 1) return -2;
-  if (!valid_tree(tree)) return -3;
-  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -4;
-  if (nproc < 1) return -5;
-  int64_t w4[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr}, w[kNumKinds];
-  if (weights)
-    for (int c = 0; c < 4; ++c) {
-      if (weights[c] < 1) return -6;
-      w4[c] = weights[c];
-    }
-  expand_weights(w4, w);
+}  // extern "C"
+
+namespace tqr {
+namespace {
+// Per-kind weights from 6 weights of the ABI (GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR).
+void weights6(const int64_t w6[6], int64_t out[kNumKinds]) {
+  expand_weights(w6, out);
+  out[kTsqrt] = w6[4];
+  out[kTsmqr] = out[kTsmqrB] = w6[5];
+}
+
+int schedule_impl(int p, int q, int tree, int bs, int nproc, const int64_t w[kNumKinds], int64_t *makespan,
+                  int64_t *alap_bound, int64_t *lost_area) {
   try {
     std::vector<Elim> elims;
     elimination_list(p, q, tree_base(tree), bs, elims);
-    GraphBuilder b(p * q * 2);
+    GraphBuilder b(p * q * kRegionsPerTile);
     add_factor_program(b, p, q, elims, tree_ts(tree));
     const int n = static_cast<int>(b.tasks.size());
     std::vector<std::vector<int32_t>> succ(n);
@@ -410,6 +416,50 @@ int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weigh
   return TQR_OK;
 }
 
+int set_claim_order_impl(int mode, const int64_t w[kNumKinds]) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_order_mode = mode;
+  for (int c = 0; c < kNumKinds; ++c) g_order_w[c] = w[c];
+  ++g_order_gen;
+  return TQR_OK;
+}
+}  // namespace
+}  // namespace tqr
+
+extern "C" {
+
+int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights, int64_t *makespan,
+                 int64_t *alap_bound, int64_t *lost_area) {
+  if (p < 1) return -1;
+  if (q < 1) return -2;
+  if (!valid_tree(tree)) return -3;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -4;
+  if (nproc < 1) return -5;
+  int64_t w4[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr}, w[kNumKinds];
+  if (weights)
+    for (int c = 0; c < 4; ++c) {
+      if (weights[c] < 1) return -6;
+      w4[c] = weights[c];
+    }
+  expand_weights(w4, w);
+  return schedule_impl(p, q, tree, bs, nproc, w, makespan, alap_bound, lost_area);
+}
+
+int tqr_schedule_ts(int p, int q, int tree, int bs, int nproc, const int64_t *weights, int64_t *makespan,
+                    int64_t *alap_bound, int64_t *lost_area) {
+  if (p < 1) return -1;
+  if (q < 1) return -2;
+  if (!valid_tree(tree)) return -3;
+  if (tree_base(tree) == TQR_PLASMA && bs < 1) return -4;
+  if (nproc < 1) return -5;
+  if (!weights) return -6;
+  for (int c = 0; c < 6; ++c)
+    if (weights[c] < 1) return -6;
+  int64_t w[kNumKinds];
+  weights6(weights, w);
+  return schedule_impl(p, q, tree, bs, nproc, w, makespan, alap_bound, lost_area);
+}
+
 int tqr_set_claim_order(int mode, const int64_t *weights) {
   if (mode < 0 || mode > 2) return -1;
   int64_t w4[4] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr}, w[kNumKinds];
@@ -419,11 +469,19 @@ int tqr_set_claim_order(int mode, const int64_t *weights) {
       w4[c] = weights[c];
     }
   expand_weights(w4, w);
-  std::lock_guard<std::mutex> lock(g_mu);
-  g_order_mode = mode;
-  for (int c = 0; c < kNumKinds; ++c) g_order_w[c] = w[c];
-  ++g_order_gen;
-  return TQR_OK;
+  return set_claim_order_impl(mode, w);
+}
+
+int tqr_set_claim_order_ts(int mode, const int64_t *weights) {
+  if (mode < 0 || mode > 2) return -1;
+  int64_t w6[6] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr}, w[kNumKinds];
+  if (weights && mode == 1)
+    for (int c = 0; c < 6; ++c) {
+      if (weights[c] < 1) return -2;
+      w6[c] = weights[c];
+    }
+  weights6(w6, w);
+  return set_claim_order_impl(mode, w);
 }
 
 int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T_bytes) {
@@ -455,7 +513,7 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
       order = effective_order(prec);
     }
     if (order.mode == 1) order.nproc = executor_slots(dbl, is_tensor_prec(prec), nb, ib);
-    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order)) != 0) return rc;
+    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order, is_tensor_prec(prec))) != 0) return rc;
     ExecParams prm{};
     prm.A = A;
     prm.lda = lda;

@@ -125,7 +125,7 @@ struct Merged {
   double flops = 0.0;
 };
 
-int merge_batch(int nbatch, const int64_t *m, const int64_t *n, const int *prm, int slots, Merged &out) {
+int merge_batch(int nbatch, const int64_t *m, const int64_t *n, const int *prm, int slots, int prec, Merged &out) {
   if (slots < 1) slots = 1;
   out.flops = 0.0;
   // one graph per distinct (P, Q, tree, bs)
@@ -142,7 +142,7 @@ int merge_batch(int nbatch, const int64_t *m, const int64_t *n, const int *prm, 
       std::vector<Elim> elims;
       if (!elimination_list(P, Q, tree_base(o[2]), o[3], elims)) return fail(-5, "elimination list");
       auto g = std::make_unique<Graph>();
-      build_factor_graph(P, Q, elims, *g, -1, nullptr, tree_ts(o[2]));
+      build_factor_graph(P, Q, elims, *g, -1, nullptr, tree_ts(o[2]), is_tensor_prec(prec));
       it = graphs.emplace(key, std::move(g)).first;
     }
     gof[b] = it->second.get();
@@ -312,7 +312,7 @@ int tqr_batch_plan_create(int nbatch, const int64_t *m, const int64_t *n, void *
     if (pl->slots < 1) pl->slots = 1;
 
     Merged mg;
-    const int rc = merge_batch(nbatch, m, n, prm.data(), pl->slots, mg);
+    const int rc = merge_batch(nbatch, m, n, prm.data(), pl->slots, prec, mg);
     if (rc) return rc;
     pl->flops = mg.flops;
     const int64_t N = static_cast<int64_t>(mg.tasks.size());
@@ -368,7 +368,7 @@ int tqr_batch_order(int nbatch, const int64_t *m, const int64_t *n, int prec, co
       if (rc) return fail(rc, "matrix " + std::to_string(b) + ": invalid size or tuning");
     }
     Merged mg;
-    const int rc = merge_batch(nbatch, m, n, prm.data(), slots, mg);
+    const int rc = merge_batch(nbatch, m, n, prm.data(), slots, prec, mg);
     if (rc) return rc;
     const int64_t N = static_cast<int64_t>(mg.tasks.size());
     if (mat_of && local) {

@@ -146,7 +146,7 @@ void grasap(int p, int q, int n_asap, std::vector<Elim> &out) {
   if (n_asap >= q) first_asap = 0;
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : gl) by_col[e.k].push_back(e);
-  GraphBuilder b(p * q * 2);
+  GraphBuilder b(p * q * kRegionsPerTile);
   for (int k = 0; k < kmax; ++k) {
     std::vector<int> gid = add_panel_tasks(b, p, q, k);
     std::vector<Elim> col;

@@ -1152,30 +1152,20 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     switch (task.kind) {
       case kGeqrt:
         task_geqrt<Real, S>(q, s, task.i, task.k);
-        if (kMixed) {
-          __syncthreads();
-          phase_mark(s.ph, 2);
-          prep_geqrt_ops(q, smem_raw, task.i, task.k);
-          phase_mark(s.ph, 3);
-        }
         break;
       case kTtqrt:
         task_ttqrt<Real, S, false>(q, s, task.i, task.piv, task.k);
-        if (kMixed) {
-          __syncthreads();
-          phase_mark(s.ph, 2);
-          prep_ttqrt_ops(q, smem_raw, task.i, task.k, false);
-          phase_mark(s.ph, 3);
-        }
         break;
       case kTsqrt:
         task_ttqrt<Real, S, true>(q, s, task.i, task.piv, task.k);
-        if (kMixed) {
-          __syncthreads();
-          phase_mark(s.ph, 2);
-          prep_ttqrt_ops(q, smem_raw, task.i, task.k, true);
-          phase_mark(s.ph, 3);
-        }
+        break;
+      case kPrepG:  // tensor-core graphs only: the operand images of GEQRT(i,k)
+        if (kMixed) prep_geqrt_ops(q, smem_raw, task.i, task.k);
+        phase_mark(s.ph, 3);
+        break;
+      case kPrepT:  // ... of the TTQRT (piv >= 0 and tile upper part) or TSQRT that zeroed (i,k)
+        if (kMixed) prep_ttqrt_ops(q, smem_raw, task.i, task.k, task.j != 0);
+        phase_mark(s.ph, 3);
         break;
       case kUnmqr: {
         if (kMixed) {

@@ -49,7 +49,7 @@ int GraphBuilder::add(const Task &t, int w, const int *reads, int nr, const int 
   return id;
 }
 
-std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square) {
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square, bool prep) {
   std::vector<int> geqrt_ids;
   for (int i = k; i < p; ++i) {
     if (square && square[i]) {
@@ -58,36 +58,43 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const cha
     }
     const int rw[2] = {region_L(q, i, k), region_U(q, i, k)};
     geqrt_ids.push_back(b.add(Task{kGeqrt, i, -1, (int16_t)k, -1}, kWGeqrt, nullptr, 0, rw, 2));
-    for (int j = k + 1; j < q; ++j) {
+    if (prep) {
       const int rd[1] = {region_L(q, i, k)};
+      const int wr[1] = {region_ops(q, i, k, 0)};
+      b.add(Task{kPrepG, i, -1, (int16_t)k, -1}, 0, rd, 1, wr, 1);
+    }
+    for (int j = k + 1; j < q; ++j) {
+      const int rd[2] = {region_L(q, i, k), region_ops(q, i, k, 0)};
       const int wr[2] = {region_L(q, i, j), region_U(q, i, j)};
-      b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)j}, kWUnmqr, rd, 1, wr, 2);
+      b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)j}, kWUnmqr, rd, prep ? 2 : 1, wr, 2);
     }
   }
   return geqrt_ids;
 }
 
-void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square) {
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square, bool prep) {
   for (const Elim &e : col) {
-    if (square && square[e.i]) {
+    const bool ts = square && square[e.i];
+    if (ts) {
       // TSQRT overwrites the whole square tile (i,k) with its reflectors; TSMQR reads it
       const int wr3[3] = {region_U(q, e.piv, k), region_L(q, e.i, k), region_U(q, e.i, k)};
       b.add(Task{kTsqrt, e.i, e.piv, (int16_t)k, -1}, kWTsqrt, nullptr, 0, wr3, 3);
-      for (int j = k + 1; j < q; ++j) {
-        const int rd[2] = {region_L(q, e.i, k), region_U(q, e.i, k)};
-        const int w4[4] = {region_L(q, e.piv, j), region_U(q, e.piv, j), region_L(q, e.i, j),
-                           region_U(q, e.i, j)};
-        b.add(Task{kTsmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, kWTsmqr, rd, 2, w4, 4);
-      }
-      continue;
+    } else {
+      const int wr[2] = {region_U(q, e.piv, k), region_U(q, e.i, k)};
+      b.add(Task{kTtqrt, e.i, e.piv, (int16_t)k, -1}, kWTtqrt, nullptr, 0, wr, 2);
     }
-    const int wr[2] = {region_U(q, e.piv, k), region_U(q, e.i, k)};
-    b.add(Task{kTtqrt, e.i, e.piv, (int16_t)k, -1}, kWTtqrt, nullptr, 0, wr, 2);
+    if (prep) {
+      const int rd[2] = {region_U(q, e.i, k), region_L(q, e.i, k)};
+      const int wr[1] = {region_ops(q, e.i, k, 1)};
+      // j carries the kernel: 1 = TSQRT (dense reflector tile), 0 = TTQRT
+      b.add(Task{kPrepT, e.i, e.piv, (int16_t)k, (int16_t)(ts ? 1 : 0)}, 0, rd, ts ? 2 : 1, wr, 1);
+    }
     for (int j = k + 1; j < q; ++j) {
-      const int rd[1] = {region_U(q, e.i, k)};
+      const int rd[3] = {region_U(q, e.i, k), region_ops(q, e.i, k, 1), region_L(q, e.i, k)};
       const int w4[4] = {region_L(q, e.piv, j), region_U(q, e.piv, j), region_L(q, e.i, j),
                          region_U(q, e.i, j)};
-      b.add(Task{kTtmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, kWTtmqr, rd, 1, w4, 4);
+      b.add(Task{ts ? kTsmqr : kTtmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, ts ? kWTsmqr : kWTtmqr, rd,
+            (prep ? 2 : 1) + (ts ? 1 : 0), w4, 4);
     }
   }
 }
@@ -261,7 +268,7 @@ std::vector<std::vector<char>> ts_square_rows(int p, int q, const std::vector<El
   return square;
 }
 
-void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts) {
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts, bool prep) {
   const int kmax = std::min(p, q);
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : elims) by_col[e.k].push_back(e);
@@ -269,15 +276,15 @@ void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &
   if (ts) square = ts_square_rows(p, q, elims);
   for (int k = 0; k < kmax; ++k) {
     const char *sq = ts ? square[k].data() : nullptr;
-    add_panel_tasks(b, p, q, k, sq);
-    add_elim_tasks(b, q, k, by_col[k], sq);
+    add_panel_tasks(b, p, q, k, sq, prep);
+    add_elim_tasks(b, q, k, by_col[k], sq, prep);
   }
 }
 
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge,
-                        const OrderSpec *order, bool ts) {
-  GraphBuilder b(p * q * 2);
-  add_factor_program(b, p, q, elims, ts);
+                        const OrderSpec *order, bool ts, bool prep) {
+  GraphBuilder b(p * q * kRegionsPerTile);
+  add_factor_program(b, p, q, elims, ts, prep);
   finalize_graph(b, g, drop_edge, order);
 }
 

@@ -42,8 +42,13 @@ enum TaskKind : int32_t {
   kTsqrt = 6,   // TSQRT(i,piv,k): zeroes the square tile (i,k) under R(piv,k)
   kTsmqr = 7,   // TSMQR(i,piv,k,j)
   kTsmqrB = 8,  // TSMQR(i,piv,k) applied to tile rows (piv, i) of a right-hand-side block
+  // tensor-core precisions: the operand images of a factored tile, written by a task of
+  // its own so that the next panel task of a chain does not wait for them
+  kPrepG = 9,   // images of GEQRT(i,k)'s reflectors (read by UNMQR(i,k,j))
+  kPrepT = 10,  // images of the TTQRT / TSQRT that zeroed tile (i,k) (read by TTMQR / TSMQR);
+                // its j is 1 after a TSQRT, 0 after a TTQRT
 };
-constexpr int kNumKinds = 9;
+constexpr int kNumKinds = 11;
 
 // A task as the device executor reads it (16 bytes).
 struct Task {
@@ -94,16 +99,22 @@ struct GraphBuilder {
 };
 
 // Tile regions of the factorization graph: each tile (i,j) has a strictly-lower part
-// (GEQRT reflectors) and an upper part (R, then TTQRT reflectors).
-inline int region_L(int q, int i, int j) { return (i * q + j) * 2; }
-inline int region_U(int q, int i, int j) { return (i * q + j) * 2 + 1; }
+// (GEQRT reflectors) and an upper part (R, then TTQRT reflectors), and two operand-image
+// slots (tensor-core precisions: GEQRT's and the TT/TS elimination's images).
+constexpr int kRegionsPerTile = 4;
+inline int region_L(int q, int i, int j) { return (i * q + j) * kRegionsPerTile; }
+inline int region_U(int q, int i, int j) { return (i * q + j) * kRegionsPerTile + 1; }
+inline int region_ops(int q, int i, int j, int which) { return (i * q + j) * kRegionsPerTile + 2 + which; }
 // Adds GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k of panel k except the rows with
 // square[i] != 0 (zeroed by TS kernels); returns the task ids of the GEQRTs (index i - k,
-// -1 for a skipped row).
-std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square = nullptr);
+// -1 for a skipped row).  prep: a PREP_G(i,k) task after each GEQRT writes its operand
+// images, which the UNMQRs read.
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square = nullptr,
+                                 bool prep = false);
 // Adds the eliminations of panel k in order: TSQRT / TSMQR(i,piv,k,j) when square[i] != 0,
-// TTQRT / TTMQR(i,piv,k,j) otherwise.
-void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square = nullptr);
+// TTQRT / TTMQR(i,piv,k,j) otherwise; prep: a PREP_T(i,k) task after each TTQRT / TSQRT.
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square = nullptr,
+                    bool prep = false);
 // Orders a built graph for the executor (earliest start, then longest remaining path)
 // and fills the successor CSR.
 // Executor (claim) order of a factorization graph.  mode 0: earliest start with
@@ -115,13 +126,14 @@ struct OrderSpec {
   int mode = 0;
   int nproc = 1;
   // per task kind (TaskKind index; the apply-Q kinds are unused)
-  int64_t w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr};
+  int64_t w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr, 1, 1};
   int id = 0;  // identity of the weight set in the plan cache (built-in sets < 0)
 };
 void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1, const OrderSpec *order = nullptr);
 // Tasks of the sequential program (all panels, in column order) added to b; ts: the TS
 // form of the list.
-void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts = false);
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts = false,
+                        bool prep = false);
 // Backflow priorities (a task's weight plus the largest priority of its successors) of
 // a graph in program order with successor lists succ and weights w.
 std::vector<int64_t> backflow_priorities(const std::vector<std::vector<int32_t>> &succ,
@@ -140,8 +152,10 @@ int64_t alap_derived_bound(const std::vector<int64_t> &w, const std::vector<int6
 // Builds the factorization task graph of a p x q tile matrix with the given list
 // (column-by-column program of Algorithm "elimTR"; dependencies from the tile regions
 // each kernel reads and writes, Eq. ttdeps / ttdeps2).
+// prep: the tensor-core form, with operand-image preparation tasks (PREP_G / PREP_T).
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
-                        int64_t drop_edge = -1, const OrderSpec *order = nullptr, bool ts = false);
+                        int64_t drop_edge = -1, const OrderSpec *order = nullptr, bool ts = false,
+                        bool prep = false);
 // Builds the graph that applies Q^T (or Q when reverse) to a right-hand-side block.
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g, bool ts = false);
 
