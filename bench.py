@@ -47,8 +47,9 @@ BF16_FALLBACK = (1900.0, 1700.0)
 # (tqr_set_claim_order mode 2: GEQRT, TTQRT, UNMQR, TTMQR at nb 128, bf16x6; measured task
 # durations with tuned panel weights), and the mean task durations (us) of the same
 # executor from a per-task trace on GB300 (32768 x 4096), the weights of the schedule bound.
-TENSOR_CLAIM_WEIGHTS = (330, 360, 20, 32)
-TENSOR_TASK_MEAN_US = (293, 304, 19, 31)
+TENSOR_CLAIM_WEIGHTS = (265, 285, 20, 32, 320, 32, 66)
+# GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR, operand-image preparation (PlasmaTree-TS(32) trace)
+TENSOR_TASK_MEAN_US = (253, 286, 25, 29, 270, 29, 72)
 
 
 def parse_args():
@@ -65,7 +66,10 @@ def parse_args():
     ap.add_argument("--no-trees", action="store_true",
                     help="skip the FP64 factorization under the six trees and their TS forms "
                          "(32768x4096, nb 256, ib 32; about 20 s)")
-    ap.add_argument("--tree", default="greedy")
+    ap.add_argument("--tree", default="plasma-ts", help="tree of the mixed arm (a '-ts' suffix: its TS form)")
+    ap.add_argument("--bs", type=int, default=32, help="PlasmaTree domain size of the mixed arm")
+    ap.add_argument("--fp64-tree", default="plasma-ts")
+    ap.add_argument("--fp64-bs", type=int, default=16)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-m", type=int, default=8192)
@@ -108,25 +112,27 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import synthetic
 from oracle import elimlists as E, householder as H
-m, n, nb, ib, tree, reps = {m}, {n}, {nb}, {ib}, {tree!r}, {reps}
+m, n, nb, ib, tree, bs, reps = {m}, {n}, {nb}, {ib}, {tree!r}, {bs}, {reps}
 A, X, B = synthetic.least_squares_problem(m, n, {cond}, 1e-3, 1, synthetic.SEED_BASE + 3)
 p, q = H.tile_grid(m, n, nb)
 TREES = dict(flat=E.FLAT, plasma=E.PLASMA, binary=E.BINARY, fibonacci=E.FIBONACCI, greedy=E.GREEDY,
              grasap=E.GRASAP, asap=E.ASAP)
+ts = tree.endswith("-ts")
+base = tree[:-3] if ts else tree
 times = []
 for r in range(reps):
     t0 = time.perf_counter()
-    elims = E.elimination_list(p, q, TREES[tree], bs=4)
-    H.lstsq(A, B, nb, ib, elims)
+    elims = E.elimination_list(p, q, TREES[base], bs=bs)
+    H.lstsq(A, B, nb, ib, elims, ts)
     times.append(time.perf_counter() - t0)
 print(json.dumps(dict(times=times, flops=2.0 * n * n * (m - n / 3.0))))
 """
 
 
-def run_oracle(m, n, nb, ib, tree, reps, cond, threads=1):
+def run_oracle(m, n, nb, ib, tree, bs, reps, cond, threads=1):
     t = str(threads)
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
-    code = ORACLE_SNIPPET.format(root=ROOT, m=m, n=n, nb=nb, ib=ib, tree=tree, reps=reps, cond=cond)
+    code = ORACLE_SNIPPET.format(root=ROOT, m=m, n=n, nb=nb, ib=ib, tree=tree, bs=bs, reps=reps, cond=cond)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
@@ -150,12 +156,13 @@ def cpu_baseline(args):
     threads (the value) and with one thread (beside it)."""
     ms, ns = min(args.sample_m, args.m), min(args.sample_n, args.n)
     cores, model = host_cpu()
-    multi = run_oracle(ms, ns, 256, 32, args.tree, 1, args.cond, threads=cores)
-    one = run_oracle(ms, ns, 256, 32, args.tree, 1, args.cond, threads=1)
+    multi = run_oracle(ms, ns, 256, 32, args.fp64_tree, args.fp64_bs, 1, args.cond, threads=cores)
+    one = run_oracle(ms, ns, 256, 32, args.fp64_tree, args.fp64_bs, 1, args.cond, threads=1)
     tm, t1 = multi["times"][0], one["times"][0]
     return {"value": multi["flops"] / tm / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
             "cpu_model": model,
-            "sample": f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.tree}) of a {ms}x{ns} matrix "
+            "sample": f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.fp64_tree} bs {args.fp64_bs}) "
+                      f"of a {ms}x{ns} matrix "
                       f"of the same kind, numpy with {cores} BLAS threads (nproc), {tm:.1f} s; rate = nominal "
                       f"flops / time",
             "single_thread": {"value": one["flops"] / t1 / 1e12, "unit": "TFLOP/s", "cores": 1, "seconds": t1}}
@@ -163,9 +170,10 @@ def cpu_baseline(args):
 
 def workload_config(args):
     return {"workload": f"least squares {args.m}x{args.n}, cond {args.cond:g}, 1 rhs; mixed tiled QR "
-                        f"({args.prec}, nb 128, ib 32, {args.tree}) + FP64 refinement vs FP64 tiled QR "
-                        f"(nb 256, ib 32)",
+                        f"({args.prec}, nb 128, ib 32, {args.tree} bs {args.bs}) + FP64 refinement vs FP64 "
+                        f"tiled QR (nb 256, ib 32, {args.fp64_tree} bs {args.fp64_bs})",
             "m": args.m, "n": args.n, "cond": args.cond, "nrhs": 1, "prec": args.prec, "tree": args.tree,
+            "bs": args.bs, "fp64_tree": args.fp64_tree, "fp64_bs": args.fp64_bs,
             "nb_mixed": 128, "nb_fp64": 256, "ib": 32,
             "l2": "inputs larger than L2 (A is %.2f GB FP64)" % (args.m * args.n * 8 / 1e9),
             "parallelism": "independent replicas" if args.gpus > 1 else "single GPU"}
@@ -175,11 +183,12 @@ def reference_arm(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     ms, ns = min(2048, args.m), min(512, args.n)
-    r = run_oracle(ms, ns, 256, 32, args.tree, args.warmup + args.steps, args.cond)
+    r = run_oracle(ms, ns, 256, 32, args.fp64_tree, args.fp64_bs, args.warmup + args.steps, args.cond)
     times = r["times"][args.warmup:]
     tot = sum(times)
     value = r["flops"] * len(times) / tot / 1e12
-    sample = (f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.tree}) of a {ms}x{ns} matrix of "
+    sample = (f"oracle FP64 tiled-QR least squares (nb 256, ib 32, {args.fp64_tree} bs {args.fp64_bs}) of a "
+              f"{ms}x{ns} matrix of "
               f"the workload's kind per step, one BLAS thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
@@ -478,12 +487,12 @@ def main_gpu(args):
 
     # ---- plain FP64 arm (the same entry point, FP64 tiled QR) ----
     ws64 = torch.empty(tqr.lstsq_workspace_size(m, n, 1, 256, 32, "fp64"), dtype=torch.uint8, device=dev)
-    tqr.lstsq(A, b, 256, 32, args.tree, 4, "fp64", X=X, workspace=ws64, stream=stream)
+    tqr.lstsq(A, b, 256, 32, args.fp64_tree, args.fp64_bs, "fp64", X=X, workspace=ws64, stream=stream)
     torch.cuda.synchronize()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
     for _ in range(args.fp64_steps):
-        tqr.lstsq(A, b, 256, 32, args.tree, 4, "fp64", X=X, workspace=ws64, stream=stream)
+        tqr.lstsq(A, b, 256, 32, args.fp64_tree, args.fp64_bs, "fp64", X=X, workspace=ws64, stream=stream)
     g1.record(stream)
     torch.cuda.synchronize()
     fp64_ms = g0.elapsed_time(g1) / args.fp64_steps
@@ -496,7 +505,7 @@ def main_gpu(args):
     ws = torch.empty(tqr.lstsq_workspace_size(m, n, 1, 128, 32, args.prec), dtype=torch.uint8, device=dev)
 
     def step():
-        return tqr.lstsq(A, b, 128, 32, args.tree, 4, args.prec, tol=tol, max_iter=1000, X=X, workspace=ws,
+        return tqr.lstsq(A, b, 128, 32, args.tree, args.bs, args.prec, tol=tol, max_iter=1000, X=X, workspace=ws,
                          stream=stream, return_iters=True)[1]
 
     tqr.set_timing(True)
@@ -528,13 +537,13 @@ def main_gpu(args):
     if args.also_prec and args.also_prec != args.prec:
         ws2 = torch.empty(tqr.lstsq_workspace_size(m, n, 1, 128, 32, args.also_prec), dtype=torch.uint8,
                           device=dev)
-        it2 = tqr.lstsq(A, b, 128, 32, args.tree, 4, args.also_prec, tol=tol, max_iter=1000, X=X, workspace=ws2,
+        it2 = tqr.lstsq(A, b, 128, 32, args.tree, args.bs, args.also_prec, tol=tol, max_iter=1000, X=X, workspace=ws2,
                         stream=stream, return_iters=True)[1]
         torch.cuda.synchronize()
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(stream)
         for _ in range(2):
-            it2 = tqr.lstsq(A, b, 128, 32, args.tree, 4, args.also_prec, tol=tol, max_iter=1000, X=X,
+            it2 = tqr.lstsq(A, b, 128, 32, args.tree, args.bs, args.also_prec, tol=tol, max_iter=1000, X=X,
                             workspace=ws2, stream=stream, return_iters=True)[1]
         h1.record(stream)
         torch.cuda.synchronize()
@@ -580,7 +589,7 @@ def main_gpu(args):
     def step_e2e():
         A_dev.copy_(A_host, non_blocking=True)
         b_dev.copy_(b_host, non_blocking=True)
-        tqr.lstsq(A_dev.t(), b_dev.t(), 128, 32, args.tree, 4, args.prec, tol=tol, max_iter=1000, X=X,
+        tqr.lstsq(A_dev.t(), b_dev.t(), 128, 32, args.tree, args.bs, args.prec, tol=tol, max_iter=1000, X=X,
                   workspace=ws, stream=stream)
         X_host.copy_(X.t(), non_blocking=True)
 
@@ -660,17 +669,21 @@ def minimal_bytes(args, nb=128, ib=32, esz=4):
 
 def tile_task_bytes(args):
     """Algorithmic bytes of one tensor-core factorization as a tile-task graph (nb 128, FP32
-    tiles of 64 KB, split operand images of nparts x 32 KB): every update reads and writes its
-    C tile(s) and reads its operand images (UNMQR: V, Z; TTMQR: V2, Z2, T^T); every panel task
-    reads and writes its tile (TTQRT: two triangles) and writes its images and T (16 KB).
-    A tile touched by consecutive tasks is counted each time: this is the traffic of the
+    tiles of 64 KB, split operand images of nparts x 32 KB, T blocks of 16 KB): every update
+    reads and writes its C tile(s) and reads its operand images (UNMQR: V, Z; TTMQR / TSMQR:
+    V2, Z2, T^T); a panel task reads and writes what it factors (GEQRT one tile, TTQRT two
+    triangles, TSQRT a triangle and a tile) and writes T; a preparation task reads the
+    factored tile and T and writes the images (2 after GEQRT, 3 after TTQRT / TSQRT).  A
+    tile touched by consecutive tasks is counted each time: this is the traffic of the
     method when no tile stays in L2 between tasks."""
     import paper_1303_3182_gb300 as tqr
     nparts = {"bf16": 1, "fp16": 1, "bf16x3": 2, "bf16x6": 3}[args.prec]
     tile, img, tblk = 128 * 128 * 4, nparts * 128 * 128 * 2, 32 * 128 * 4
-    c = tqr.plan_stats(args.m, args.n, 128, args.tree, 4)
-    return (c["UNMQR"] * (2 * tile + 2 * img) + c["TTMQR"] * (4 * tile + 3 * img)
-            + c["GEQRT"] * (2 * tile + 2 * img + tblk) + c["TTQRT"] * (2 * tile + 3 * img + tblk))
+    c = tqr.plan_counts(args.m, args.n, 128, args.tree, args.bs)
+    panel = c["GEQRT"] * (2 * tile + tblk) + c["TTQRT"] * (2 * tile + tblk) + c["TSQRT"] * (3 * tile + tblk)
+    prep = c["GEQRT"] * (tile + tblk + 2 * img) + (c["TTQRT"] + c["TSQRT"]) * (tile + tblk + 3 * img)
+    upd = c["UNMQR"] * (2 * tile + 2 * img) + (c["TTMQR"] + c["TSMQR"]) * (4 * tile + 3 * img)
+    return panel + prep + upd
 
 
 def schedule_bound(args, executor_ms):
@@ -683,7 +696,7 @@ def schedule_bound(args, executor_ms):
     import paper_1303_3182_gb300 as tqr
     nproc = torch.cuda.get_device_properties(0).multi_processor_count
     p, q = -(-args.m // 128), -(-args.n // 128)
-    ms, bound, lost = tqr.schedule(p, q, args.tree, 4, nproc, TENSOR_TASK_MEAN_US)
+    ms, bound, lost = tqr.schedule(p, q, args.tree, args.bs, nproc, TENSOR_TASK_MEAN_US)
     return {"claim_order": "CP-method list schedule on the resident CTAs (library default for tensor-core "
                            "precisions)", "claim_weights": list(TENSOR_CLAIM_WEIGHTS), "processors": nproc,
             "task_mean_us": list(TENSOR_TASK_MEAN_US),

@@ -113,9 +113,12 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len,
 int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
                  int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
 
-/* tqr_schedule with six kernel weights (GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR), each
- * >= 1: the TS kernels weighed on their own, e.g. by measured task durations.  weights
- * must not be NULL (-6); other arguments and errors as tqr_schedule. */
+/* tqr_schedule with seven weights: the kernels GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR
+ * (each >= 1; the TS kernels weighed on their own, e.g. by measured task durations) and
+ * the operand-image preparation tasks of the tensor-core precisions (>= 1: the graph the
+ * tensor-core executor runs, with one preparation task after every GEQRT, TTQRT and
+ * TSQRT; 0: the graph without them).  weights must not be NULL (-6); other arguments and
+ * errors as tqr_schedule. */
 int tqr_schedule_ts(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
                     int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
 
@@ -180,6 +183,25 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
 int tqr_batch_params(int nbatch, const int64_t *m, const int64_t *n, int prec,
                      const int64_t *table, int nrows, int *params);
 
+/* Autotuned size-class table of a batch (device work on "stream", synchronized).  The
+ * matrices are grouped into classes: a row bucket (1..1024, 1025..4096, 4097..) times the
+ * exact column count.  For each class the library factors a sample of up to 32 of the
+ * class's own shapes (seeded pseudo-random entries in scratch device memory it allocates
+ * and frees, inputs restored before every timed launch) as one batched launch per
+ * candidate and keeps the fastest by device time: the tile size nb in {32, 64, 128, 256}
+ * (Greedy, ib = min(nb, 32)), then ib in {8, 16, 32} at that nb, then the tree among
+ * Greedy, BinaryTree, Fibonacci, FlatTree, PlasmaTree(4) and the TS forms of FlatTree and
+ * PlasmaTree(4).  Tensor-core precisions keep nb = 128 and try ib in {16, 32}.  Results are
+ * cached per device, precision and class until tqr_finalize(); a cached class costs
+ * nothing.  This tuning is the library's own (the thesis factors one matrix at a time).
+ *   table    : out, capacity rows of 8 int64 {m_lo, m_hi, n_lo, n_hi, nb, ib, tree, bs}
+ *              (the layout tqr_batch_params reads), or NULL to query the row count.
+ *   nrows    : out, the number of classes (rows).
+ * Errors: -1 nbatch < 1, -2 NULL or a size < 1, -4 prec, -6 capacity too small, -7 nrows
+ * NULL; TQR_ENOMEM, TQR_ECUDA. */
+int tqr_batch_autotune(int nbatch, const int64_t *m, const int64_t *n, int prec, int64_t *table,
+                       int capacity, int *nrows, void *stream);
+
 /* Offsets of the matrices' T workspaces in one buffer: T of matrix b occupies bytes
  * [offsets[b], offsets[b] + tqr_workspace_size(m[b], n[b], nb_b, ib_b, prec)) and
  * offsets[nbatch] is the total; every offset is a multiple of 256.  Host only. */
@@ -195,8 +217,10 @@ typedef struct tqr_batch_plan tqr_batch_plan;
  *               for TQR_FP64, float otherwise) and its T workspace (tqr_workspace_size
  *               bytes for its nb/ib).  The plan keeps the pointers; the caller keeps the
  *               buffers alive while the plan is used and owns them.
- *   params    : 4 * nbatch ints from tqr_batch_params (NULL: built-in rule).  Tensor-
- *               core precisions need nb = 128 for every matrix.
+ *   params    : 4 * nbatch ints from tqr_batch_params, or NULL: each matrix takes its
+ *               size class's autotuned setting (tqr_batch_autotune, tuned on the legacy
+ *               stream on first use, then cached) - size T with tqr_batch_params over the
+ *               table tqr_batch_autotune returns.  Tensor-core precisions need nb = 128.
  *   prec      : TQR_FP64, TQR_FP32 or a tensor-core precision.
  * Task order: every matrix's own order (earliest start, then longest remaining path)
  * is kept; matrices are started longest-critical-path first, each offset by the work
@@ -241,7 +265,8 @@ void tqr_batch_plan_destroy(tqr_batch_plan *plan);
 
 /* One-shot batched factorization: tqr_batch_plan_create + one tqr_batch_plan_run
  * without a graph + destroy.  The call always synchronizes the stream (the plan's
- * buffers are freed before it returns). */
+ * buffers are freed before it returns).  params NULL = the autotuned settings (see
+ * tqr_batch_plan_create). */
 int tqr_factor_batched(int nbatch, const int64_t *m, const int64_t *n, void *const *A,
                        const int64_t *lda, const int *params, int prec, void *const *T,
                        void *stream);

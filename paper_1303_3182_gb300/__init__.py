@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             "tqr_batch_plan_status": (i32, [vp, vp]),
             "tqr_batch_plan_info": (i32, [vp, c_i64p]),
             "tqr_batch_plan_destroy": (None, [vp]),
+            "tqr_batch_autotune": (i32, [i32, c_i64p, c_i64p, i32, c_i64p, i32, ctypes.POINTER(ctypes.c_int), vp]),
             "tqr_factor_batched": (i32, [i32, c_i64p, c_i64p, ctypes.POINTER(vp), c_i64p,
                                          ctypes.POINTER(ctypes.c_int), i32, ctypes.POINTER(vp), vp]),
         }
@@ -173,10 +174,11 @@ def _weights4(weights):
 def schedule(p: int, q: int, tree="greedy", bs: int = 1, nproc: int = 1, weights=None):
     """Bounded-processor schedule of the factorization task graph on nproc processors:
     (CP-method makespan, ALAP Derived bound, lost area); weights are four kernel weights
-    (GEQRT, TTQRT, UNMQR, TTMQR; None = 4, 2, 6, 6; TS kernels 3 x TTQRT, 2 x TTMQR) or six
-    (..., TSQRT, TSMQR)."""
+    (GEQRT, TTQRT, UNMQR, TTMQR; None = 4, 2, 6, 6; TS kernels 3 x TTQRT, 2 x TTMQR), six
+    (..., TSQRT, TSMQR) or seven (..., operand-image preparation: the tensor-core graph)."""
     ms, bound, la = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
-    if weights is not None and len(weights) == 6:
+    if weights is not None and len(weights) in (6, 7):
+        weights = list(weights) + [0] * (7 - len(weights))
         fn, name = lib().tqr_schedule_ts, "tqr_schedule_ts"
     else:
         fn, name = lib().tqr_schedule, "tqr_schedule"
@@ -393,10 +395,29 @@ def _i64(a):
     return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
+def batch_autotune(ms, ns, prec="fp32", stream=None):
+    """tqr_batch_autotune: the library's per-size-class tuning table of a batch, an
+    (nclasses, 8) int64 array of rows (m_lo, m_hi, n_lo, n_hi, nb, ib, tree, bs), tuned by
+    device timing on first use and cached in the library."""
+    m, mp = _i64(ms)
+    n, np_ = _i64(ns)
+    rows = ctypes.c_int(0)
+    L = lib()
+    _check("tqr_batch_autotune", L.tqr_batch_autotune(len(m), mp, np_, _prec(prec), None, 0, ctypes.byref(rows),
+                                                      _stream(stream)))
+    table = np.zeros((max(rows.value, 1), 8), dtype=np.int64)
+    _check("tqr_batch_autotune", L.tqr_batch_autotune(len(m), mp, np_, _prec(prec),
+                                                      table.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                                      rows.value, ctypes.byref(rows), _stream(stream)))
+    return table[:rows.value]
+
+
 def batch_params(ms, ns, prec="fp32", table=None):
     """(nbatch, 4) int32 array of per-matrix (nb, ib, tree, bs): the first row of
     ``table`` (rows m_lo, m_hi, n_lo, n_hi, nb, ib, tree, bs) covering each matrix, else
-    the library's built-in size classes."""
+    the library's built-in size classes; table="auto" takes batch_autotune's table."""
+    if isinstance(table, str) and table == "auto":
+        table = batch_autotune(ms, ns, prec)
     m, mp = _i64(ms)
     n, np_ = _i64(ns)
     out = np.zeros((len(m), 4), dtype=np.int32)
@@ -507,11 +528,14 @@ class BatchPlan:
 
 def factor_batched(As, prec="fp32", params=None, T=None, stream=None):
     """One-shot batched factorization (tqr_factor_batched) of a list of column-major CUDA
-    tensors in place.  Returns (T buffer, byte offsets, params)."""
+    tensors in place.  params None: the library's autotuned settings (NULL through the
+    C ABI; T is sized from the same cached tuning table).  Returns (T buffer, byte
+    offsets, params)."""
     import torch
     ms = [int(a.shape[0]) for a in As]
     ns = [int(a.shape[1]) for a in As]
-    params = batch_params(ms, ns, prec) if params is None else \
+    auto = params is None
+    params = batch_params(ms, ns, prec, "auto") if auto else \
         np.ascontiguousarray(np.asarray(params, dtype=np.int32).reshape(-1, 4))
     off = batch_workspace_offsets(ms, ns, prec, params)
     if T is None:
@@ -524,6 +548,6 @@ def factor_batched(As, prec="fp32", params=None, T=None, stream=None):
     Tp = VP(*[T.data_ptr() + int(o) for o in off[:-1]])
     _check("tqr_factor_batched",
            lib().tqr_factor_batched(len(As), mp, np_, Ap, lp,
-                                    params.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _prec(prec),
-                                    Tp, _stream(stream)))
+                                    None if auto else params.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                    _prec(prec), Tp, _stream(stream)))
     return T, off, params

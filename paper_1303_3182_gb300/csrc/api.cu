@@ -386,12 +386,12 @@ void weights6(const int64_t w6[6], int64_t out[kNumKinds]) {
 }
 
 int schedule_impl(int p, int q, int tree, int bs, int nproc, const int64_t w[kNumKinds], int64_t *makespan,
-                  int64_t *alap_bound, int64_t *lost_area) {
+                  int64_t *alap_bound, int64_t *lost_area, bool prep = false) {
   try {
     std::vector<Elim> elims;
     elimination_list(p, q, tree_base(tree), bs, elims);
     GraphBuilder b(p * q * kRegionsPerTile);
-    add_factor_program(b, p, q, elims, tree_ts(tree));
+    add_factor_program(b, p, q, elims, tree_ts(tree), prep);
     const int n = static_cast<int>(b.tasks.size());
     std::vector<std::vector<int32_t>> succ(n);
     std::vector<int32_t> npred(n);
@@ -455,9 +455,11 @@ int tqr_schedule_ts(int p, int q, int tree, int bs, int nproc, const int64_t *we
   if (!weights) return -6;
   for (int c = 0; c < 6; ++c)
     if (weights[c] < 1) return -6;
+  if (weights[6] < 0) return -6;
   int64_t w[kNumKinds];
   weights6(weights, w);
-  return schedule_impl(p, q, tree, bs, nproc, w, makespan, alap_bound, lost_area);
+  w[kPrepG] = w[kPrepT] = weights[6];
+  return schedule_impl(p, q, tree, bs, nproc, w, makespan, alap_bound, lost_area, weights[6] > 0);
 }
 
 int tqr_set_claim_order(int mode, const int64_t *weights) {
@@ -760,6 +762,7 @@ const char *tqr_last_error(void) { return g_last_error.c_str(); }
 
 void tqr_finalize(void) {
   reset_static_scratch();
+  forget_autotune();
   std::lock_guard<std::mutex> lock(g_mu);
   g_plans.clear();
   for (auto &kv : g_scratch) cudaFree(kv.second.flags);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -285,12 +286,27 @@ int tqr_batch_plan_create(int nbatch, const int64_t *m, const int64_t *n, void *
   if (nbatch < 1 || !m || !n || !A || !lda || !T) return fail(-1, "empty batch or NULL array");
   try {
     std::vector<int> prm(4 * static_cast<size_t>(nbatch));
+    // no per-matrix tuning given: the autotuned setting of each size class (tuned on the
+    // legacy stream on first use, then cached)
+    std::vector<std::array<int64_t, 8>> rows;
+    if (!params) {
+      for (int b = 0; b < nbatch; ++b)
+        if (m[b] < 1 || n[b] < 1) return fail(-1, "matrix " + std::to_string(b) + ": size < 1");
+      const int rc = autotune_table(nbatch, m, n, prec, nullptr, rows);
+      if (rc) return rc;
+    }
     for (int b = 0; b < nbatch; ++b) {
       int *o = prm.data() + 4 * b;
-      if (params)
+      if (params) {
         std::memcpy(o, params + 4 * b, 4 * sizeof(int));
-      else
+      } else {
         default_params(std::max<int64_t>(m[b], 1), n[b], prec, o);
+        for (const auto &r : rows)
+          if (m[b] >= r[0] && m[b] <= r[1] && n[b] >= r[2] && n[b] <= r[3]) {
+            for (int c = 0; c < 4; ++c) o[c] = static_cast<int>(r[4 + c]);
+            break;
+          }
+      }
       const int rc = check_tiles(m[b], n[b], o[0], o[1], o[2], o[3], prec);
       if (rc) return fail(rc, "matrix " + std::to_string(b) + ": " + tqr_strerror(rc) + " (status " +
                                   std::to_string(rc) + ")");

@@ -1,6 +1,7 @@
 // Internal declarations of libtqr shared by the host and device translation units.
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -238,6 +239,12 @@ int launch_trsm(int64_t n, const void *A, int64_t lda, bool real_is_double, doub
 int trsm_flag_count(int64_t n);
 // Forgets the cached device addresses of tqr_trsm_static's fixed scratch (tqr_finalize).
 void reset_static_scratch();
+// The batched factorization's per-size-class autotuner (autotune.cu): one row {m_lo, m_hi,
+// n_lo, n_hi, nb, ib, tree, bs} per class of the batch, tuned on "stream" on first use and
+// cached per device, precision and class.  forget_autotune clears the cache.
+int autotune_table(int nbatch, const int64_t *m, const int64_t *n, int prec, void *stream,
+                   std::vector<std::array<int64_t, 8>> &rows);
+void forget_autotune();
 // Inverses of the 64 x 64 diagonal blocks of an upper-triangular R (FP64, 64*64 doubles
 // per block; identity on the padding of a partial last block).
 int launch_diag_inverse(int64_t n, const void *A, int64_t lda, bool real_is_double, double *Dinv, void *stream);

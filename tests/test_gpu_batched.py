@@ -191,3 +191,36 @@ def test_batched_full_size_sample_against_unique_r():
         err = np.max(np.abs(_r_positive(Rg) - _r_positive(Rl)))
         assert err <= tol, f"matrix {b} ({m}x{n}): {err} > {tol}"
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+def test_factor_batched_null_params_autotunes(prec):
+    """tqr_factor_batched with params NULL (through the C ABI): the library tunes each size
+    class of the batch by device timing (tqr_batch_autotune: tile size, inner block, tree)
+    and factors every matrix with its class's setting.  The table has one row per class
+    (row bucket x column count) with settings tqr_factor accepts; every matrix's result
+    equals tqr_factor's with the same setting bit for bit; a second call takes the cached
+    table."""
+    shapes = [(300, 32)] * 5 + [(2000, 64)] * 3 + [(5000, 128)] * 2 + [(700, 32)] * 2
+    dtype = torch.float32
+    mats = [synthetic.gaussian(m, n, seed=6100 + b).astype(np.float32).astype(np.float64)
+            for b, (m, n) in enumerate(shapes)]
+    As = [to_dev(A, dtype) for A in mats]
+    T, off, params = tqr.factor_batched(As, prec)  # params None -> NULL -> autotuned
+    torch.cuda.synchronize()
+    ms, ns = [m for m, _ in shapes], [n for _, n in shapes]
+    table = tqr.batch_autotune(ms, ns, prec)
+    assert np.array_equal(table, tqr.batch_autotune(ms, ns, prec))  # cached
+    classes = {(0 if m <= 1024 else (1 if m <= 4096 else 2), n) for m, n in shapes}
+    assert len(table) == len(classes)
+    for row in table:
+        nb, ib, tree, bs = (int(x) for x in row[4:])
+        assert ib <= nb and ib <= 32 and (nb == 128 if prec != "fp32" else nb in (32, 64, 128, 256))
+    for b, (m, n) in enumerate(shapes):
+        row = [r for r in table if r[0] <= m <= r[1] and r[2] <= n <= r[3]]
+        assert len(row) == 1 and list(params[b]) == [int(x) for x in row[0][4:]]
+        nb, ib, tree, bs = (int(x) for x in params[b])
+        ref = to_dev(mats[b], dtype)
+        tqr.factor(ref, nb, ib, tree, bs, prec)
+        torch.cuda.synchronize()
+        assert torch.equal(ref, As[b]), b

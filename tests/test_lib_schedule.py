@@ -104,15 +104,19 @@ def test_claim_orders_equal_the_oracle_schedules(p, q, tree, bs):
 
 def test_bench_tile_task_bytes_match_the_oracle_kernel_counts():
     """bench.py's algorithmic bytes of the tensor-core factorization (tile-task traffic) from
-    the library's plan statistics equal the same sum over the oracle's kernel counts."""
+    the library's plan counts equal the same sum over the oracle's kernel counts of the
+    benchmark's tree (the TS form of PlasmaTree(32) and, for comparison, Greedy)."""
     import bench
 
-    class Args:
-        m, n, tree, prec = 32768, 4096, "greedy", "bf16x6"
-
-    p, q = 256, 32
-    c = E.kernel_counts(p, q, E.elimination_list(p, q, E.GREEDY))
-    tile, img, tblk = 128 * 128 * 4, 3 * 128 * 128 * 2, 32 * 128 * 4
-    want = (c["UNMQR"] * (2 * tile + 2 * img) + c["TTMQR"] * (4 * tile + 3 * img)
-            + c["GEQRT"] * (2 * tile + 2 * img + tblk) + c["TTQRT"] * (2 * tile + 3 * img + tblk))
-    assert bench.tile_task_bytes(Args) == want
+    for tree, bs, ts in (("plasma-ts", 32, True), ("greedy", 1, False)):
+        class Args:
+            m, n, prec = 32768, 4096, "bf16x6"
+        Args.tree, Args.bs = tree, bs
+        p, q = 256, 32
+        base = E.PLASMA if tree.startswith("plasma") else E.GREEDY
+        c = E.kernel_counts(p, q, E.elimination_list(p, q, base, bs=bs), ts=ts)
+        tile, img, tblk = 128 * 128 * 4, 3 * 128 * 128 * 2, 32 * 128 * 4
+        want = (c["GEQRT"] * (2 * tile + tblk) + c["TTQRT"] * (2 * tile + tblk) + c["TSQRT"] * (3 * tile + tblk)
+                + c["GEQRT"] * (tile + tblk + 2 * img) + (c["TTQRT"] + c["TSQRT"]) * (tile + tblk + 3 * img)
+                + c["UNMQR"] * (2 * tile + 2 * img) + (c["TTMQR"] + c["TSMQR"]) * (4 * tile + 3 * img))
+        assert bench.tile_task_bytes(Args) == want, tree
