@@ -11,6 +11,9 @@ the library; the two share only the seeded generators of ``synthetic``.
   kernels TSQRT/TSMQR applied one reflector at a time, the tiled algorithm (TT form,
   and the TS form of a list: TS kernels for the rows that never pivot in a column),
   apply-Q, back substitution, least squares.
+* ``zhouseholder`` - the same in double complex (the thesis's second precision): LAPACK's
+  complex reflector convention (real beta, H^H [alpha; x] = [beta; 0]), the complex tile
+  kernels (TT and TS), the tiled algorithm, Q^H / Q, least squares.
 * ``refine``     - FP64 least-squares checks (backward error, residual).
 * ``schedule``   - bounded-processor scheduling of the task graph (thesis Chapter 5):
   Backflow priorities, the CP-method list schedule, the ALAP Derived bound.

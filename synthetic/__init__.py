@@ -19,6 +19,14 @@ def gaussian(m: int, n: int, seed: int) -> np.ndarray:
     return np.asfortranarray(rng.standard_normal((m, n)))
 
 
+def complex_gaussian(m: int, n: int, seed: int) -> np.ndarray:
+    """m x n matrix of i.i.d. standard complex normal entries (N(0, 1/2) real and imaginary
+    parts), complex128."""
+    rng = np.random.default_rng(seed)
+    z = (rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))) / np.sqrt(2.0)
+    return np.asfortranarray(z)
+
+
 def haar_orthonormal(m: int, n: int, rng: np.random.Generator) -> np.ndarray:
     """m x n matrix with Haar-distributed orthonormal columns (m >= n)."""
     G = rng.standard_normal((m, n))
