@@ -63,9 +63,16 @@ enum { TQR_TS = 16 };
  *                lo*hi, ~2^-16 relative) with FP32 accumulation.
  *   TQR_BF16X6 : as TQR_BF16X3 with a three-way split and six products (~2^-24, close
  *                to FP32 updates).
- *   TQR_BF16, TQR_FP16 : as TQR_BF16X3 with one bf16 / fp16 product. */
+ *   TQR_BF16, TQR_FP16 : as TQR_BF16X3 with one bf16 / fp16 product.
+ *   TQR_Z64    : double complex, the thesis's second precision (Section 3.3): matrices,
+ *                T and right-hand sides are interleaved (re, im) doubles, leading
+ *                dimensions count complex elements; LAPACK's complex reflectors (real
+ *                beta, H^H [alpha; x] = [beta; 0]), so R has a real diagonal; tqr_apply_qt
+ *                applies Q^H (trans = 0) or Q; nb <= 128; no batched or tensor-core form.
+ *                Reported flops are 4 x 2 n^2 (m - n/3) (a complex multiply-add is 8
+ *                real flops). */
 typedef enum { TQR_FP64 = 0, TQR_BF16 = 1, TQR_FP16 = 2, TQR_BF16X3 = 3, TQR_FP32 = 4,
-               TQR_BF16X6 = 5 } tqr_prec;
+               TQR_BF16X6 = 5, TQR_Z64 = 6 } tqr_prec;
 
 enum {
   TQR_OK = 0,

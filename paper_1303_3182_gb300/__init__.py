@@ -25,8 +25,8 @@ TS = 16  # flag: the TS form of a tree (TSQRT/TSMQR for rows that never pivot)
 TREES = {"flat": FLAT, "plasma": PLASMA, "binary": BINARY, "fibonacci": FIBONACCI,
          "greedy": GREEDY, "grasap": GRASAP, "asap": ASAP}
 TREES.update({name + "-ts": v | TS for name, v in list(TREES.items())})
-FP64, BF16, FP16, BF16X3, FP32, BF16X6 = 0, 1, 2, 3, 4, 5
-PRECS = {"fp64": FP64, "bf16": BF16, "fp16": FP16, "bf16x3": BF16X3, "fp32": FP32, "bf16x6": BF16X6}
+FP64, BF16, FP16, BF16X3, FP32, BF16X6, Z64 = 0, 1, 2, 3, 4, 5, 6
+PRECS = {"fp64": FP64, "bf16": BF16, "fp16": FP16, "bf16x3": BF16X3, "fp32": FP32, "bf16x6": BF16X6, "z64": Z64}
 TQR_ETIMEOUT = 3
 TQR_EUNSUPPORTED = 5
 
@@ -307,12 +307,13 @@ def finalize() -> None:
 
 def _dtype_of(prec):
     import torch
-    return torch.float64 if _prec(prec) == FP64 else torch.float32
+    p = _prec(prec)
+    return torch.complex128 if p == Z64 else (torch.float64 if p == FP64 else torch.float32)
 
 
 def factor(A, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64", T=None, stream=None):
-    """Tiled QR of A in place (column-major CUDA tensor, float64 for fp64 else float32).
-    Returns the T workspace tensor (bytes)."""
+    """Tiled QR of A in place (column-major CUDA tensor: float64 for fp64, complex128 for
+    z64, float32 otherwise).  Returns the T workspace tensor (bytes)."""
     import torch
     m, n = A.shape
     if A.dtype != _dtype_of(prec) or not A.is_cuda:
@@ -328,11 +329,13 @@ def factor(A, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64", T=None,
 
 def apply_qt(A, T, B, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64",
              trans: int = 0, stream=None):
-    """B <- Q^T B (trans=0) or Q B (trans=1) in place; B is a float64 column-major
-    tensor with A's row count."""
+    """B <- Q^T B (trans=0; Q^H for z64) or Q B (trans=1) in place; B is a float64
+    (complex128 for z64) column-major tensor with A's row count."""
+    import torch
     m, n = A.shape
-    if B.dtype.itemsize != 8 or B.shape[0] != m:
-        raise ValueError("B must be float64 with m rows")
+    want = torch.complex128 if _prec(prec) == Z64 else torch.float64
+    if B.dtype != want or B.shape[0] != m:
+        raise ValueError("B must be float64 (complex128 for z64) with m rows")
     _check("tqr_apply_qt", lib().tqr_apply_qt(m, n, nb, ib, _tree(tree), bs, _prec(prec), trans,
                                               ctypes.c_void_p(A.data_ptr()), _ld(A, m),
                                               ctypes.c_void_p(T.data_ptr()),
@@ -367,12 +370,14 @@ def lstsq_workspace_size(m, n, nrhs, nb, ib, prec="fp64") -> int:
 
 def lstsq(A, B, nb: int, ib: int, tree="greedy", bs: int = 1, prec="fp64", tol: float = 1e-14,
           max_iter: int = 100, X=None, workspace=None, stream=None, return_iters: bool = False):
-    """Least-squares solution X of min ||A X - B|| (float64 column-major CUDA tensors)."""
+    """Least-squares solution X of min ||A X - B|| (float64 column-major CUDA tensors;
+    complex128 for z64)."""
     import torch
     m, n = A.shape
     nrhs = B.shape[1]
     if X is None:
-        X = colmajor(torch.empty((n, nrhs), dtype=torch.float64, device=A.device))
+        dt = torch.complex128 if _prec(prec) == Z64 else torch.float64
+        X = colmajor(torch.empty((n, nrhs), dtype=dt, device=A.device))
     if workspace is None:
         workspace = torch.empty(lstsq_workspace_size(m, n, nrhs, nb, ib, prec), dtype=torch.uint8,
                                 device=A.device)

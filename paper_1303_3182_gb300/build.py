@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 SOURCES = ["api.cu", "batch.cu", "factor.cu", "exec_f64.cu", "exec_f32.cu", "exec_f32_apply.cu", "exec_mixed.cu",
-           "solve.cu", "precond.cu", "refine.cu", "peak.cu", "autotune.cu", "graph.cpp", "elim.cpp"]
+           "solve.cu", "precond.cu", "refine.cu", "peak.cu", "autotune.cu", "zexec.cu", "graph.cpp", "elim.cpp"]
 HEADERS = ["tqr_internal.h", "umma.cuh", "executor.cuh", "mixed_tasks.cuh"]
 LIB = os.path.join(PKG, "libtqr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

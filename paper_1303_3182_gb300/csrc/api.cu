@@ -310,7 +310,8 @@ int check_tiles(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec
   if (ib < 1 || ib > nb || ib > 32) return -4;
   if (!valid_tree(tree)) return -5;
   if (tree_base(tree) == TQR_PLASMA && bs < 1) return -6;
-  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -7;
+  if (prec < TQR_FP64 || prec > TQR_Z64) return -7;
+  if (prec == TQR_Z64 && nb > 128) return -3;
   if (ceil_div(m, nb) > 32767 || ceil_div(n, nb) > 32767) return -3;
   return 0;
 }
@@ -322,7 +323,7 @@ size_t ops_offset(int64_t m, int64_t n, int nb, int ib) {
 
 size_t factor_workspace_bytes(int64_t m, int64_t n, int nb, int ib, int prec) {
   const int64_t P = ceil_div(m, nb), Q = ceil_div(n, nb), K = std::min(P, Q);
-  const size_t esz = prec == TQR_FP64 ? sizeof(double) : sizeof(float);
+  const size_t esz = prec == TQR_Z64 ? 2 * sizeof(double) : (prec == TQR_FP64 ? sizeof(double) : sizeof(float));
   if (!is_tensor_prec(prec)) return static_cast<size_t>(2 * P * K) * ib * nb * esz;
   return ops_offset(m, n, nb, ib) + static_cast<size_t>(2 * P * K) * mixed_slot_bytes(tensor_parts(prec));
 }
@@ -502,7 +503,8 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
   if (lda < m) return -9;
   if (!T) return -10;
   const bool dbl = prec == TQR_FP64;
-  if (!is_tensor_prec(prec) && executor_smem_bytes(nb, ib, dbl, false) == 0) {
+  if (prec == TQR_Z64 ? zexecutor_smem_bytes(nb, ib) == 0
+                      : (!is_tensor_prec(prec) && executor_smem_bytes(nb, ib, dbl, false) == 0)) {
     g_last_error = "nb/ib too large for one SM's shared memory";
     return TQR_EUNSUPPORTED;
   }
@@ -514,7 +516,8 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
       std::lock_guard<std::mutex> lock(g_mu);
       order = effective_order(prec);
     }
-    if (order.mode == 1) order.nproc = executor_slots(dbl, is_tensor_prec(prec), nb, ib);
+    if (order.mode == 1)
+      order.nproc = prec == TQR_Z64 ? zexec_slots(nb, ib) : executor_slots(dbl, is_tensor_prec(prec), nb, ib);
     if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order, is_tensor_prec(prec))) != 0) return rc;
     ExecParams prm{};
     prm.A = A;
@@ -527,6 +530,7 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
     prm.Q = Q;
     prm.T = T;
     prm.B = nullptr;
+    prm.cplx = prec == TQR_Z64 ? 1 : 0;
     if (is_tensor_prec(prec)) {
       prm.mixed = 1;
       prm.ops = static_cast<char *>(T) + ops_offset(m, n, nb, ib);
@@ -554,7 +558,8 @@ int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int pre
   if (nrhs < 0) return -14;
   if (nrhs == 0) return TQR_OK;
   const bool dbl = prec == TQR_FP64;
-  if (executor_smem_bytes(nb, ib, dbl, true) == 0) return TQR_EUNSUPPORTED;
+  if (prec == TQR_Z64 ? zexecutor_smem_bytes(nb, ib) == 0 : executor_smem_bytes(nb, ib, dbl, true) == 0)
+    return TQR_EUNSUPPORTED;
   try {
     const int P = static_cast<int>(ceil_div(m, nb)), Q = static_cast<int>(ceil_div(n, nb));
     Plan *plan = nullptr;
@@ -573,6 +578,7 @@ int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int pre
     prm.ldb = ldb;
     prm.nrhs = nrhs;
     prm.trans = trans;
+    prm.cplx = prec == TQR_Z64 ? 1 : 0;
     return run_plan(plan, prm, dbl, static_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc &) {
     return TQR_ENOMEM;
@@ -582,13 +588,25 @@ int tqr_apply_qt(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int pre
 int tqr_trsm(int64_t n, int prec, const void *A, int64_t lda, double *B, int64_t ldb, int64_t nrhs,
              void *stream) {
   if (n < 1) return -1;
-  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -2;
+  if (prec < TQR_FP64 || prec > TQR_Z64) return -2;
   if (!A) return -3;
   if (lda < n) return -4;
   if (!B) return -5;
   if (ldb < n) return -6;
   if (nrhs < 0) return -7;
   if (nrhs == 0) return TQR_OK;
+  if (prec == TQR_Z64) {
+    cudaStream_t zst = static_cast<cudaStream_t>(stream);
+    LaunchTimer ztimer(2, zst);
+    const int zrc = launch_ztrsm(n, A, lda, B, ldb, nrhs, stream);
+    ztimer.stop(zst);
+    if (zrc) return cuda_fail(static_cast<cudaError_t>(zrc), "complex trsm launch");
+    if (g_sync) {
+      const cudaError_t e = cudaStreamSynchronize(zst);
+      if (e != cudaSuccess) return cuda_fail(e, "complex trsm");
+    }
+    return TQR_OK;
+  }
   Scratch *s = nullptr;
   const int nflags = trsm_flag_count(n);
   int rc = get_scratch(nflags, &s);
@@ -613,9 +631,10 @@ int tqr_lstsq_workspace_size(int64_t m, int64_t n, int64_t nrhs, int nb, int ib,
   size_t tb = 0;
   if ((rc = tqr_workspace_size(m, n, nb, ib, prec, &tb)) != 0) return rc;
   const size_t nr = static_cast<size_t>(std::max<int64_t>(nrhs, 1));
-  if (prec == TQR_FP64) {
-    *bytes = align_up(static_cast<size_t>(m) * n * sizeof(double), 256) + align_up(tb, 256) +
-             align_up(static_cast<size_t>(m) * nr * sizeof(double), 256);
+  if (prec == TQR_FP64 || prec == TQR_Z64) {
+    const size_t esz = prec == TQR_Z64 ? 2 * sizeof(double) : sizeof(double);
+    *bytes = align_up(static_cast<size_t>(m) * n * esz, 256) + align_up(tb, 256) +
+             align_up(static_cast<size_t>(m) * nr * esz, 256);
   } else {
     const size_t ldf = align_up(static_cast<size_t>(m), 32);
     const size_t nr64 = std::min<size_t>(nr, 64);
@@ -647,21 +666,21 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
   char *ws = static_cast<char *>(workspace);
   size_t tb = 0;
   tqr_workspace_size(m, n, nb, ib, prec, &tb);
-  if (prec == TQR_FP64) {
-    double *Aw = reinterpret_cast<double *>(ws);
-    void *Tw = ws + align_up(static_cast<size_t>(m) * n * sizeof(double), 256);
+  if (prec == TQR_FP64 || prec == TQR_Z64) {
+    // plain QR solve: X = R^{-1} (Q^T B)(0:n) (Q^H for the complex precision); elements of
+    // esz bytes (complex: interleaved pairs, leading dimensions in complex elements)
+    const size_t esz = prec == TQR_Z64 ? 2 * sizeof(double) : sizeof(double);
+    char *Aw = ws;
+    void *Tw = ws + align_up(static_cast<size_t>(m) * n * esz, 256);
     double *Bw = reinterpret_cast<double *>(static_cast<char *>(Tw) + align_up(tb, 256));
-    cudaError_t e = cudaMemcpy2DAsync(Aw, m * sizeof(double), A, lda * sizeof(double), m * sizeof(double), n,
-                                      cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaMemcpy2DAsync(Aw, m * esz, A, lda * esz, m * esz, n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(Bw, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
-                            cudaMemcpyDeviceToDevice, st);
+      e = cudaMemcpy2DAsync(Bw, m * esz, B, ldb * esz, m * esz, nrhs, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-in");
     if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Aw, m, Tw, stream)) != 0) return rc;
     if ((rc = tqr_apply_qt(m, n, nb, ib, tree, bs, prec, 0, Aw, m, Tw, Bw, m, nrhs, stream)) != 0) return rc;
     if ((rc = tqr_trsm(n, prec, Aw, m, Bw, m, nrhs, stream)) != 0) return rc;
-    e = cudaMemcpy2DAsync(X, ldx * sizeof(double), Bw, m * sizeof(double), n * sizeof(double), nrhs,
-                          cudaMemcpyDeviceToDevice, st);
+    e = cudaMemcpy2DAsync(X, ldx * esz, Bw, m * esz, n * esz, nrhs, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "lstsq copy-out");
     if (g_sync) {
       e = cudaStreamSynchronize(st);

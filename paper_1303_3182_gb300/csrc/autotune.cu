@@ -243,7 +243,7 @@ extern "C" int tqr_batch_autotune(int nbatch, const int64_t *m, const int64_t *n
   if (!m || !n) return -2;
   for (int b = 0; b < nbatch; ++b)
     if (m[b] < 1 || n[b] < 1) return -2;
-  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -4;
+  if (prec < TQR_FP64 || prec >= TQR_Z64) return -4;
   if (!nrows) return -7;
   try {
     std::vector<std::array<int64_t, 8>> rows;

@@ -239,7 +239,7 @@ int tqr_batch_params(int nbatch, const int64_t *m, const int64_t *n, int prec, c
                      int *params) {
   if (nbatch < 1 || !m || !n) return -1;
   if (!params) return -4;
-  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -7;
+  if (prec < TQR_FP64 || prec >= TQR_Z64) return -7;
   for (int r = 0; table && r < nrows; ++r) {
     const int64_t *row = table + 8 * r;
     const int rc = check_tiles(1, 1, static_cast<int>(row[4]), static_cast<int>(row[5]), static_cast<int>(row[6]),
@@ -284,6 +284,7 @@ int tqr_batch_plan_create(int nbatch, const int64_t *m, const int64_t *n, void *
   if (!plan) return -4;
   *plan = nullptr;
   if (nbatch < 1 || !m || !n || !A || !lda || !T) return fail(-1, "empty batch or NULL array");
+  if (prec == TQR_Z64) return fail(-7, "the batched factorization has no double-complex form");
   try {
     std::vector<int> prm(4 * static_cast<size_t>(nbatch));
     // no per-matrix tuning given: the autotuned setting of each size class (tuned on the

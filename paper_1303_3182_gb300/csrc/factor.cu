@@ -28,6 +28,7 @@ int executor_slots(bool real_is_double, bool mixed, int nb, int ib) {
 }
 
 int launch_executor(const ExecParams &p, bool real_is_double, void *stream) {
+  if (p.cplx) return zexec_launch(p, stream);
   const bool apply_q = p.B != nullptr;
   if (p.mixed && !apply_q && !real_is_double) return exec_launch_mixed(p, stream, mixed_smem_bytes());
   const size_t smem = executor_smem_bytes(p.nb, p.ib, real_is_double, apply_q);

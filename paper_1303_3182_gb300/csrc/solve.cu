@@ -306,7 +306,7 @@ extern "C" int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, 
                                int64_t nrhs, void *stream) {
   using namespace tqr;
   if (n < 1) return -1;
-  if (prec < TQR_FP64 || prec > TQR_BF16X6) return -2;
+  if (prec < TQR_FP64 || prec >= TQR_Z64) return -2;
   if (!A) return -3;
   if (lda < n) return -4;
   if (!B) return -5;

@@ -192,6 +192,7 @@ struct ExecParams {
   int fmt;               // 1 = bf16, 0 = fp16
   int mixed;             // 1: GEQRT/TTQRT prepare images, UNMQR/TTMQR run on tcgen05
   int vec4;              // A is 16-byte aligned with lda % 4 == 0 (vector loads allowed)
+  int cplx;              // 1: double-complex storage (the complex executor runs the graph)
   int64_t *trace;        // optional: per task {claim, start, end, sm} globaltimer stamps
   // batched factorization: per-task matrix index and per-matrix geometry (else null)
   const int32_t *mat_of;
@@ -210,6 +211,12 @@ int exec_launch_mixed(const ExecParams &p, void *stream, size_t smem);
 int exec_slots_f64(size_t smem);
 int exec_slots_f32(size_t smem);
 int exec_slots_mixed(size_t smem);
+// The double-complex executor (zexec.cu): shared memory (0 if nb/ib do not fit), launch,
+// resident CTAs; and the complex triangular solve R X = B (R upper n x n, lda; B ldb).
+size_t zexecutor_smem_bytes(int nb, int ib);
+int zexec_launch(const ExecParams &p, void *stream);
+int zexec_slots(int nb, int ib);
+int launch_ztrsm(int64_t n, const void *R, int64_t lda, void *B, int64_t ldb, int64_t nrhs, void *stream);
 // Dynamic shared memory the executor needs (0 if nb/ib do not fit on one SM).
 size_t executor_smem_bytes(int nb, int ib, bool real_is_double, bool apply_q);
 // Resident factorization CTAs on the current device (SMs x CTAs per SM), 0 on error.

@@ -190,3 +190,17 @@ def _conflict(a, b):
     ra, wa = _regions(a)
     rb, wb = _regions(b)
     return bool(wa & (rb | wb)) or bool(wb & ra)
+
+
+def test_complex_precision_arguments():
+    """TQR_Z64: 16-byte T entries, nb <= 128, no batched form (host checks only)."""
+    L = tqr.lib()
+    sz = tqr.workspace_size(256, 128, 64, 16, "z64")
+    assert sz == 2 * tqr.workspace_size(256, 128, 64, 16, "fp64")
+    out = ctypes.c_size_t(0)
+    assert L.tqr_workspace_size(256, 128, 256, 16, tqr.Z64, ctypes.byref(out)) == -3
+    assert L.tqr_factor(256, 128, 256, 16, 4, 1, tqr.Z64, ctypes.c_void_p(1), 256, ctypes.c_void_p(1), None) == -3
+    m = (ctypes.c_int64 * 1)(64)
+    ptrs = (ctypes.c_void_p * 1)(1)
+    h = ctypes.c_void_p(0)
+    assert L.tqr_batch_plan_create(1, m, m, ptrs, m, None, tqr.Z64, ptrs, ctypes.byref(h)) == -7
