@@ -11,14 +11,14 @@
 // the tensor cores read, so that an update task fetches them with bulk copies.
 //
 // UNMQR(i,k,j) on C (nb x nb):   W^T = C^T V  (tcgen05, TMEM)  ->  C -= Z W
-// TTMQR(i,piv,k,j) on [C1; C2]:  W^T = C1^T + C2^T V2 (TMEM initialised with C1^T)
-//                                C2 -= Z2 W,  C1 -= T^T W
+// TTMQR(i,piv,k,j) on [C1; C2]:  W^T = C1^T + C2^T V2,  C2 -= Z2 W,  C1 -= T^T W
+// (TSMQR: the same with a dense V2)
 // Operands are split into 1, 2 or 3 16-bit parts (x = p0 + p1 + p2, each the rounding of
 // what the previous parts leave) and multiplied as the sum of the part products whose
 // orders add up to less than the part count: one bf16/fp16 product, split-bf16 x3
 // (hi*hi + hi*lo + lo*hi, ~2^-16 relative) or split-bf16 x6 (three parts, ~2^-24),
-// always accumulated in FP32 in tensor memory.  C tiles are read once into TMEM and the
-// second product accumulates onto them with a negated B, so C is read and written once.
+// accumulated in FP32 in tensor memory into fresh accumulators, small part products first
+// (issue_levels); the old tile values are added to the update in FP32 by the epilogue.
 // The tensor-core tile is nb = 128.
 #pragma once
 
@@ -358,29 +358,60 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   __syncthreads();
 }
 
-// D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) op(B)^T over K = 128 for split operands:
-// sum of the products A_qa B_qb with qa + qb < nparts (hi*hi; + hi*lo + lo*hi for two
-// parts; + hi*lo2 + mid*mid + lo2*hi for three), smallest terms first.  neg_b negates B.
-// Only the k-steps ks0 .. ks1-1 (16 columns of K each) are issued, so that a GEMM can be
-// issued in parts as its operands become ready.
-__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const unsigned char *bufA, const unsigned char *bufB,
-                                           int nparts, int fmt, int neg_b, uint32_t accumulate_first,
-                                           int ks0 = 0, int ks1 = kMNB / 16) {
+// D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) op(B)^T for split operands: the part
+// products A_qa B_qb of one "level" s = qa + qb (s < nparts: hi*hi is level 0; hi*lo and
+// lo*hi level 1; hi*lo2, mid*mid, lo2*hi level 2) for the k-steps ks0 .. ks1-1 (16 columns
+// of K each), levels lvl_hi down to lvl_lo, level-major.  neg_b negates B.  acc: whether
+// the first MMA accumulates onto D; set to 1 afterwards.
+//
+// Order matters for accuracy: the tensor cores round the running FP32 sum of every MMA
+// towards zero relative to its magnitude, so a product added to a large accumulator loses
+// up to an ulp of that accumulator, and these losses share a sign.  The updates therefore
+// accumulate into a fresh D (the tile itself is added once, in FP32, by the epilogue) and
+// issue every small level over the whole K range before the level-0 products: of the
+// 8 nparts(nparts+1)/2 MMAs of a product only the 8 level-0 ones meet a full-size sum.
+__device__ __forceinline__ void issue_levels(uint32_t d_tmem, const unsigned char *bufA, const unsigned char *bufB,
+                                             int nparts, int fmt, int neg_b, uint32_t &acc, int ks0, int ks1,
+                                             int lvl_lo, int lvl_hi) {
   const uint32_t idesc = umma::idesc_f16(128, 128, fmt, neg_b);
   const uint32_t a0 = umma::smem_u32(bufA), b0 = umma::smem_u32(bufB);
 #pragma unroll 1
-  for (int ks = ks0; ks < ks1; ++ks) {
-    const uint32_t off = (ks >> 2) * (kMNB * 128) + (ks & 3) * 32;
-    uint32_t acc = (ks > 0 || accumulate_first) ? 1u : 0u;
-    for (int s = nparts - 1; s >= 0; --s) {        // s = qa + qb
-      for (int qa = s; qa >= 0; --qa) {
-        const int qb = s - qa;
-        umma::mma_f16(d_tmem, umma::smem_desc(a0 + qa * kImg + off), umma::smem_desc(b0 + qb * kImg + off),
-                      idesc, acc);
+  for (int lv = lvl_hi; lv >= lvl_lo; --lv) {
+#pragma unroll 1
+    for (int ks = ks0; ks < ks1; ++ks) {
+      const uint32_t off = (ks >> 2) * (kMNB * 128) + (ks & 3) * 32;
+      for (int qa = lv; qa >= 0; --qa) {
+        const int qb = lv - qa;
+        if (qa >= nparts || qb >= nparts) continue;
+        umma::mma_f16(d_tmem, umma::smem_desc(a0 + qa * kImg + off), umma::smem_desc(b0 + qb * kImg + off), idesc,
+                      acc);
         acc = 1u;
       }
     }
   }
+}
+
+// One K half h (k-steps 4h .. 4h+3) of a fresh product D = A op(B)^T, issued as its
+// operand half becomes ready: half 0 issues the small levels of its k-steps; half 1 the
+// small levels of its own, then the level-0 products of all eight k-steps.  With one
+// part (bf16 / fp16) each half issues its own k-steps.
+__device__ __forceinline__ void issue_product_half(uint32_t d_tmem, const unsigned char *bufA,
+                                                   const unsigned char *bufB, int nparts, int fmt, int neg_b,
+                                                   uint32_t &acc, int h) {
+  if (nparts == 1) {
+    issue_levels(d_tmem, bufA, bufB, nparts, fmt, neg_b, acc, 4 * h, 4 * h + 4, 0, 0);
+    return;
+  }
+  issue_levels(d_tmem, bufA, bufB, nparts, fmt, neg_b, acc, 4 * h, 4 * h + 4, 1, nparts - 1);
+  if (h == 1) issue_levels(d_tmem, bufA, bufB, nparts, fmt, neg_b, acc, 0, 8, 0, 0);
+}
+
+// A whole fresh product D = A op(B)^T (both operands resident), in the same order.
+__device__ __forceinline__ void issue_product(uint32_t d_tmem, const unsigned char *bufA, const unsigned char *bufB,
+                                              int nparts, int fmt, int neg_b) {
+  uint32_t acc = 0u;
+  issue_product_half(d_tmem, bufA, bufB, nparts, fmt, neg_b, acc, 0);
+  issue_product_half(d_tmem, bufA, bufB, nparts, fmt, neg_b, acc, 1);
 }
 
 // Loads this thread's row r of a tile (half the columns, by warp group) and stores it
@@ -443,13 +474,32 @@ __device__ void c_transposed_image(unsigned char *img, const float *C, int64_t l
 
 // W^T (TMEM lane c, column a) -> split image of W as a B operand (row c, k = a), K half h
 // only (a in 64h .. 64h+63: warps 0-3 take the first 32 columns, warps 4-7 the next 32).
-__device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, int nparts, int h) {
+// C1 non-null (TTMQR / TSMQR): W^T(c, a) += C1(a, c) in FP32 first - the identity part of
+// the pair's reflectors - with C1(a, c) read from global memory (zero for c >= ncols).
+__device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, int nparts, int h,
+                                  const float *C1 = nullptr, int64_t ldc1 = 0, int ncols = 0, bool vec4 = false) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = (warp & 3) * 32 + lane;
   const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
   const int a0 = 64 * h + (warp >> 2) * 32;
   float v[32];
   umma::tmem_ld32(tmem_w + lane_base + a0, v);
+  if (C1) {
+    const float *col = C1 + static_cast<int64_t>(c) * ldc1 + a0;
+    if (c < ncols && vec4) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 q4 = __ldcg(reinterpret_cast<const float4 *>(col) + u);
+        v[4 * u] += q4.x;
+        v[4 * u + 1] += q4.y;
+        v[4 * u + 2] += q4.z;
+        v[4 * u + 3] += q4.w;
+      }
+    } else if (c < ncols) {
+#pragma unroll
+      for (int u = 0; u < 32; ++u) v[u] += __ldcg(col + u);
+    }
+  }
   with_parts(nparts, [&](auto np) {
     constexpr int NP = decltype(np)::value;
 #pragma unroll
@@ -463,19 +513,27 @@ __device__ void w_image_from_tmem(unsigned char *img, uint32_t tmem_w, int fmt, 
   });
 }
 
-// Stores the accumulator at tmem_d (lane r, column c) into C(r, c).
-__device__ void tmem_to_tile(float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem_d) {
+// C(r, c) = base(r, c) + P(r, c), the update P at tmem_p (lane r, column c) added in FP32 to
+// the tile's old values: base at tmem_base (lane r) when tmem_base != 0, else read from C.
+__device__ void tile_plus_tmem(float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem_p, uint32_t tmem_base) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = (warp & 3) * 32 + lane;
   const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
   for (int g = 0; g < 2; ++g) {
     const int c0 = (warp >> 2) * 64 + g * 32;
-    float v[32];
-    umma::tmem_ld32(tmem_d + lane_base + c0, v);
+    float v[32], b[32];
+    umma::tmem_ld32(tmem_p + lane_base + c0, v);
+    if (tmem_base) {
+      umma::tmem_ld32(tmem_base + lane_base + c0, b);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        b[j] = (r < nrows && c0 + j < ncols) ? __ldcg(C + r + static_cast<int64_t>(c0 + j) * ldc) : 0.f;
+    }
     if (r < nrows) {
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (c0 + j < ncols) C[r + static_cast<int64_t>(c0 + j) * ldc] = v[j];
+        if (c0 + j < ncols) C[r + static_cast<int64_t>(c0 + j) * ldc] = b[j] + v[j];
     }
   }
 }
@@ -533,9 +591,10 @@ __device__ __forceinline__ OperandBufs operand_bufs(unsigned char *raw, int npar
   return b;
 }
 
-// UNMQR(i,k,j) on tensor cores:  D2 = C (TMEM),  W^T = C^T V,  D2 += Z (-W),  C = D2.
-// Each GEMM is issued in two K halves: the MMAs of the first half run while the second
-// half of its split operand (C^T, then W) is being written.
+// UNMQR(i,k,j) on tensor cores:  W^T = C^T V (TMEM 0..127),  P = Z (-W) (TMEM 128..255),
+// C = C_old + P (C_old kept in TMEM 256..383, added in FP32).  Each product is issued in
+// two K halves: the MMAs of the first half run while the second half of its split operand
+// (C^T, then W) is being written.
 __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int k, int j) {
   const TileGeom geo{p.m, p.n, kMNB};
   const OperandBufs b = operand_bufs(raw, p.nparts);
@@ -549,7 +608,8 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   }
   float *C = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 128);
+  tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 256);
+  uint32_t acc = 0u;
   for (int h = 0; h < 2; ++h) {
     c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
     umma::fence_proxy_async();
@@ -559,7 +619,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
       const bool ok = h != 0 || wait_loads(p, ms);
       if (ok) {
         umma::fence_after();
-        issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 0, 4 * h, 4 * h + 4);
+        issue_product_half(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, acc, h);
         if (h == 1) umma::commit(ms.bar_mma);
       }
     }
@@ -574,6 +634,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     umma::bulk_g2s(b.Y, imgZ, b.bytes, ms.bar_ld);
   }
   phase_mark(ms.ph, 1);
+  acc = 0u;
   for (int h = 0; h < 2; ++h) {
     w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h);
     umma::fence_proxy_async();
@@ -583,7 +644,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
       const bool ok = !(h == 0 && !b.Zb) || wait_loads(p, ms);
       if (ok) {
         umma::fence_after();
-        issue_gemm(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
+        issue_product_half(ms.tmem + 128, bufZ, b.X, p.nparts, p.fmt, 1, acc, h);
         if (h == 1) umma::commit(ms.bar_mma);
       }
     }
@@ -595,13 +656,15 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   umma::fence_after();
   sync_all_tc();
   if (task_failed(ms)) return;
-  tmem_to_tile(C, p.lda, mb, ncols, ms.tmem + 128);
+  tile_plus_tmem(C, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 256);
   sync_all_tc();
   phase_mark(ms.ph, 3);
 }
 
-// TTMQR(i,piv,k,j):  D1 = C1^T (TMEM), D2 = C2, D3 = C1;  W^T = D1 + C2^T V2;
-// D2 += Z2 (-W);  D3 += T^T (-W);  C2 = D2, C1 = D3.  GEMM1 and GEMM2 are issued in two
+// TTMQR(i,piv,k,j) / TSMQR (V2 dense):  W^T = C1^T + C2^T V2 (the product fresh in TMEM
+// 0..127, C1^T added in FP32 while W's image is written);  P2 = Z2 (-W) (TMEM 128..255),
+// P1 = T^T (-W) (256..383);  C2 = C2_old + P2 (C2_old kept in TMEM 384..511), C1 = C1_old
+// + P1 (C1_old read again from global memory).  The first two products are issued in two
 // K halves like UNMQR's.
 __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int piv, int k,
                                 int j) {
@@ -617,31 +680,14 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   float *C1 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, piv, j);
   float *C2 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 128);
-  tile_rows_to_tmem(C1, p.lda, kMNB, ncols, ms.tmem, 256);
-  // D1 (lane c, column a) = C1(a, c): the identity part of the TT reflectors
-  {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = (warp & 3) * 32 + lane;
-    const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const float *col = C1 + static_cast<int64_t>(c) * p.lda;
-    for (int g = 0; g < 2; ++g) {
-      const int a0 = (warp >> 2) * 64 + g * 32;
-      float v[32];
-      if (c < ncols && p.vec4) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 q4 = __ldcg(reinterpret_cast<const float4 *>(col + a0) + u);
-          v[4 * u] = q4.x; v[4 * u + 1] = q4.y; v[4 * u + 2] = q4.z; v[4 * u + 3] = q4.w;
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < 32; ++u) v[u] = c < ncols ? __ldcg(col + a0 + u) : 0.f;
-      }
-      umma::tmem_st32(ms.tmem + lane_base + a0, v);
-    }
-    umma::tmem_wait_st();
+  // C1 is read twice more (transposed for W, then by the epilogue): pull it into L2 now
+  for (int c = threadIdx.x; c < ncols; c += kThreads) {
+    const char *col = reinterpret_cast<const char *>(C1 + static_cast<int64_t>(c) * p.lda);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(col));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(col + 256));
   }
+  tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 384);
+  uint32_t acc = 0u;
   for (int h = 0; h < 2; ++h) {
     c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
     umma::fence_proxy_async();
@@ -651,7 +697,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
       const bool ok = h != 0 || wait_loads(p, ms);
       if (ok) {
         umma::fence_after();
-        issue_gemm(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, 1, 4 * h, 4 * h + 4);
+        issue_product_half(ms.tmem, b.X, b.Y, p.nparts, p.fmt, 0, acc, h);
         if (h == 1) umma::commit(ms.bar_mma);
       }
     }
@@ -666,24 +712,25 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     umma::bulk_g2s(b.Y, b.Zb ? imgT : imgZ, b.bytes, ms.bar_ld);
   }
   phase_mark(ms.ph, 1);
+  acc = 0u;
   for (int h = 0; h < 2; ++h) {
-    w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h);
+    w_image_from_tmem(b.X, ms.tmem, p.fmt, p.nparts, h, C1, p.lda, ncols, p.vec4 != 0);
     umma::fence_proxy_async();
     sync_all_tc();
     if (task_failed(ms)) return;
     if (threadIdx.x == 0) {
       if (b.Zb) {
-        issue_gemm(ms.tmem + 128, b.Zb, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);  // C2 -= Z2 W
-        if (h == 1 && wait_loads(p, ms)) {                                             // T^T in Y
+        issue_product_half(ms.tmem + 128, b.Zb, b.X, p.nparts, p.fmt, 1, acc, h);  // P2 = -Z2 W
+        if (h == 1 && wait_loads(p, ms)) {                                           // T^T in Y
           umma::fence_after();
-          issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);                    // C1 -= T^T W
+          issue_product(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1);                 // P1 = -T^T W
           umma::commit(ms.bar_mma);
         }
       } else {
-        const bool ok = h != 0 || wait_loads(p, ms);                                   // Z2 in Y
+        const bool ok = h != 0 || wait_loads(p, ms);                                 // Z2 in Y
         if (ok) {
           umma::fence_after();
-          issue_gemm(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, 1, 4 * h, 4 * h + 4);
+          issue_product_half(ms.tmem + 128, b.Y, b.X, p.nparts, p.fmt, 1, acc, h);
           if (h == 1) umma::commit(ms.bar_mma);
         }
       }
@@ -703,7 +750,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
       umma::bulk_g2s(b.Y, imgT, b.bytes, ms.bar_ld);
       if (wait_loads(p, ms)) {
         umma::fence_after();
-        issue_gemm(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1, 1);
+        issue_product(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1);
         umma::commit(ms.bar_mma);
       }
     }
@@ -714,8 +761,8 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   umma::fence_after();
   sync_all_tc();
   if (task_failed(ms)) return;
-  tmem_to_tile(C2, p.lda, mb, ncols, ms.tmem + 128);
-  tmem_to_tile(C1, p.lda, kMNB, ncols, ms.tmem + 256);
+  tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 384);
+  tile_plus_tmem(C1, p.lda, kMNB, ncols, ms.tmem + 256, 0);
   sync_all_tc();
   phase_mark(ms.ph, 3);
 }
