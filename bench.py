@@ -48,7 +48,7 @@ BF16_FALLBACK = (1900.0, 1700.0)
 # durations with tuned panel weights), and the mean task durations (us) of the same
 # executor from a per-task trace on GB300 (32768 x 4096), the weights of the schedule bound.
 TENSOR_CLAIM_WEIGHTS = (265, 285, 20, 32, 320, 32, 66)
-# GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR, operand-image preparation (PlasmaTree-TS(32) trace)
+# GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR, operand-image preparation (PlasmaTree-TS trace)
 TENSOR_TASK_MEAN_US = (253, 286, 25, 29, 270, 29, 72)
 
 
@@ -67,7 +67,7 @@ def parse_args():
                     help="skip the FP64 factorization under the six trees and their TS forms "
                          "(32768x4096, nb 256, ib 32; about 20 s)")
     ap.add_argument("--tree", default="plasma-ts", help="tree of the mixed arm (a '-ts' suffix: its TS form)")
-    ap.add_argument("--bs", type=int, default=32, help="PlasmaTree domain size of the mixed arm")
+    ap.add_argument("--bs", type=int, default=16, help="PlasmaTree domain size of the mixed arm")
     ap.add_argument("--fp64-tree", default="plasma-ts")
     ap.add_argument("--fp64-bs", type=int, default=16)
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -77,7 +77,9 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched measurement (2048 FP32 matrices, one launch)")
     ap.add_argument("--batch-prec", default="fp32")
-    ap.add_argument("--batch-table", default="", help="JSON tuning table (autotune output) for the batch")
+    ap.add_argument("--batch-table", default="auto",
+                    help="tuning table of the batch: 'auto' (the library's autotuner, tqr_batch_autotune), "
+                         "'builtin' (the built-in size classes) or a JSON file with a 'table'")
     ap.add_argument("--batch-reps", type=int, default=5)
     ap.add_argument("--no-c5", action="store_true",
                     help="skip the square 16384^2 solve (cond 1e4, 64 right-hand sides; about 1 min)")
@@ -278,10 +280,17 @@ def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
     all_shapes = synthetic.ragged_batch_shapes(BATCH_COUNT, seed=synthetic.SEED_BASE + 4)
     shapes = [all_shapes[b] for b in replicas.shard(len(all_shapes), rank, world)]
     ms, ns = [m for m, _ in shapes], [n for _, n in shapes]
-    table = None
-    if args.batch_table:
+    table, tuning, tune_s = None, "built-in size classes", 0.0
+    if args.batch_table == "auto":
+        import time
+        t0 = time.perf_counter()
+        table = tqr.batch_autotune([m for m, _ in all_shapes], [n for _, n in all_shapes], prec)
+        tune_s = time.perf_counter() - t0
+        tuning = "autotuned (tqr_batch_autotune: per size class, device-timed)"
+    elif args.batch_table and args.batch_table != "builtin":
         with open(args.batch_table) as fh:
             table = json.load(fh)["table"]
+        tuning = "table " + args.batch_table
     params = tqr.batch_params(ms, ns, prec, table)
     db = DeviceBatch(shapes, replicas.replica_seed(synthetic.SEED_BASE + 4, rank),
                      dtype=torch.float64 if prec == "fp64" else torch.float32)
@@ -342,7 +351,8 @@ def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
         "metric": "nominal TFLOP/s of one batched launch", "value": achieved, "unit": "TFLOP/s",
         "ms_graph_launch": graph_ms, "ms_plain_launch": plain_ms, "ms_one_launch_per_matrix": per_ms,
         "speedup_vs_per_matrix": per_ms / graph_ms, "tasks": info["tasks"], "edges": info["edges"],
-        "resident_ctas": info["slots"], "tuning": "table " + args.batch_table if table else "built-in size classes",
+        "resident_ctas": info["slots"], "tuning": tuning, "tuning_seconds": tune_s,
+        "table": [[int(x) for x in row] for row in table] if table is not None else None,
         "ranks": world, "scaling": "strong (the 2048 matrices split across ranks)",
         "roofline": {"bound": "alu" if flops / peak > byts / (hbm_gbs * 1e-3) else "hbm",
                      "peak_tflops": peak, "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
@@ -450,6 +460,44 @@ def c5_measurement(args, n=16384, nrhs=64, cond=1e4):
         r["speedup_vs_fp64"] = fp64["ms"] / r["ms"]
         r["equal_error"] = r["backward_error"] <= 2 * fp64["backward_error"]
         out["mixed"].append(r)
+    return out
+
+
+# ---------------------------------------------------------------------------------
+# Double complex (the thesis's second precision): 8192 x 2048 N(0,1) complex matrix
+# ---------------------------------------------------------------------------------
+
+def z64_measurement(m=8192, n=2048, nb=128, ib=32, fp64_peak=None):
+    """Device time of the double-complex tiled QR (TQR_Z64) under Greedy and the TS form of
+    PlasmaTree(16); flops 4 x 2 n^2 (m - n/3) (a complex multiply-add is 8 real flops)."""
+    import torch
+
+    import paper_1303_3182_gb300 as tqr
+    import synthetic
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(synthetic.SEED_BASE + 6)
+    A0 = torch.randn(n, m, dtype=torch.complex128, device="cuda", generator=g).t()
+    work = torch.empty_like(A0.t()).t()
+    T = torch.empty(tqr.workspace_size(m, n, nb, ib, "z64"), dtype=torch.uint8, device="cuda")
+    flops = 4.0 * tqr.nominal_flops(m, n)
+    out = {"workload": f"double-complex tiled QR {m}x{n}, N(0,1) real and imaginary parts, seed 1303318206, "
+                       f"nb {nb}, ib {ib}", "complex_flops": flops, "trees": {}}
+    tqr.set_timing(True)
+    for tree, bs in (("greedy", 1), ("plasma-ts", 16)):
+        work.copy_(A0)
+        tqr.factor(work, nb, ib, tree, bs, "z64", T=T)  # plan and warm-up
+        work.copy_(A0)
+        tqr.kernel_time("factor", reset=True)
+        tqr.factor(work, nb, ib, tree, bs, "z64", T=T)
+        ms = tqr.kernel_time("factor", reset=True)[0]
+        r = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12}
+        if fp64_peak:
+            r["frac_of_fp64_peak"] = r["tflops"] / fp64_peak
+        out["trees"][f"{tree}" + (f"({bs})" if tree.startswith("plasma") else "")] = r
+    tqr.set_timing(False)
+    del A0, work, T
+    torch.cuda.empty_cache()
     return out
 
 
@@ -577,6 +625,7 @@ def main_gpu(args):
     if not args.no_batched:
         batched = batched_measurement(args, hbm_peak(), rank, world, dev)
     c5 = c5_measurement(args) if (not args.no_c5 and world == 1) else None
+    z64 = z64_measurement(fp64_peak=max(tqr.fp64_peak().values())) if world == 1 else None
     c1 = c1_measurement() if world == 1 else None
 
     # ---- end to end: host buffers, copies inside the timed region ----
@@ -650,6 +699,7 @@ def main_gpu(args):
         "batched": batched,
         "c5": c5,
         "c1": c1,
+        "z64": z64,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "schedule": schedule_bound(args, fac_avg),
         "clocks": clk.summary(),

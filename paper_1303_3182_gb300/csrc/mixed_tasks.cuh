@@ -364,12 +364,15 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
 // of K each), levels lvl_hi down to lvl_lo, level-major.  neg_b negates B.  acc: whether
 // the first MMA accumulates onto D; set to 1 afterwards.
 //
-// Order matters for accuracy: the tensor cores round the running FP32 sum of every MMA
-// towards zero relative to its magnitude, so a product added to a large accumulator loses
-// up to an ulp of that accumulator, and these losses share a sign.  The updates therefore
-// accumulate into a fresh D (the tile itself is added once, in FP32, by the epilogue) and
-// issue every small level over the whole K range before the level-0 products: of the
-// 8 nparts(nparts+1)/2 MMAs of a product only the 8 level-0 ones meet a full-size sum.
+// Order matters for accuracy.  Each MMA adds its products to the FP32 sum held in tensor
+// memory; a small part product added to a large sum keeps only the bits that sum can
+// hold.  Measured on GB300 with every part product added onto the TMEM copy of the tile,
+// the split-bf16 x6 factorization's backward error grew about linearly with n (1.2e-5 at
+// 4096 x 1024, against 1.0e-6 for FP32 SIMT updates), the sign of a bias.  The updates
+// therefore accumulate into a fresh D (the tile itself is added once, in FP32, by the
+// epilogue) and issue every small level over the whole K range before the level-0
+// products, so only the 8 level-0 MMAs of a product meet a full-size sum: the same
+// factorization's backward error is then 1.8e-6 and grows like the FP32 updates'.
 __device__ __forceinline__ void issue_levels(uint32_t d_tmem, const unsigned char *bufA, const unsigned char *bufB,
                                              int nparts, int fmt, int neg_b, uint32_t &acc, int ks0, int ks1,
                                              int lvl_lo, int lvl_hi) {
