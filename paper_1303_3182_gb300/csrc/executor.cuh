@@ -96,6 +96,7 @@ struct Smem {
   float *Wv;     // FP32 storage: [32 * kWvLd] W by rows (16-byte aligned), else null
   float *red;    // FP32 storage: [3 * 32 * 33] partial sums of V^T C, else null
   int ldv, ldw, ldt;
+  int ldp;       // leading dimension of P1 (ldt, or that of a resident pivot tile)
   uint64_t *ph;  // phase clock of the execution trace, or null
 };
 
@@ -118,6 +119,7 @@ __device__ Smem<S> carve(unsigned char *raw, int nb, int ib) {
   s.ldv = odd_ld(nb);
   s.ldw = ib + 1;
   s.ldt = ib + 1;
+  s.ldp = s.ldt;
   S *p = reinterpret_cast<S *>(raw);
   s.V = p;
   p += s.ldv * ib;
@@ -533,7 +535,7 @@ template <typename S, int kPanel, int kR>
 __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr bool kTT = kPanel != 0;  // TT and TS: the head is a row of R(piv)
-  auto head = [&](int c, int cc) -> S & { return kTT ? s.P1[c + cc * s.ldt] : s.V[c + cc * s.ldv]; };
+  auto head = [&](int c, int cc) -> S & { return kTT ? s.P1[c + cc * s.ldp] : s.V[c + cc * s.ldv]; };
   auto tlo = [&](int c) { return kTT ? 0 : c + 1; };
   auto thi = [&](int c) { return kPanel == 1 ? min(c0 + c + 1, mb) : rows; };
   auto col = [&](int c) -> S * { return s.V + c * s.ldv; };
@@ -890,7 +892,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
     load_block_mode(s.V, s.ldv, t2 + static_cast<int64_t>(c0) * p.lda, p.lda, rb, kb,
                     [c0](int r, int c) { return (kTS || r <= c0 + c) ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
     // P1 = upper part of the diagonal block of R(piv)
-    load_block_mode(s.P1, s.ldt, t1 + c0 + static_cast<int64_t>(c0) * p.lda, p.lda, kb, kb,
+    load_block_mode(s.P1, s.ldp, t1 + c0 + static_cast<int64_t>(c0) * p.lda, p.lda, kb, kb,
                     [](int r, int c) { return r <= c ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
     __syncthreads();
     panel_factor_dispatch<S, kTS ? 2 : 1>(s, kb, rb, c0, mb);
@@ -903,7 +905,7 @@ __device__ void task_ttqrt(const ExecParams &p, Smem<S> &s, int i, int piv, int 
         if (kTS || r <= c0 + c) t2[r + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.V[r + c * s.ldv]);
     for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
       const int c = idx / kb, r = idx - c * kb;
-      if (r <= c) t1[(c0 + r) + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.P1[r + c * s.ldt]);
+      if (r <= c) t1[(c0 + r) + static_cast<int64_t>(c0 + c) * p.lda] = static_cast<Real>(s.P1[r + c * s.ldp]);
     }
     store_t(Tt, ib, c0, width, s, kb);
     __syncthreads();
@@ -1151,13 +1153,22 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
     }
     switch (task.kind) {
       case kGeqrt:
-        task_geqrt<Real, S>(q, s, task.i, task.k);
+        if (kMixed)  // tensor-core path (FP32, nb 128): the tile stays in shared memory
+          task_geqrt_resident(q, smem_raw, s.ph, task.i, task.k);
+        else
+          task_geqrt<Real, S>(q, s, task.i, task.k);
         break;
       case kTtqrt:
-        task_ttqrt<Real, S, false>(q, s, task.i, task.piv, task.k);
+        if (kMixed)
+          task_pairqrt_resident<false>(q, smem_raw, s.ph, task.i, task.piv, task.k);
+        else
+          task_ttqrt<Real, S, false>(q, s, task.i, task.piv, task.k);
         break;
       case kTsqrt:
-        task_ttqrt<Real, S, true>(q, s, task.i, task.piv, task.k);
+        if (kMixed)
+          task_pairqrt_resident<true>(q, smem_raw, s.ph, task.i, task.piv, task.k);
+        else
+          task_ttqrt<Real, S, true>(q, s, task.i, task.piv, task.k);
         break;
       case kPrepG:  // tensor-core graphs only: the operand images of GEQRT(i,k)
         if (kMixed) prep_geqrt_ops(q, smem_raw, task.i, task.k);

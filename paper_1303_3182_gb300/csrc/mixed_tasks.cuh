@@ -358,6 +358,159 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------------
+// Panel tasks of the tensor-core path with the tile resident in shared memory: the tile
+// (and, for TTQRT / TSQRT, the pivot tile's upper triangle) is read once, every ib-block
+// is factored and applied to the later columns in shared memory, and the result is
+// written back once - the in-tile trailing updates make no round trips to global memory.
+// The arithmetic is that of task_geqrt / task_ttqrt (the same SIMT panel, Gram, T and
+// block-reflector code), so the results are bit for bit those of the chunked tasks.
+struct ResBufs {
+  float *Ct, *Rp, *save;  // resident tile, resident pivot triangle, R block of a GEQRT
+  Smem<float> s;
+};
+
+constexpr size_t kResidentFloats = 2 * static_cast<size_t>(kMLD) * kMNB + 4 * 33 * 32 + 2 * 32 + 4 + 32 * kWvLd +
+                                   3 * 32 * 33;
+static_assert(kResidentFloats * sizeof(float) <= 3 * static_cast<size_t>(kMNB) * kMLD * sizeof(float) + 1024,
+              "the resident panel fits the tensor-core executor's shared memory");
+
+__device__ ResBufs res_carve(unsigned char *raw, int ib, uint64_t *ph) {
+  ResBufs r;
+  float *p = reinterpret_cast<float *>(raw);
+  r.Ct = p;
+  p += kMLD * kMNB;
+  r.Rp = p;
+  p += kMLD * kMNB;
+  Smem<float> &s = r.s;
+  s.ldv = kMLD;
+  s.ldw = ib + 1;
+  s.ldt = ib + 1;
+  s.ldp = kMLD;
+  s.W = p;
+  p += 33 * 32;
+  s.T = p;
+  p += 33 * 32;
+  s.G = p;
+  p += 33 * 32;
+  s.tau_s = p;
+  p += 32;
+  s.scal_s = p;
+  p += 32;
+  r.save = p;
+  p += 33 * 32;
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~static_cast<uintptr_t>(15);
+  s.Wv = reinterpret_cast<float *>(a);
+  s.red = s.Wv + 32 * kWvLd;
+  s.V = r.Ct;
+  s.C = s.C1 = nullptr;
+  s.P1 = r.Rp;
+  s.ph = ph;
+  return r;
+}
+
+// GEQRT(i,k) with the tile resident.
+__device__ void task_geqrt_resident(const ExecParams &p, unsigned char *raw, uint64_t *ph, int i, int k) {
+  const TileGeom geo{p.m, p.n, kMNB};
+  const int ib = p.ib;
+  ResBufs rb = res_carve(raw, ib, ph);
+  Smem<float> &s = rb.s;
+  float *tile = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, k);
+  float *Tg = t_ptr(static_cast<float *>(p.T), p.P, ib, kMNB, i, k, 0);
+  const int mb = geo.rows(i), ncol = geo.cols(k), K = min(mb, ncol);
+  load_block(rb.Ct, kMLD, tile, p.lda, mb, ncol);
+  __syncthreads();
+  for (int c0 = 0; c0 < kMNB; c0 += ib) {
+    const int width = min(ib, kMNB - c0), kb = max(0, min(ib, K - c0));
+    if (kb == 0) {
+      store_t(Tg, ib, c0, width, s, 0);
+      continue;
+    }
+    const int rows = mb - c0;
+    s.V = rb.Ct + c0 + c0 * kMLD;
+    panel_factor_dispatch<float, 0>(s, kb, rows, c0, mb);
+    phase_mark(s.ph, 0);
+    // the explicit reflector block (unit diagonal, zeros above) for the Gram matrix and the
+    // block reflector; the R block it covers is kept aside and put back afterwards
+    for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
+      const int c = idx / kb, r = idx - c * kb;
+      if (r <= c) {
+        rb.save[r + c * 33] = s.V[r + c * kMLD];
+        s.V[r + c * kMLD] = r == c ? 1.f : 0.f;
+      }
+    }
+    __syncthreads();
+    panel_gram(s, kb, rows);
+    build_t(s, kb);
+    store_t(Tg, ib, c0, width, s, kb);
+    __syncthreads();
+    phase_mark(s.ph, 1);
+    for (int cs = c0 + kb; cs < ncol; cs += 32) {
+      const int w = min(32, ncol - cs);
+      apply_block(rb.Ct + c0 + cs * kMLD, kMLD, rows, static_cast<float *>(nullptr), 0, w, s.V, kMLD, s.T, s.ldt, kb,
+                  s.W, s.ldw, false, s.Wv, s.red);
+    }
+    for (int idx = threadIdx.x; idx < kb * kb; idx += kThreads) {
+      const int c = idx / kb, r = idx - c * kb;
+      if (r <= c) s.V[r + c * kMLD] = rb.save[r + c * 33];
+    }
+    __syncthreads();
+    phase_mark(s.ph, 2);
+  }
+  store_block(tile, p.lda, rb.Ct, kMLD, mb, ncol);
+  __syncthreads();
+}
+
+// TTQRT(i,piv,k) (ts false) / TSQRT(i,piv,k) (ts true) with both tiles resident: the
+// upper triangle of (piv,k) and the upper triangle (TT) or the whole (TS) of (i,k).
+template <bool kTS>
+__device__ void task_pairqrt_resident(const ExecParams &p, unsigned char *raw, uint64_t *ph, int i, int piv, int k) {
+  const TileGeom geo{p.m, p.n, kMNB};
+  const int ib = p.ib;
+  ResBufs rb = res_carve(raw, ib, ph);
+  Smem<float> &s = rb.s;
+  float *A = static_cast<float *>(p.A);
+  float *t1 = tile_ptr(A, p.lda, kMNB, piv, k), *t2 = tile_ptr(A, p.lda, kMNB, i, k);
+  float *Tt = t_ptr(static_cast<float *>(p.T), p.P, ib, kMNB, i, k, 1);
+  const int mb = geo.rows(i), K = geo.cols(k);
+  auto upper = [](int r, int c) { return r <= c ? static_cast<int>(kLoad) : static_cast<int>(kZero); };
+  load_block_mode(rb.Rp, kMLD, t1, p.lda, K, K, upper);
+  load_block_mode(rb.Ct, kMLD, t2, p.lda, mb, K,
+                  [](int r, int c) { return (kTS || r <= c) ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
+  __syncthreads();
+  for (int c0 = 0; c0 < kMNB; c0 += ib) {
+    const int width = min(ib, kMNB - c0), kb = max(0, min(ib, K - c0));
+    if (kb == 0) {
+      store_t(Tt, ib, c0, width, s, 0);
+      continue;
+    }
+    const int rbk = kTS ? mb : min(c0 + kb, mb);
+    s.V = rb.Ct + c0 * kMLD;
+    s.P1 = rb.Rp + c0 + c0 * kMLD;
+    panel_factor_dispatch<float, kTS ? 2 : 1>(s, kb, rbk, c0, mb);
+    phase_mark(s.ph, 0);
+    panel_gram(s, kb, rbk);
+    build_t(s, kb);
+    store_t(Tt, ib, c0, width, s, kb);
+    __syncthreads();
+    phase_mark(s.ph, 1);
+    for (int cs = c0 + kb; cs < K; cs += 32) {
+      const int w = min(32, K - cs);
+      apply_block(rb.Ct + cs * kMLD, kMLD, rbk, rb.Rp + c0 + cs * kMLD, kMLD, w, s.V, kMLD, s.T, s.ldt, kb, s.W,
+                  s.ldw, false, s.Wv, s.red);
+    }
+    phase_mark(s.ph, 2);
+  }
+  // write back what the kernel owns: the triangles (TT) or the triangle and the whole tile (TS)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < K; c += kWarps) {
+    for (int r = lane; r < mb; r += 32)
+      if (kTS || r <= c) t2[r + static_cast<int64_t>(c) * p.lda] = rb.Ct[r + c * kMLD];
+    for (int r = lane; r <= c; r += 32) t1[r + static_cast<int64_t>(c) * p.lda] = rb.Rp[r + c * kMLD];
+  }
+  __syncthreads();
+}
+
 // D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) op(B)^T for split operands: the part
 // products A_qa B_qb of one "level" s = qa + qb (s < nparts: hi*hi is level 0; hi*lo and
 // lo*hi level 1; hi*lo2, mid*mid, lo2*hi level 2) for the k-steps ks0 .. ks1-1 (16 columns

@@ -191,3 +191,23 @@ def test_mixed_first_column_reflectors_elementwise(tree, prec):
             if ref is not None:
                 worst = max(worst, np.max(np.abs(tb[0, i, which].T - ref)))
     assert worst <= 4 * tol, worst
+
+
+@pytest.mark.parametrize("tree", ["greedy", "plasma-ts"])
+def test_resident_panels_equal_the_chunked_simt_panels(tree):
+    """The tensor-core path factors its panels with the tile resident in shared memory; the
+    FP32 SIMT path (same nb, ib) streams the trailing columns through global memory in
+    chunks.  Both run the same panel, Gram, T and block-reflector arithmetic, and no
+    tensor-core product reaches tile column 0, so tile column 0 and its T factors agree bit
+    for bit."""
+    m, n, ib = 1024, 384, 32
+    A = synthetic.gaussian(m, n, seed=41).astype(np.float32).astype(np.float64)
+    Ad, T = factor_mixed(A, "bf16x6", tree, ib)
+    As = to_dev(A, torch.float32)
+    Ts = torch.zeros(tqr.workspace_size(m, n, 128, ib, "fp32"), dtype=torch.uint8, device="cuda")
+    tqr.factor(As, 128, ib, tree, 2, "fp32", T=Ts)
+    torch.cuda.synchronize()
+    assert torch.equal(Ad[:, :128], As[:, :128])
+    p = m // 128
+    nT = 2 * p * 1 * ib * 128 * 4  # the T slots of tile column 0
+    assert torch.equal(T[:nT], Ts[:nT])
