@@ -37,10 +37,10 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BATCH_COUNT = 2048
 # DRAM bytes (read + write) per nominal flop of the two executors, from one ncu capture
 # each of the unchanged kernels on smaller inputs of the same kind (the tensor-core
-# executor on a 24576 x 2048 matrix: 14.656 GB for 2.004e11 nominal flops, traffic
-# growing with the number of tile updates as the flops do; the batched FP32 executor on
-# the first 256 matrices of the batch: 1.328 GB for 4.907e10 flops).
-MIXED_TRAFFIC_PER_FLOP = 14.656e9 / 2.004e11
+# executor, PlasmaTree-TS(16), on a 24576 x 2048 matrix: 6.773 GB for 2.004e11 nominal
+# flops, traffic growing with the number of tile updates as the flops do; the batched FP32
+# executor on the first 256 matrices of the batch: 1.328 GB for 4.907e10 flops).
+MIXED_TRAFFIC_PER_FLOP = 6.773e9 / 2.004e11
 BATCH_TRAFFIC_PER_FLOP = 1.328e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
 # Kernel weights of the library's default claim order for the tensor-core precisions
@@ -672,7 +672,8 @@ def main_gpu(args):
         "roofline": {"kernel": "executor_kernel<float,float,1> (mixed tiled-QR task graph, one launch per step)",
                      "bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                      "frac": achieved / bf16_sust, "traffic": flops * MIXED_TRAFFIC_PER_FLOP,
-                     "traffic_note": "bytes per launch, ncu capture at 24576x2048 scaled by nominal flops",
+                     "traffic_note": "bytes per launch, ncu capture at 24576x2048 (PlasmaTree-TS(16)) scaled "
+                                     "by nominal flops",
                      "algorithmic_bytes": tile_task_bytes(args),
                      "algorithmic_bytes_note": "tile-task traffic: C tiles read and written by every task that "
                                                "updates them, split operand images written once and read by "
