@@ -120,12 +120,13 @@ int tqr_elimlist(int p, int q, int tree, int bs, int32_t *list, int64_t *len,
 int tqr_schedule(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
                  int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
 
-/* tqr_schedule with seven weights: the kernels GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR
- * (each >= 1; the TS kernels weighed on their own, e.g. by measured task durations) and
- * the operand-image preparation tasks of the tensor-core precisions (>= 1: the graph the
- * tensor-core executor runs, with one preparation task after every GEQRT, TTQRT and
- * TSQRT; 0: the graph without them).  weights must not be NULL (-6); other arguments and
- * errors as tqr_schedule. */
+/* tqr_schedule with nine weights: the kernels GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR
+ * (each >= 1; the TS kernels weighed on their own, e.g. by measured task durations); the
+ * operand-image preparation tasks of the tensor-core precisions (>= 1: one preparation
+ * task after every GEQRT, TTQRT and TSQRT; 0: none); and the 32-column block tasks of a
+ * split TTQRT and TSQRT (both >= 1, with preparation tasks: each TT / TS panel as four
+ * block tasks, the graph the tensor-core executor runs for ib dividing 32; 0: unsplit).
+ * weights must not be NULL (-6); other arguments and errors as tqr_schedule. */
 int tqr_schedule_ts(int p, int q, int tree, int bs, int nproc, const int64_t *weights,
                     int64_t *makespan, int64_t *alap_bound, int64_t *lost_area);
 
@@ -403,9 +404,10 @@ void tqr_finalize(void);               /* free every cached plan and cached scra
  * tqr_plan_stats: task and edge counts of the task graph the executor runs for a
  *   factorization of the given shape/tree: out[0..5] = #GEQRT, #TTQRT, #UNMQR, #TTMQR,
  *   #edges, critical path in units (same weights as tqr_elimlist).
- * tqr_debug_drop_edge: when set to e >= 0, the next plan built omits the release of
- *   its e-th dependency edge, so that a wait can never finish; used to check that the
- *   kernel returns TQR_ETIMEOUT instead of hanging.  -1 (default) disables it.
+ * tqr_debug_drop_edge: when set to e >= 0, the next plan built (a factorization plan or a
+ *   batch plan) omits the release of its e-th dependency edge, so that a wait can never
+ *   finish; used to check that the kernel returns TQR_ETIMEOUT instead of hanging.  -1
+ *   (default) disables it.
  * tqr_debug_claim_order: the executor (claim) order of the factorization task graph of a
  *   p x q tile matrix, built as a plan is: mode 0 = earliest start on unbounded
  *   processors, mode 1 = start order of the CP-method list schedule on nproc processors

@@ -175,10 +175,11 @@ def schedule(p: int, q: int, tree="greedy", bs: int = 1, nproc: int = 1, weights
     """Bounded-processor schedule of the factorization task graph on nproc processors:
     (CP-method makespan, ALAP Derived bound, lost area); weights are four kernel weights
     (GEQRT, TTQRT, UNMQR, TTMQR; None = 4, 2, 6, 6; TS kernels 3 x TTQRT, 2 x TTMQR), six
-    (..., TSQRT, TSMQR) or seven (..., operand-image preparation: the tensor-core graph)."""
+    (..., TSQRT, TSMQR), seven (..., operand-image preparation: the tensor-core graph) or
+    nine (..., TTQRT block, TSQRT block: the tensor-core graph with split panels)."""
     ms, bound, la = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
-    if weights is not None and len(weights) in (6, 7):
-        weights = list(weights) + [0] * (7 - len(weights))
+    if weights is not None and len(weights) in (6, 7, 9):
+        weights = list(weights) + [0] * (9 - len(weights))
         fn, name = lib().tqr_schedule_ts, "tqr_schedule_ts"
     else:
         fn, name = lib().tqr_schedule, "tqr_schedule"

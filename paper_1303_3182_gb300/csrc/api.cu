@@ -22,26 +22,28 @@ std::mutex g_mu;
 int64_t g_drop_edge = -1;  // test hook, see tqr_debug_drop_edge
 // Claim order of factorization plans (tqr_set_claim_order): mode 0 or 1 as set, or
 // the automatic default (mode 2): the bounded-processor CP-method order with built-in
-// kernel weights (GEQRT, TTQRT, UNMQR, TTMQR) for the tensor-core precisions and FP64,
-// the unbounded-processor order for FP32.  The weights come from task durations in
-// microseconds measured on GB300:
-//   tensor cores (nb 128, split-bf16 x6): about 295, 305-323, 20, 32 - panels cost 10 to
-//   16 times an update there, while the thesis's weights give them less than an update;
-//   the panel weights were tuned on the 32768 x 4096 factorization (330, 360: 76.3 ms;
-//   the plain means 293/304/19/31 gave 78.5 ms, other TTQRT/GEQRT ratios up to 80.9 ms);
-//   FP64 (nb 256): 5146, 4249, 6394, 6369 - with them FlatTree's 32768 x 4096
-//   factorization takes 1488 ms instead of 1635 ms with the unbounded order (its ALAP
-//   Derived bound is 1468 ms), Greedy's 1448 ms against 1443 ms (bound 1424 ms).
+// kernel weights for the tensor-core precisions and FP64, the unbounded-processor order
+// for FP32.  The weights are task durations in microseconds measured on GB300:
+//   tensor cores (nb 128, split-bf16 x6, the graph with preparation tasks): GEQRT ~236,
+//   TTQRT ~239, UNMQR ~25, TTMQR ~28, TSQRT ~267, TSMQR ~28, preparation ~71 (panel
+//   weights taken somewhat above their means, as a sweep on the 32768 x 4096 Greedy
+//   factorization preferred), split-panel blocks about a quarter of a panel plus the
+//   block's own tile loads - panels cost ten updates there, while the thesis's weights
+//   give them less than an update;
+//   FP64 (nb 256): 5146, 4249, 6394, 6369, TSQRT 6767, TSMQR 9457 - with them FlatTree's
+//   32768 x 4096 factorization takes 1488 ms instead of 1635 ms with the unbounded order
+//   (its ALAP Derived bound is 1468 ms).
 int g_order_mode = 2;
-int64_t g_order_w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr, 1, 1};
+int64_t g_order_w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr,
+                                 1, 1, 1, 2};
 int g_order_gen = 0;        // bumped by every tqr_set_claim_order call
 // per TaskKind: GEQRT, TTQRT, UNMQR, TTMQR, (apply-Q kinds, unused), TSQRT, TSMQR.  The
 // TS kernels' weights are measured task means on GB300 as well: tensor cores 340-375 /
 // 29-30 us (TSQRT taken like the tuned panel weights, a little above its mean), FP64
 // 6767 / 9457 us (TSMQR 1.37 times faster per flop than UNMQR + TTMQR, as the thesis
 // found the TS kernels faster on its CPUs).
-constexpr int64_t kTensorOrderWeights[kNumKinds] = {265, 285, 20, 32, 20, 32, 320, 32, 32, 66, 66};
-constexpr int64_t kFp64OrderWeights[kNumKinds] = {5146, 4249, 6394, 6369, 6394, 6369, 6767, 9457, 9457, 1, 1};
+constexpr int64_t kTensorOrderWeights[kNumKinds] = {265, 285, 20, 32, 20, 32, 320, 32, 32, 66, 66, 80, 85};
+constexpr int64_t kFp64OrderWeights[kNumKinds] = {5146, 4249, 6394, 6369, 6394, 6369, 6767, 9457, 9457, 1, 1, 1, 1};
 
 // Per-kind weights from the four TT-kernel weights of the ABI (GEQRT, TTQRT, UNMQR,
 // TTMQR): the TS kernels take the thesis's ratios to their TT counterparts, TSQRT = 3
@@ -54,6 +56,9 @@ void expand_weights(const int64_t w4[4], int64_t out[kNumKinds]) {
   out[kTsqrt] = 3 * w4[1];
   out[kTsmqr] = out[kTsmqrB] = 2 * w4[3];
   out[kPrepG] = out[kPrepT] = 1;  // operand images (tensor-core precisions): short
+  // a quarter of the TT / TS panel per 32-column block task
+  out[kTtqrtS] = std::max<int64_t>(1, out[kTtqrt] / kPanelSplits);
+  out[kTsqrtS] = std::max<int64_t>(1, out[kTsqrt] / kPanelSplits);
 }
 
 bool valid_tree(int tree) {
@@ -173,9 +178,10 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 // Returns the cached plan for (kind, P, Q, tree, bs) on the current device.
 // order: the claim order of a factorization plan (kind 0), with spec.nproc the
 // executor's resident CTAs; ignored for the apply-Q plans.
-// prep: the tensor-core form of a factorization graph (operand-preparation tasks).
+// prep: the tensor-core form of a factorization graph (operand-preparation tasks); split:
+// with its TT / TS panels as 32-column block tasks.
 int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSpec *order = nullptr,
-             bool prep = false) {
+             bool prep = false, bool split = false) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -188,7 +194,7 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   // the order's identity (spec.id: user weights carry the setting's generation, each
   // built-in weight set a negative key of its own) is part of the key; a plan built with
   // the test hook is never reused: it gets a key of its own
-  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : (kind == 0 && prep ? 3 : kind), P, Q, tree,
+  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : (kind == 0 && prep ? (split ? 4 : 3) : kind), P, Q, tree,
                     tree_base(tree) == TQR_PLASMA ? bs : 0, bounded ? spec.id : 0, bounded ? spec.nproc : 0};
   auto it = g_plans.find(key);
   if (it != g_plans.end()) {
@@ -200,7 +206,7 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   auto plan = std::make_unique<Plan>();
   plan->device = dev;
   if (kind == 0)
-    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree), prep);
+    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree), prep, prep && split);
   else
     build_applyq_graph(P, Q, elims, kind == 2, plan->g, tree_ts(tree));
   if (drop >= 0) g_drop_edge = -1;  // the test hook applies to one plan only
@@ -293,6 +299,13 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+int64_t take_debug_drop_edge() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int64_t e = g_drop_edge;
+  g_drop_edge = -1;
+  return e;
+}
+
 bool is_tensor_prec(int prec) {
   return prec == TQR_BF16 || prec == TQR_FP16 || prec == TQR_BF16X3 || prec == TQR_BF16X6;
 }
@@ -384,15 +397,16 @@ void weights6(const int64_t w6[6], int64_t out[kNumKinds]) {
   expand_weights(w6, out);
   out[kTsqrt] = w6[4];
   out[kTsmqr] = out[kTsmqrB] = w6[5];
+  out[kTsqrtS] = std::max<int64_t>(1, w6[4] / kPanelSplits);
 }
 
 int schedule_impl(int p, int q, int tree, int bs, int nproc, const int64_t w[kNumKinds], int64_t *makespan,
-                  int64_t *alap_bound, int64_t *lost_area, bool prep = false) {
+                  int64_t *alap_bound, int64_t *lost_area, bool prep = false, bool split = false) {
   try {
     std::vector<Elim> elims;
     elimination_list(p, q, tree_base(tree), bs, elims);
     GraphBuilder b(p * q * kRegionsPerTile);
-    add_factor_program(b, p, q, elims, tree_ts(tree), prep);
+    add_factor_program(b, p, q, elims, tree_ts(tree), prep, split);
     const int n = static_cast<int>(b.tasks.size());
     std::vector<std::vector<int32_t>> succ(n);
     std::vector<int32_t> npred(n);
@@ -456,11 +470,17 @@ int tqr_schedule_ts(int p, int q, int tree, int bs, int nproc, const int64_t *we
   if (!weights) return -6;
   for (int c = 0; c < 6; ++c)
     if (weights[c] < 1) return -6;
-  if (weights[6] < 0) return -6;
+  for (int c = 6; c < 9; ++c)
+    if (weights[c] < 0) return -6;
+  const bool prep = weights[6] > 0, split = prep && weights[7] > 0 && weights[8] > 0;
   int64_t w[kNumKinds];
   weights6(weights, w);
   w[kPrepG] = w[kPrepT] = weights[6];
-  return schedule_impl(p, q, tree, bs, nproc, w, makespan, alap_bound, lost_area, weights[6] > 0);
+  if (split) {
+    w[kTtqrtS] = weights[7];
+    w[kTsqrtS] = weights[8];
+  }
+  return schedule_impl(p, q, tree, bs, nproc, w, makespan, alap_bound, lost_area, prep, split);
 }
 
 int tqr_set_claim_order(int mode, const int64_t *weights) {
@@ -518,7 +538,11 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
     }
     if (order.mode == 1)
       order.nproc = prec == TQR_Z64 ? zexec_slots(nb, ib) : executor_slots(dbl, is_tensor_prec(prec), nb, ib);
-    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order, is_tensor_prec(prec))) != 0) return rc;
+    // tensor-core graphs split their TT / TS panels into 32-column block tasks when the
+    // inner block divides 32
+    const bool tensor = is_tensor_prec(prec);
+    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order, tensor, tensor && kPanelSplitCols % ib == 0)) != 0)
+      return rc;
     ExecParams prm{};
     prm.A = A;
     prm.lda = lda;

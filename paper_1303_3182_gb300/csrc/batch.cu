@@ -137,13 +137,14 @@ int merge_batch(int nbatch, const int64_t *m, const int64_t *n, const int *prm, 
   for (int b = 0; b < nbatch; ++b) {
     const int *o = prm + 4 * b;
     const int P = static_cast<int>(cdiv(m[b], o[0])), Q = static_cast<int>(cdiv(n[b], o[0]));
-    const Key key{P, Q, o[2], tree_base(o[2]) == TQR_PLASMA ? o[3] : 0};
+    const bool tensor = is_tensor_prec(prec), split = tensor && kPanelSplitCols % o[1] == 0;
+    const Key key{P, Q, o[2] | (split ? 1 << 20 : 0), tree_base(o[2]) == TQR_PLASMA ? o[3] : 0};
     auto it = graphs.find(key);
     if (it == graphs.end()) {
       std::vector<Elim> elims;
       if (!elimination_list(P, Q, tree_base(o[2]), o[3], elims)) return fail(-5, "elimination list");
       auto g = std::make_unique<Graph>();
-      build_factor_graph(P, Q, elims, *g, -1, nullptr, tree_ts(o[2]), is_tensor_prec(prec));
+      build_factor_graph(P, Q, elims, *g, -1, nullptr, tree_ts(o[2]), tensor, split);
       it = graphs.emplace(key, std::move(g)).first;
     }
     gof[b] = it->second.get();
@@ -331,6 +332,21 @@ int tqr_batch_plan_create(int nbatch, const int64_t *m, const int64_t *n, void *
     Merged mg;
     const int rc = merge_batch(nbatch, m, n, prm.data(), pl->slots, prec, mg);
     if (rc) return rc;
+    // test hook (tqr_debug_drop_edge): leave out the release of one merged dependency edge,
+    // so that its successor's wait can only end by the wait limit
+    const int64_t drop = take_debug_drop_edge();
+    if (drop >= 0 && drop < static_cast<int64_t>(mg.succ_idx.size())) {
+      const int64_t N0 = static_cast<int64_t>(mg.tasks.size());
+      std::vector<int32_t> ptr(N0 + 1, 0), idx;
+      idx.reserve(mg.succ_idx.size());
+      for (int64_t r = 0; r < N0; ++r) {
+        for (int32_t x = mg.succ_ptr[r]; x < mg.succ_ptr[r + 1]; ++x)
+          if (x != drop) idx.push_back(mg.succ_idx[x]);
+        ptr[r + 1] = static_cast<int32_t>(idx.size());
+      }
+      mg.succ_ptr.swap(ptr);
+      mg.succ_idx.swap(idx);
+    }
     pl->flops = mg.flops;
     const int64_t N = static_cast<int64_t>(mg.tasks.size());
     const int64_t E = static_cast<int64_t>(mg.succ_idx.size());

@@ -1170,6 +1170,12 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
         else
           task_ttqrt<Real, S, true>(q, s, task.i, task.piv, task.k);
         break;
+      case kTtqrtS:  // tensor-core graphs only: block j of a split TTQRT / TSQRT
+        if (kMixed) task_pairqrt_split<false>(q, smem_raw, s.ph, task.i, task.piv, task.k, task.j);
+        break;
+      case kTsqrtS:
+        if (kMixed) task_pairqrt_split<true>(q, smem_raw, s.ph, task.i, task.piv, task.k, task.j);
+        break;
       case kPrepG:  // tensor-core graphs only: the operand images of GEQRT(i,k)
         if (kMixed) prep_geqrt_ops(q, smem_raw, task.i, task.k);
         phase_mark(s.ph, 3);

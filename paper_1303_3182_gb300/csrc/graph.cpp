@@ -49,6 +49,23 @@ int GraphBuilder::add(const Task &t, int w, const int *reads, int nr, const int 
   return id;
 }
 
+namespace {
+// Region id lists of the task kinds: the whole upper part of a tile is its row blocks.
+struct Regions {
+  int r[16];
+  int n = 0;
+  void add(int x) { r[n++] = x; }
+  void L(int q, int i, int j) { add(region_L(q, i, j)); }
+  void U(int q, int i, int j) {
+    for (int bb = 0; bb < kPanelSplits; ++bb) add(region_Ub(q, i, j, bb));
+  }
+  void tile(int q, int i, int j) {
+    L(q, i, j);
+    U(q, i, j);
+  }
+};
+}  // namespace
+
 std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square, bool prep) {
   std::vector<int> geqrt_ids;
   for (int i = k; i < p; ++i) {
@@ -56,8 +73,9 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const cha
       geqrt_ids.push_back(-1);
       continue;
     }
-    const int rw[2] = {region_L(q, i, k), region_U(q, i, k)};
-    geqrt_ids.push_back(b.add(Task{kGeqrt, i, -1, (int16_t)k, -1}, kWGeqrt, nullptr, 0, rw, 2));
+    Regions w;
+    w.tile(q, i, k);
+    geqrt_ids.push_back(b.add(Task{kGeqrt, i, -1, (int16_t)k, -1}, kWGeqrt, nullptr, 0, w.r, w.n));
     if (prep) {
       const int rd[1] = {region_L(q, i, k)};
       const int wr[1] = {region_ops(q, i, k, 0)};
@@ -65,36 +83,63 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const cha
     }
     for (int j = k + 1; j < q; ++j) {
       const int rd[2] = {region_L(q, i, k), region_ops(q, i, k, 0)};
-      const int wr[2] = {region_L(q, i, j), region_U(q, i, j)};
-      b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)j}, kWUnmqr, rd, prep ? 2 : 1, wr, 2);
+      Regions wj;
+      wj.tile(q, i, j);
+      b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)j}, kWUnmqr, rd, prep ? 2 : 1, wj.r, wj.n);
     }
   }
   return geqrt_ids;
 }
 
-void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square, bool prep) {
+void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square, bool prep,
+                    bool split) {
   for (const Elim &e : col) {
     const bool ts = square && square[e.i];
-    if (ts) {
-      // TSQRT overwrites the whole square tile (i,k) with its reflectors; TSMQR reads it
-      const int wr3[3] = {region_U(q, e.piv, k), region_L(q, e.i, k), region_U(q, e.i, k)};
-      b.add(Task{kTsqrt, e.i, e.piv, (int16_t)k, -1}, kWTsqrt, nullptr, 0, wr3, 3);
+    if (split) {
+      // block bb writes row block bb of the pivot's R and the zeroed tile (its later
+      // columns): blocks of one elimination run in order, and block bb of the next
+      // elimination on the same pivot waits only for block bb of this one
+      for (int bb = 0; bb < kPanelSplits; ++bb) {
+        Regions w;
+        w.add(region_Ub(q, e.piv, k, bb));
+        if (ts)
+          w.tile(q, e.i, k);
+        else
+          w.U(q, e.i, k);
+        b.add(Task{ts ? kTsqrtS : kTtqrtS, e.i, e.piv, (int16_t)k, (int16_t)bb}, ts ? 2 : 1, nullptr, 0, w.r, w.n);
+      }
     } else {
-      const int wr[2] = {region_U(q, e.piv, k), region_U(q, e.i, k)};
-      b.add(Task{kTtqrt, e.i, e.piv, (int16_t)k, -1}, kWTtqrt, nullptr, 0, wr, 2);
+      // TSQRT overwrites the whole square tile (i,k) with its reflectors; TTQRT its upper part
+      Regions w;
+      w.U(q, e.piv, k);
+      if (ts)
+        w.tile(q, e.i, k);
+      else
+        w.U(q, e.i, k);
+      b.add(Task{ts ? kTsqrt : kTtqrt, e.i, e.piv, (int16_t)k, -1}, ts ? kWTsqrt : kWTtqrt, nullptr, 0, w.r, w.n);
     }
     if (prep) {
-      const int rd[2] = {region_U(q, e.i, k), region_L(q, e.i, k)};
+      Regions rd;
+      if (ts)
+        rd.tile(q, e.i, k);
+      else
+        rd.U(q, e.i, k);
       const int wr[1] = {region_ops(q, e.i, k, 1)};
       // j carries the kernel: 1 = TSQRT (dense reflector tile), 0 = TTQRT
-      b.add(Task{kPrepT, e.i, e.piv, (int16_t)k, (int16_t)(ts ? 1 : 0)}, 0, rd, ts ? 2 : 1, wr, 1);
+      b.add(Task{kPrepT, e.i, e.piv, (int16_t)k, (int16_t)(ts ? 1 : 0)}, 0, rd.r, rd.n, wr, 1);
     }
     for (int j = k + 1; j < q; ++j) {
-      const int rd[3] = {region_U(q, e.i, k), region_ops(q, e.i, k, 1), region_L(q, e.i, k)};
-      const int w4[4] = {region_L(q, e.piv, j), region_U(q, e.piv, j), region_L(q, e.i, j),
-                         region_U(q, e.i, j)};
-      b.add(Task{ts ? kTsmqr : kTtmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, ts ? kWTsmqr : kWTtmqr, rd,
-            (prep ? 2 : 1) + (ts ? 1 : 0), w4, 4);
+      Regions rd;
+      if (ts)
+        rd.tile(q, e.i, k);
+      else
+        rd.U(q, e.i, k);
+      if (prep) rd.add(region_ops(q, e.i, k, 1));
+      Regions w4;
+      w4.tile(q, e.piv, j);
+      w4.tile(q, e.i, j);
+      b.add(Task{ts ? kTsmqr : kTtmqr, e.i, e.piv, (int16_t)k, (int16_t)j}, ts ? kWTsmqr : kWTtmqr, rd.r, rd.n, w4.r,
+            w4.n);
     }
   }
 }
@@ -268,7 +313,8 @@ std::vector<std::vector<char>> ts_square_rows(int p, int q, const std::vector<El
   return square;
 }
 
-void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts, bool prep) {
+void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts, bool prep,
+                        bool split) {
   const int kmax = std::min(p, q);
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : elims) by_col[e.k].push_back(e);
@@ -277,14 +323,14 @@ void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &
   for (int k = 0; k < kmax; ++k) {
     const char *sq = ts ? square[k].data() : nullptr;
     add_panel_tasks(b, p, q, k, sq, prep);
-    add_elim_tasks(b, q, k, by_col[k], sq, prep);
+    add_elim_tasks(b, q, k, by_col[k], sq, prep, split);
   }
 }
 
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge,
-                        const OrderSpec *order, bool ts, bool prep) {
+                        const OrderSpec *order, bool ts, bool prep, bool split) {
   GraphBuilder b(p * q * kRegionsPerTile);
-  add_factor_program(b, p, q, elims, ts, prep);
+  add_factor_program(b, p, q, elims, ts, prep, split);
   finalize_graph(b, g, drop_edge, order);
 }
 

@@ -511,6 +511,72 @@ __device__ void task_pairqrt_resident(const ExecParams &p, unsigned char *raw, u
   __syncthreads();
 }
 
+// Block b of a split TTQRT (ts false) / TSQRT (ts true): the ib-blocks of columns
+// 32b .. 32b+31 of the elimination, with rows 32b .. 32b+31 of the pivot's R and the zeroed
+// tile's columns 32b .. K-1 resident (TT: its upper part, rows < 32b + 32; TS: all rows).
+// Blocks run in order for one elimination (block b+1 needs the columns block b updated),
+// and block b of the next elimination on the same pivot needs only R's row block b; the
+// arithmetic per ib-block is task_pairqrt_resident's.
+template <bool kTS>
+__device__ void task_pairqrt_split(const ExecParams &p, unsigned char *raw, uint64_t *ph, int i, int piv, int k,
+                                   int b) {
+  const TileGeom geo{p.m, p.n, kMNB};
+  const int ib = p.ib;
+  const int c0 = b * kPanelSplitCols;
+  ResBufs rb = res_carve(raw, ib, ph);
+  Smem<float> &s = rb.s;
+  float *A = static_cast<float *>(p.A);
+  float *t1 = tile_ptr(A, p.lda, kMNB, piv, k), *t2 = tile_ptr(A, p.lda, kMNB, i, k);
+  float *Tt = t_ptr(static_cast<float *>(p.T), p.P, ib, kMNB, i, k, 1);
+  const int mb = geo.rows(i), K = geo.cols(k);
+  const int c1 = min(c0 + kPanelSplitCols, kMNB);
+  if (c0 >= K) {  // a ragged last tile column: these reflectors do not exist
+    for (int cb = c0; cb < c1; cb += ib) store_t(Tt, ib, cb, min(ib, kMNB - cb), s, 0);
+    __syncthreads();
+    return;
+  }
+  const int r1 = min(c1, K);                   // R rows of this block: c0 .. r1-1
+  const int rows_i = kTS ? mb : min(c1, mb);   // rows of the zeroed tile the block touches
+  // resident (local column c - c0; R rows local r - c0)
+  load_block_mode(rb.Rp, kMLD, t1 + c0 + static_cast<int64_t>(c0) * p.lda, p.lda, r1 - c0, K - c0,
+                  [](int r, int c) { return r <= c ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
+  load_block_mode(rb.Ct, kMLD, t2 + static_cast<int64_t>(c0) * p.lda, p.lda, rows_i, K - c0, [c0](int r, int c) {
+    return (kTS || r <= c0 + c) ? static_cast<int>(kLoad) : static_cast<int>(kZero);
+  });
+  __syncthreads();
+  for (int cb = c0; cb < c1; cb += ib) {
+    const int width = min(ib, kMNB - cb), kb = max(0, min(ib, K - cb));
+    if (kb == 0) {
+      store_t(Tt, ib, cb, width, s, 0);
+      continue;
+    }
+    const int rbk = kTS ? mb : min(cb + kb, mb);
+    s.V = rb.Ct + (cb - c0) * kMLD;
+    s.P1 = rb.Rp + (cb - c0) + (cb - c0) * kMLD;
+    panel_factor_dispatch<float, kTS ? 2 : 1>(s, kb, rbk, cb, mb);
+    phase_mark(s.ph, 0);
+    panel_gram(s, kb, rbk);
+    build_t(s, kb);
+    store_t(Tt, ib, cb, width, s, kb);
+    __syncthreads();
+    phase_mark(s.ph, 1);
+    for (int cs = cb + kb; cs < K; cs += 32) {
+      const int w = min(32, K - cs);
+      apply_block(rb.Ct + (cs - c0) * kMLD, kMLD, rbk, rb.Rp + (cb - c0) + (cs - c0) * kMLD, kMLD, w, s.V, kMLD,
+                  s.T, s.ldt, kb, s.W, s.ldw, false, s.Wv, s.red);
+    }
+    phase_mark(s.ph, 2);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = c0 + warp; c < K; c += kWarps) {
+    for (int r = lane; r < rows_i; r += 32)
+      if (kTS || r <= c) t2[r + static_cast<int64_t>(c) * p.lda] = rb.Ct[r + (c - c0) * kMLD];
+    for (int r = c0 + lane; r < r1 && r <= c; r += 32)
+      t1[r + static_cast<int64_t>(c) * p.lda] = rb.Rp[(r - c0) + (c - c0) * kMLD];
+  }
+  __syncthreads();
+}
+
 // D(128 x 128, FP32 in TMEM) (+)= A (128 x 128) op(B)^T for split operands: the part
 // products A_qa B_qb of one "level" s = qa + qb (s < nparts: hi*hi is level 0; hi*lo and
 // lo*hi level 1; hi*lo2, mid*mid, lo2*hi level 2) for the k-steps ks0 .. ks1-1 (16 columns

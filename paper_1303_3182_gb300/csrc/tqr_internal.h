@@ -48,8 +48,15 @@ enum TaskKind : int32_t {
   kPrepG = 9,   // images of GEQRT(i,k)'s reflectors (read by UNMQR(i,k,j))
   kPrepT = 10,  // images of the TTQRT / TSQRT that zeroed tile (i,k) (read by TTMQR / TSMQR);
                 // its j is 1 after a TSQRT, 0 after a TTQRT
+  // tensor-core graphs: a TTQRT / TSQRT split into kPanelSplits tasks of 32 columns each
+  // (block j = b), so that the next elimination on the same pivot can start block b as
+  // soon as block b of this one has finished with the pivot's row block b
+  kTtqrtS = 11,
+  kTsqrtS = 12,
 };
-constexpr int kNumKinds = 11;
+constexpr int kNumKinds = 13;
+constexpr int kPanelSplits = 4;     // 32-column blocks of a 128-column tile
+constexpr int kPanelSplitCols = 32;
 
 // A task as the device executor reads it (16 bytes).
 struct Task {
@@ -100,12 +107,16 @@ struct GraphBuilder {
 };
 
 // Tile regions of the factorization graph: each tile (i,j) has a strictly-lower part
-// (GEQRT reflectors) and an upper part (R, then TTQRT reflectors), and two operand-image
-// slots (tensor-core precisions: GEQRT's and the TT/TS elimination's images).
-constexpr int kRegionsPerTile = 4;
+// (GEQRT reflectors), an upper part (R, then TTQRT reflectors) kept as kPanelSplits row
+// blocks (a split panel task writes one row block of its pivot's R), and two operand-image
+// slots (tensor-core precisions: GEQRT's and the TT/TS elimination's images).  A task that
+// touches the upper part as a whole touches all of its row blocks.
+constexpr int kRegionsPerTile = 3 + kPanelSplits;
 inline int region_L(int q, int i, int j) { return (i * q + j) * kRegionsPerTile; }
-inline int region_U(int q, int i, int j) { return (i * q + j) * kRegionsPerTile + 1; }
-inline int region_ops(int q, int i, int j, int which) { return (i * q + j) * kRegionsPerTile + 2 + which; }
+inline int region_Ub(int q, int i, int j, int b) { return (i * q + j) * kRegionsPerTile + 1 + b; }
+inline int region_ops(int q, int i, int j, int which) {
+  return (i * q + j) * kRegionsPerTile + 1 + kPanelSplits + which;
+}
 // Adds GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k of panel k except the rows with
 // square[i] != 0 (zeroed by TS kernels); returns the task ids of the GEQRTs (index i - k,
 // -1 for a skipped row).  prep: a PREP_G(i,k) task after each GEQRT writes its operand
@@ -113,9 +124,10 @@ inline int region_ops(int q, int i, int j, int which) { return (i * q + j) * kRe
 std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square = nullptr,
                                  bool prep = false);
 // Adds the eliminations of panel k in order: TSQRT / TSMQR(i,piv,k,j) when square[i] != 0,
-// TTQRT / TTMQR(i,piv,k,j) otherwise; prep: a PREP_T(i,k) task after each TTQRT / TSQRT.
+// TTQRT / TTMQR(i,piv,k,j) otherwise; prep: a PREP_T(i,k) task after each TTQRT / TSQRT;
+// split: each TTQRT / TSQRT as kPanelSplits block tasks (kTtqrtS / kTsqrtS, block in j).
 void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square = nullptr,
-                    bool prep = false);
+                    bool prep = false, bool split = false);
 // Orders a built graph for the executor (earliest start, then longest remaining path)
 // and fills the successor CSR.
 // Executor (claim) order of a factorization graph.  mode 0: earliest start with
@@ -127,14 +139,14 @@ struct OrderSpec {
   int mode = 0;
   int nproc = 1;
   // per task kind (TaskKind index; the apply-Q kinds are unused)
-  int64_t w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr, 1, 1};
+  int64_t w[kNumKinds] = {kWGeqrt, kWTtqrt, kWUnmqr, kWTtmqr, kWUnmqr, kWTtmqr, kWTsqrt, kWTsmqr, kWTsmqr, 1, 1, 1, 2};
   int id = 0;  // identity of the weight set in the plan cache (built-in sets < 0)
 };
 void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1, const OrderSpec *order = nullptr);
 // Tasks of the sequential program (all panels, in column order) added to b; ts: the TS
 // form of the list.
 void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts = false,
-                        bool prep = false);
+                        bool prep = false, bool split = false);
 // Backflow priorities (a task's weight plus the largest priority of its successors) of
 // a graph in program order with successor lists succ and weights w.
 std::vector<int64_t> backflow_priorities(const std::vector<std::vector<int32_t>> &succ,
@@ -153,14 +165,17 @@ int64_t alap_derived_bound(const std::vector<int64_t> &w, const std::vector<int6
 // Builds the factorization task graph of a p x q tile matrix with the given list
 // (column-by-column program of Algorithm "elimTR"; dependencies from the tile regions
 // each kernel reads and writes, Eq. ttdeps / ttdeps2).
-// prep: the tensor-core form, with operand-image preparation tasks (PREP_G / PREP_T).
+// prep: the tensor-core form, with operand-image preparation tasks (PREP_G / PREP_T);
+// split: its TTQRT / TSQRT split into 32-column block tasks.
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
                         int64_t drop_edge = -1, const OrderSpec *order = nullptr, bool ts = false,
-                        bool prep = false);
+                        bool prep = false, bool split = false);
 // Builds the graph that applies Q^T (or Q when reverse) to a right-hand-side block.
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g, bool ts = false);
 
 void set_error(const std::string &msg);
+// The pending tqr_debug_drop_edge value (-1 if none), cleared by the call (batch plans).
+int64_t take_debug_drop_edge();
 // Number of kernels this library has launched (tqr_launch_count).
 void count_launch(int64_t k = 1);
 int64_t wait_limit_ns();   // current device-wait limit (tqr_set_wait_limit_ns)

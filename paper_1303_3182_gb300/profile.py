@@ -46,7 +46,7 @@ def _factor(a, tqr, torch):
         tr = tqr.trace_fetch()
         t0 = int(tr[:, 4].min())
         names = ["GEQRT", "TTQRT", "UNMQR", "TTMQR", "UNMQR_B", "TTMQR_B", "TSQRT", "TSMQR", "TSMQR_B",
-                 "PREP_G", "PREP_T"]
+                 "PREP_G", "PREP_T", "TTQRT_S", "TSQRT_S"]
         recs = [{"kind": names[int(r[0])], "i": int(r[1]), "piv": int(r[2]), "k": int(r[3]) & 0xFFFF,
                  "j": (int(r[3]) >> 16) if (int(r[3]) >> 16) < 32768 else -1, "sm": int(r[7]),
                  "start_us": (int(r[5]) - t0) / 1e3, "end_us": (int(r[6]) - t0) / 1e3,

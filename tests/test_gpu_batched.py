@@ -224,3 +224,30 @@ def test_factor_batched_null_params_autotunes(prec):
         tqr.factor(ref, nb, ib, tree, bs, prec)
         torch.cuda.synchronize()
         assert torch.equal(ref, As[b]), b
+
+
+def test_batched_wait_timeout_reports_error_and_context_survives():
+    """A batch plan built with one merged dependency release left out (tqr_debug_drop_edge):
+    the waiting CTA gives up after the wait limit, the run returns TQR_ETIMEOUT through the
+    plan's status, and a following batch of the same matrices factors as before."""
+    shapes = [(300, 64), (520, 128), (256, 32)]
+    mats = [synthetic.gaussian(m, n, seed=6300 + b).astype(np.float32).astype(np.float64)
+            for b, (m, n) in enumerate(shapes)]
+    params = [[64, 16, tqr.GREEDY, 1]] * len(shapes)
+    ref = [to_dev(A, torch.float32) for A in mats]
+    tqr.factor_batched(ref, "fp32", params=params)
+    torch.cuda.synchronize()
+    old = tqr.set_wait_limit_ns(200 * 10 ** 6)
+    try:
+        tqr.debug_drop_edge(3)
+        with pytest.raises(tqr.TqrError) as ei:
+            tqr.factor_batched([to_dev(A, torch.float32) for A in mats], "fp32", params=params)
+        assert ei.value.status == tqr.TQR_ETIMEOUT
+    finally:
+        tqr.set_wait_limit_ns(old)
+        tqr.debug_drop_edge(-1)
+    again = [to_dev(A, torch.float32) for A in mats]
+    tqr.factor_batched(again, "fp32", params=params)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, again):
+        assert torch.equal(a, b)

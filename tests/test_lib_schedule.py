@@ -120,3 +120,24 @@ def test_bench_tile_task_bytes_match_the_oracle_kernel_counts():
                 + c["GEQRT"] * (tile + tblk + 2 * img) + (c["TTQRT"] + c["TSQRT"]) * (tile + tblk + 3 * img)
                 + c["UNMQR"] * (2 * tile + 2 * img) + (c["TTMQR"] + c["TSMQR"]) * (4 * tile + 3 * img))
         assert bench.tile_task_bytes(Args) == want, tree
+
+
+def test_split_panel_graph_schedule():
+    """The tensor-core graph with operand-preparation tasks and split TT / TS panels (nine
+    weights of tqr_schedule_ts): on one processor its makespan is the sum of all task
+    weights (every task runs once: #GEQRT + #TTQRT + #TSQRT preparations, four blocks per
+    TT / TS panel); with the blocks weighing a quarter of their panel, pipelining the blocks
+    of consecutive eliminations on a pivot never lengthens the critical path."""
+    p, q = 12, 4
+    for tree, bs in (("plasma-ts", 4), ("greedy", 1), ("flat-ts", 1)):
+        c = tqr.plan_counts(p * 128, q * 128, 128, tree, bs)
+        w = [40, 20, 6, 6, 24, 6]
+        prep, wtt, wts = 3, 5, 6
+        one, _, _ = tqr.schedule(p, q, tree, bs, 1, w + [prep, wtt, wts])
+        total = (w[0] * c["GEQRT"] + w[2] * c["UNMQR"] + w[3] * c["TTMQR"] + w[5] * c["TSMQR"]
+                 + prep * (c["GEQRT"] + c["TTQRT"] + c["TSQRT"]) + 4 * wtt * c["TTQRT"] + 4 * wts * c["TSQRT"])
+        assert one == total, tree
+        big = 10 ** 6
+        unsplit, _, _ = tqr.schedule(p, q, tree, bs, big, w + [prep])
+        split, _, _ = tqr.schedule(p, q, tree, bs, big, w + [prep, w[1] // 4, w[4] // 4])
+        assert split <= unsplit, tree
