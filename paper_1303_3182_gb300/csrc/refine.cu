@@ -8,8 +8,9 @@
 // x += dx.  Restarting from the true residual makes the stopping test independent of
 // LSQR's internal estimates, which drift when the preconditioner is weak.  A products,
 // residuals, the Krylov vectors and every scalar recurrence are FP64; the triangular
-// solves read the low-precision R (FP32) and compute in FP64.  All scalar state lives in
-// device memory, so an iteration is a fixed sequence of launches without host syncs.
+// solves read the low-precision R (FP32) and compute in FP64; the two products with A inside
+// an LSQR iteration use A split into FP32 pairs with double-float arithmetic (below).  All
+// scalar state lives in device memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -94,6 +95,115 @@ __global__ void gemv_t(int64_t m, int64_t n, const double *A, int64_t lda, const
     for (; i < m; i += 32) acc[0] = fma(col[i], x[i], acc[0]);
     const double s = warp_sum_d((acc[0] + acc[1]) + (acc[2] + acc[3]));
     if (lane == 0) Y[warp + r * ldy] = s * (scale ? scale[r] : 1.0);
+  }
+}
+
+// ---- inner-solve products with A held as FP32 pairs ---------------------------------
+// The LSQR correction solve needs A v and A^T u only to the accuracy of a correction, but
+// its FP64 GEMVs are bound by this GPU's FP64 rate (m n DFMA, about twice the time the
+// 8 m n bytes of A take to stream).  For them A is split once per solve into FP32 pairs
+// a = a_hi + a_lo (a_lo the FP32 rounding of a - a_hi, 8 bytes per entry like the FP64
+// matrix), the vector likewise, and each product is formed in double-float FP32 arithmetic:
+// a x = a_hi x_hi (exact as p + e by an FMA) + (a_hi x_lo + a_lo x_hi), the sum kept as an
+// unevaluated pair with Knuth's TwoSum - about 2^-47 relative per term, against 2^-53 for
+// FP64, with FP32 instructions only.  The residual r = b - A x and A^T r of the outer
+// refinement stay in FP64.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void df_acc(DF &s, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  const float e = fmaf(ah, xh, -p) + fmaf(ah, xl, al * xh);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+__device__ __forceinline__ DF df_sum(DF a, DF b) {
+  const float t = a.hi + b.hi;
+  const float bb = t - a.hi;
+  const float err = (a.hi - (t - bb)) + (b.hi - bb);
+  return DF{t, a.lo + b.lo + err};
+}
+
+// P(i, j) = (hi, lo) split of A(i, j) (column-major, ld m).
+__global__ void split_pairs(int64_t m, int64_t n, const double *A, int64_t lda, float2 *P) {
+  const int64_t total = m * n;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t j = idx / m, i = idx - j * m;
+    const double a = A[i + j * lda];
+    const float hi = static_cast<float>(a);
+    P[idx] = make_float2(hi, static_cast<float>(a - static_cast<double>(hi)));
+  }
+}
+
+// Xp(:, r) = pair split of X(:, r), r < nrhs.
+__global__ void split_vec(int64_t len, const double *X, int64_t ldx, float2 *Xp, int nrhs) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; i < len;
+       i += static_cast<int64_t>(gridDim.x) * kT) {
+    const double a = X[i + r * ldx];
+    const float hi = static_cast<float>(a);
+    Xp[i + r * len] = make_float2(hi, static_cast<float>(a - static_cast<double>(hi)));
+  }
+}
+
+// Y(:, r) += A X(:, r) with A and X as pairs (rows of this CTA, columns [c0, c1)).
+__global__ void gemv_n_pairs(int64_t m, int64_t n, const float2 *P, const float2 *Xp, double *Y, int64_t ldy,
+                             int nrhs, int64_t chunk) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x;
+  const int64_t c0 = blockIdx.y * chunk, c1 = c0 + chunk < n ? c0 + chunk : n;
+  if (i >= m) return;
+  for (int r = 0; r < nrhs; ++r) {
+    const float2 *x = Xp + r * n;
+    DF s0{0.f, 0.f}, s1{0.f, 0.f};
+    int64_t j = c0;
+    for (; j + 2 <= c1; j += 2) {
+      const float2 a0 = P[i + j * m], a1 = P[i + (j + 1) * m];
+      const float2 x0 = x[j], x1 = x[j + 1];
+      df_acc(s0, a0.x, a0.y, x0.x, x0.y);
+      df_acc(s1, a1.x, a1.y, x1.x, x1.y);
+    }
+    for (; j < c1; ++j) {
+      const float2 a0 = P[i + j * m], x0 = x[j];
+      df_acc(s0, a0.x, a0.y, x0.x, x0.y);
+    }
+    const DF s = df_sum(s0, s1);
+    atomicAdd(Y + i + r * ldy, static_cast<double>(s.hi) + static_cast<double>(s.lo));
+  }
+}
+
+// Y(j, r) = scale(r) sum_i A(i, j) U(i, r) with A and U as pairs: one warp per column j.
+__global__ void gemv_t_pairs(int64_t m, int64_t n, const float2 *P, const float2 *Up, double *Y, int64_t ldy,
+                             int nrhs, const double *scale) {
+  const int warp = (blockIdx.x * kT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const float2 *col = P + static_cast<int64_t>(warp) * m;
+  for (int r = 0; r < nrhs; ++r) {
+    const float2 *u = Up + r * m;
+    DF s0{0.f, 0.f}, s1{0.f, 0.f};
+    int64_t i = lane;
+    for (; i + 32 < m; i += 64) {
+      const float2 a0 = col[i], a1 = col[i + 32], u0 = u[i], u1 = u[i + 32];
+      df_acc(s0, a0.x, a0.y, u0.x, u0.y);
+      df_acc(s1, a1.x, a1.y, u1.x, u1.y);
+    }
+    for (; i < m; i += 32) {
+      const float2 a0 = col[i], u0 = u[i];
+      df_acc(s0, a0.x, a0.y, u0.x, u0.y);
+    }
+    DF s = df_sum(s0, s1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DF t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+      s = df_sum(s, t);
+    }
+    if (lane == 0)
+      Y[warp + r * ldy] = (static_cast<double>(s.hi) + static_cast<double>(s.lo)) * (scale ? scale[r] : 1.0);
   }
 }
 
@@ -257,10 +367,13 @@ dim3 vgrid(int64_t len, int nrhs) {
 size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
   // U (m) and V, W, Y, Z, Tt (n) per right-hand side, five scalar arrays, ||A||_F^2, two
   // LSQR state sets, and the inverses of R's 64 x 64 diagonal blocks
+  // plus A as FP32 pairs (one double's worth per entry) and the pair splits of one m- and
+  // one n-vector per right-hand side, for the inner products
   const size_t nblk = static_cast<size_t>((n + 63) / 64);
   return static_cast<size_t>(nrhs) * (m + 5 * n) + 5 * static_cast<size_t>(nrhs) + 2 +
          2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8 + nblk * 64 * 64 +
-         2 * static_cast<size_t>(nrhs) + precond_work_doubles(n, false);
+         2 * static_cast<size_t>(nrhs) + precond_work_doubles(n, false) + static_cast<size_t>(m) * n +
+         static_cast<size_t>(nrhs) * (m + n) + 2;
 }
 
 int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream) {
@@ -290,6 +403,10 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   double *bn2 = Dinv + static_cast<size_t>((n + 63) / 64) * 64 * 64;               // [nrhs] ||b||^2
   double *xn2 = bn2 + nrhs;                                                       // [nrhs] ||x||^2
   double *Pw = xn2 + nrhs;                                                        // preconditioner solves
+  // A as FP32 pairs and the pair splits of the inner products' vectors (8-byte aligned)
+  float2 *Apair = reinterpret_cast<float2 *>(Pw + precond_work_doubles(n, false));
+  float2 *Vpair = Apair + static_cast<size_t>(m) * n;   // n x nrhs
+  float2 *Upair = Vpair + static_cast<size_t>(n) * nrhs;  // m x nrhs
   const int64_t chunk = 512;
   const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
   const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
@@ -308,6 +425,8 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   } while (0)
   TQR_CK(cudaMemsetAsync(anorm2, 0, sizeof(double), st));
   fro_norm2<<<1216, kT, 0, st>>>(m, n, A, lda, anorm2);
+  TQR_CKL();
+  split_pairs<<<1216, kT, 0, st>>>(m, n, A, lda, Apair);
   TQR_CKL();
   if ((rc = launch_diag_inverse(n, R, ldr, false, Dinv, stream)) != 0) return rc;
   if ((rc = precond_setup(n, R, ldr, false, Dinv, Pw, stream)) != 0) return rc;
@@ -395,14 +514,18 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
       if ((rc = solve_r(Tt, false)) != 0) return rc;
       scale_u<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, cur, nrhs);
       TQR_CKL();
-      gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
+      split_vec<<<vgrid(n, nrhs), kT, 0, st>>>(n, Tt, n, Vpair, nrhs);
+      TQR_CKL();
+      gemv_n_pairs<<<ggrid, kT, 0, st>>>(m, n, Apair, Vpair, U, m, nrhs, chunk);
       TQR_CKL();
       TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
       colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);
       TQR_CKL();
       finish_norm<<<1, 64, 0, st>>>(ssq_b, inv_b, betas, nrhs);
       TQR_CKL();
-      gemv_t<<<tgrid, kT, 0, st>>>(m, n, A, lda, U, m, Z, n, nrhs, inv_b);
+      split_vec<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, Upair, nrhs);
+      TQR_CKL();
+      gemv_t_pairs<<<tgrid, kT, 0, st>>>(m, n, Apair, Upair, Z, n, nrhs, inv_b);
       TQR_CKL();
       if ((rc = solve_r(Z, true)) != 0) return rc;
       axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, n, betas, ssq_a, nrhs);
