@@ -81,6 +81,8 @@ def parse_args():
                     help="tuning table of the batch: 'auto' (the library's autotuner, tqr_batch_autotune), "
                          "'builtin' (the built-in size classes) or a JSON file with a 'table'")
     ap.add_argument("--batch-reps", type=int, default=5)
+    ap.add_argument("--batch-tensor-prec", default="bf16x6",
+                    help="also run the batch with this tensor-core precision ('' = no)")
     ap.add_argument("--no-c5", action="store_true",
                     help="skip the square 16384^2 solve (cond 1e4, 64 right-hand sides; about 1 min)")
     ap.add_argument("--c5-precs", default="bf16x3,bf16x6")
@@ -263,7 +265,7 @@ class ClockSampler:
 # Batched factorization: 2048 FP32 matrices, rows U[256, 8192], columns {32..256}
 # ---------------------------------------------------------------------------------
 
-def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
+def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None, prec=None):
     """One graph-replayed persistent launch over the whole batch vs the same plan
     without a graph vs one tqr_factor launch per matrix (device time, inputs restored
     untimed before each launch; the 4.2 GB batch is larger than L2).  With several
@@ -276,7 +278,7 @@ def batched_measurement(args, hbm_gbs, rank=0, world=1, device=None):
     from paper_1303_3182_gb300 import replicas
     from paper_1303_3182_gb300.autotune import DeviceBatch, size_classes, time_launch
 
-    prec = args.batch_prec
+    prec = prec or args.batch_prec
     all_shapes = synthetic.ragged_batch_shapes(BATCH_COUNT, seed=synthetic.SEED_BASE + 4)
     shapes = [all_shapes[b] for b in replicas.shard(len(all_shapes), rank, world)]
     ms, ns = [m for m, _ in shapes], [n for _, n in shapes]
@@ -624,6 +626,12 @@ def main_gpu(args):
     batched = None
     if not args.no_batched:
         batched = batched_measurement(args, hbm_peak(), rank, world, dev)
+        if args.batch_tensor_prec:
+            # the same FP32 batch with tensor-core updates (nb 128; ib and tree autotuned per class)
+            tb = batched_measurement(args, hbm_peak(), rank, world, dev, prec=args.batch_tensor_prec)
+            batched["tensor_core"] = {k: tb[k] for k in ("value", "unit", "ms_graph_launch", "ms_one_launch_per_matrix",
+                                                          "speedup_vs_per_matrix", "tasks", "tuning", "table")}
+            batched["tensor_core"]["prec"] = args.batch_tensor_prec
     c5 = c5_measurement(args) if (not args.no_c5 and world == 1) else None
     z64 = z64_measurement(fp64_peak=max(tqr.fp64_peak().values())) if world == 1 else None
     c1 = c1_measurement() if world == 1 else None

@@ -333,12 +333,15 @@ int tqr_trsm_static(int64_t n, int prec, const void *A, int64_t lda, double *B, 
  *                      when ||A^T r|| / (||A||_F ||r||) <= tol (least-squares optimal)
  *                      or ||r|| / (||A||_F ||x|| + ||b||) <= tol (backward error of a
  *                      consistent system, e.g. square A); the refinement also stops
- *                      when a step no longer halves the worst optimality (the
- *                      FP64-attainable level).  Otherwise it solves for the correction
- *                      with LSQR (Paige & Saunders, 1982) in FP64, right-preconditioned
- *                      with the low-precision R, using LSQR's two stopping rules (the
- *                      normal-equation estimate, and the residual estimate against the
- *                      backward-error threshold).
+ *                      when a step halves neither the worst optimality nor the worst
+ *                      backward error (the FP64-attainable level).  Otherwise it solves
+ *                      for the correction with LSQR (Paige & Saunders, 1982),
+ *                      right-preconditioned with the low-precision R, using LSQR's two
+ *                      stopping rules (the normal-equation estimate, and the residual
+ *                      estimate against the backward-error threshold); the correction
+ *                      solve forms its products with A from an FP32 hi/lo split of A in
+ *                      double-float arithmetic (about 2^-47 per product), everything else
+ *                      in FP64.
  *   A, B    : device, not modified.  X : device n x nrhs, ldx >= n.
  *   iters   : out (may be NULL), refinement iterations used (max over right-hand sides).
  *   workspace / ws_bytes : device scratch of at least tqr_lstsq_workspace_size() bytes.

@@ -442,7 +442,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   TQR_CK(cudaMemcpyAsync(host_bn2.data(), bn2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   int total_it = 0;
   bool converged = false;
-  double prev_eta = 1e300;
+  double prev_eta = 1e300, prev_omega = 1e300;
   const bool debug = std::getenv("TQR_DEBUG_REFINE") != nullptr;
   const int max_outer = 12;
   for (int outer = 0; outer < max_outer; ++outer) {
@@ -494,14 +494,17 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
       converged = true;
       break;
     }
-    // an outer step that no longer halves the optimality has reached the level FP64
-    // rounding allows for this problem (as LAPACK's refinement stops): converged
-    if (worst_eta > 0.5 * prev_eta) {
+    // an outer step that halves neither the optimality nor the backward error has reached
+    // the level FP64 rounding allows for this problem (as LAPACK's refinement stops):
+    // converged.  (A least-squares problem stalls on the optimality; a consistent system,
+    // whose optimality ratio is rounding noise, on the backward error.)
+    if (worst_eta > 0.5 * prev_eta && worst_omega > 0.5 * prev_omega) {
       converged = true;
       break;
     }
     if (total_it >= max_iter) break;
     prev_eta = worst_eta;
+    prev_omega = worst_omega;
     // LSQR on min || (A R^-1) y - r ||, then X += R^{-1} y
     if ((rc = solve_r(Z, true)) != 0) return rc;
     axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, nullptr, n, nullptr, ssq_a, nrhs);
