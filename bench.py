@@ -44,12 +44,14 @@ MIXED_TRAFFIC_PER_FLOP = 6.773e9 / 2.004e11
 BATCH_TRAFFIC_PER_FLOP = 1.328e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
 # Kernel weights of the library's default claim order for the tensor-core precisions
-# (tqr_set_claim_order mode 2: GEQRT, TTQRT, UNMQR, TTMQR at nb 128, bf16x6; measured task
-# durations with tuned panel weights), and the mean task durations (us) of the same
-# executor from a per-task trace on GB300 (32768 x 4096), the weights of the schedule bound.
-TENSOR_CLAIM_WEIGHTS = (265, 285, 20, 32, 320, 32, 66)
-# GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR, operand-image preparation (PlasmaTree-TS trace)
-TENSOR_TASK_MEAN_US = (253, 286, 25, 29, 270, 29, 72)
+# (tqr_set_claim_order mode 2 at nb 128, bf16x6: measured task durations with tuned panel
+# weights), and the mean task durations (us) of the same executor from a per-task trace on
+# GB300 (32768 x 4096, PlasmaTree-TS(16)), the weights of the schedule bound.  Order:
+# GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR, operand-image preparation, TTQRT block, TSQRT
+# block (the tensor-core graph splits its TT / TS panels into 32-column block tasks, so the
+# whole-panel TTQRT / TSQRT weights do not occur in it).
+TENSOR_CLAIM_WEIGHTS = (265, 285, 20, 32, 320, 32, 66, 80, 85)
+TENSOR_TASK_MEAN_US = (245, 286, 23, 28, 270, 28, 72, 68, 75)
 
 
 def parse_args():

@@ -150,6 +150,16 @@ int tqr_set_claim_order(int mode, const int64_t *weights);
 /* tqr_set_claim_order with six weights (GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR) for
  * mode 1 (NULL = 4, 2, 6, 6, 6, 12).  Errors as tqr_set_claim_order. */
 int tqr_set_claim_order_ts(int mode, const int64_t *weights);
+/* Column parts of later TQR_FP64 / TQR_FP32 factorization plans.  The critical path of a
+ * small task graph (Section 3.2: the lower bound on its execution time however many
+ * cores run it) is a chain of panel and update kernels; with column parts each update
+ * task UNMQR / TTMQR / TSMQR becomes up to four tasks on 16-column (FP64) or 32-column
+ * (FP32) slices of its target tiles, which run on different SMs, while each column's
+ * arithmetic stays that of the whole-tile task (the factors are bit for bit the same).
+ * mode 0: never; 1 (default): when the split graph's update tasks fit on the GPU's SMs
+ * at once (a graph bound by its critical path); 2: always (when the tile holds two
+ * slices).  Plans already built keep their form.  Host only.  Errors: -1 unknown mode. */
+int tqr_set_column_parts(int mode);
 
 /* Bytes of the caller-owned T workspace of tqr_factor: two ib x nb compact-WY T
  * factors (GEQRT's and TTQRT's, Schreiber-Van Loan form, LAPACK GEQRT layout: block b

@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
             "tqr_schedule": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
             "tqr_set_claim_order": (i32, [i32, c_i64p]),
             "tqr_set_claim_order_ts": (i32, [i32, c_i64p]),
+            "tqr_set_column_parts": (i32, [i32]),
             "tqr_schedule_ts": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
             "tqr_debug_claim_order": (i32, [i32, i32, i32, i32, i32, i32, c_i64p, ctypes.POINTER(ctypes.c_int32),
                                              c_i64p]),
@@ -197,6 +198,12 @@ def set_claim_order(mode: int, weights=None) -> None:
         _check("tqr_set_claim_order_ts", lib().tqr_set_claim_order_ts(mode, _weights4(weights)))
     else:
         _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))
+
+
+def set_column_parts(mode: int) -> None:
+    """Column parts of later fp64 / fp32 factorization plans (tqr_set_column_parts): 0 =
+    never, 1 = automatic (small graphs bound by their critical path), 2 = always."""
+    _check("tqr_set_column_parts", lib().tqr_set_column_parts(mode))
 
 
 def claim_order(p: int, q: int, tree="greedy", bs: int = 1, mode: int = 0, nproc: int = 1, weights=None):

@@ -133,6 +133,7 @@ struct LaunchTimer {
 struct Plan {
   Graph g;
   int device = 0;
+  int colparts = 1;  // update tasks split into column parts (SIMT factorization plans)
   Task *d_tasks = nullptr;
   int32_t *d_succ_ptr = nullptr, *d_succ_idx = nullptr, *d_indeg = nullptr;
   int32_t *d_counters = nullptr;
@@ -181,7 +182,7 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 // prep: the tensor-core form of a factorization graph (operand-preparation tasks); split:
 // with its TT / TS panels as 32-column block tasks.
 int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSpec *order = nullptr,
-             bool prep = false, bool split = false) {
+             bool prep = false, bool split = false, int colparts = 1) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -194,7 +195,8 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   // the order's identity (spec.id: user weights carry the setting's generation, each
   // built-in weight set a negative key of its own) is part of the key; a plan built with
   // the test hook is never reused: it gets a key of its own
-  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : (kind == 0 && prep ? (split ? 4 : 3) : kind), P, Q, tree,
+  const int form = kind == 0 && prep ? (split ? 4 : 3) : (kind == 0 && colparts > 1 ? 5 : kind);
+  const PlanKey key{dev, drop >= 0 ? 100 + g_debug_plans++ : form, P, Q, tree,
                     tree_base(tree) == TQR_PLASMA ? bs : 0, bounded ? spec.id : 0, bounded ? spec.nproc : 0};
   auto it = g_plans.find(key);
   if (it != g_plans.end()) {
@@ -206,9 +208,11 @@ int get_plan(int kind, int P, int Q, int tree, int bs, Plan **out, const OrderSp
   auto plan = std::make_unique<Plan>();
   plan->device = dev;
   if (kind == 0)
-    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree), prep, prep && split);
+    build_factor_graph(P, Q, elims, plan->g, drop, bounded ? &spec : nullptr, tree_ts(tree), prep, prep && split,
+                       colparts);
   else
     build_applyq_graph(P, Q, elims, kind == 2, plan->g, tree_ts(tree));
+  plan->colparts = kind == 0 ? colparts : 1;
   if (drop >= 0) g_drop_edge = -1;  // the test hook applies to one plan only
   const Graph &g = plan->g;
   if ((e = upload(&plan->d_tasks, g.tasks)) != cudaSuccess ||
@@ -265,6 +269,8 @@ int run_plan(Plan *plan, ExecParams prm, bool dbl, cudaStream_t st) {
                                   cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_state, 0, 2 * sizeof(int32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "plan reset");
+  prm.colparts = plan->colparts;
+  prm.colw = static_cast<int>(ceil_div(prm.nb, prm.colparts));
   prm.tasks = plan->d_tasks;
   prm.succ_ptr = plan->d_succ_ptr;
   prm.succ_idx = plan->d_succ_idx;
@@ -507,6 +513,42 @@ int tqr_set_claim_order_ts(int mode, const int64_t *weights) {
   return set_claim_order_impl(mode, w);
 }
 
+namespace {
+int g_colparts_mode = 1;  // tqr_set_column_parts: 0 never, 1 automatic, 2 always
+
+// Column parts of a SIMT factorization plan: kColParts slices (each at least one 16- or
+// 32-column chunk of the update kernels) when the graph's update tasks, split, still fit
+// on the GPU's SMs at once - a graph that small is bound by its critical path, on which
+// every update then runs on several SMs - or always (mode 2); else 1.
+int column_parts(int P, int Q, int nb, bool dbl) {
+  int mode;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    mode = g_colparts_mode;
+  }
+  if (mode == 0 || Q < 2 || Q >= (1 << kColShift)) return 1;
+  const int chunk = dbl ? 16 : 32;
+  const int parts = std::min<int>(kColParts, static_cast<int>(ceil_div(nb, chunk)));
+  if (parts < 2) return 1;
+  if (mode == 2) return parts;
+  // updates of the TT program: for panel k, (P - k) UNMQR and (P - k - 1) TTMQR per later column
+  int64_t nupd = 0;
+  for (int k = 0; k < std::min(P, Q); ++k) nupd += static_cast<int64_t>(2 * (P - k) - 1) * (Q - k - 1);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess)
+    return 1;
+  return nupd * parts <= nsm ? parts : 1;
+}
+}  // namespace
+
+int tqr_set_column_parts(int mode) {
+  if (mode < 0 || mode > 2) return -1;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_colparts_mode = mode;
+  return TQR_OK;
+}
+
 int tqr_workspace_size(int64_t m, int64_t n, int nb, int ib, int prec, size_t *T_bytes) {
   const int rc = check_tiles(m, n, nb, ib, TQR_GREEDY, 1, prec);
   if (rc) return rc;
@@ -539,9 +581,10 @@ int tqr_factor(int64_t m, int64_t n, int nb, int ib, int tree, int bs, int prec,
     if (order.mode == 1)
       order.nproc = prec == TQR_Z64 ? zexec_slots(nb, ib) : executor_slots(dbl, is_tensor_prec(prec), nb, ib);
     // tensor-core graphs split their TT / TS panels into 32-column block tasks when the
-    // inner block divides 32
+    // inner block divides 32; small SIMT graphs split their updates into column parts
     const bool tensor = is_tensor_prec(prec);
-    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order, tensor, tensor && kPanelSplitCols % ib == 0)) != 0)
+    const int cparts = tensor || prec == TQR_Z64 ? 1 : column_parts(P, Q, nb, dbl);
+    if ((rc = get_plan(0, P, Q, tree, bs, &plan, &order, tensor, tensor && kPanelSplitCols % ib == 0, cparts)) != 0)
       return rc;
     ExecParams prm{};
     prm.A = A;
@@ -721,8 +764,8 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
   double *Bw = reinterpret_cast<double *>(p);
   p += align_up(static_cast<size_t>(m) * nrhs * sizeof(double), 1024);
   double *lw = reinterpret_cast<double *>(p);
-  int rcv = convert_to_f32(A, lda, Af, ldf, m, n, stream);
-  if (rcv) return cuda_fail(static_cast<cudaError_t>(rcv), "lstsq convert");
+  int rcv = lsqr_prepare(m, n, A, lda, Af, ldf, lw, stream);
+  if (rcv) return cuda_fail(static_cast<cudaError_t>(rcv), "lstsq prepare");
   if ((rc = tqr_factor(m, n, nb, ib, tree, bs, prec, Af, ldf, Tw, stream)) != 0) return rc;
   // LSQR starts from x0 = 0: with R as preconditioner a few extra iterations cost less
   // than forming x0 = R^{-1} (Q^T b)(0:n) by a pass over all reflectors
@@ -741,7 +784,7 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
     const int nr = static_cast<int>(std::min<int64_t>(64, nrhs - r0));
     int it = 0;
     const int lrc = lsqr_refine(m, n, nr, A, lda, Af, ldf, B + r0 * ldb, ldb, X + r0 * ldx, ldx,
-                                tol > 0 ? tol : 1e-14, max_iter > 0 ? max_iter : 100, &it, lw, s->flags, status,
+                                tol > 0 ? tol : 1e-14, max_iter > 0 ? max_iter : 100, &it, r0 == 0, lw, s->flags, status,
                                 g_wait_limit_ns, stream);
     if (lrc > 0) return cuda_fail(static_cast<cudaError_t>(lrc), "lstsq refinement");
     if (lrc < 0) converged = false;

@@ -343,33 +343,35 @@ __device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols
       return;
     }
   }
+  // Each phase spreads its outputs over all threads (a small kb or a short tile leaves no
+  // thread idle; FP64 instructions are the cost on this GPU), and each output's sum runs
+  // in a fixed order, so results are deterministic.
   const int tid = threadIdx.x;
-  const int a = tid & 31, g = tid >> 5;
-  // W = C1 + V^T C
-  if (a < kb) {
-    S acc[4] = {0, 0, 0, 0};
-    for (int r = 0; r < nrows; ++r) {
-      const S v = V[r + a * ldv];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = g + kWarps * u;
-        if (c < ncols) acc[u] += v * C[r + c * ldc];
-      }
+  constexpr int kMaxOut = 4;  // outputs of W per thread: kb * ncols <= 32 * 32
+  static_assert(kMaxOut * kThreads >= 32 * 32, "W outputs per thread");
+  // W = C1 + V^T C: output (a, c) per thread step, a fastest (V loads hit distinct banks,
+  // C loads broadcast); two partial sums over even and odd rows
+  for (int idx = tid; idx < kb * ncols; idx += kThreads) {
+    const int c = idx / kb, a = idx - c * kb;
+    const S *va = V + a * ldv, *cc = C + c * ldc;
+    S acc0 = 0, acc1 = 0;
+    int r = 0;
+    for (; r + 1 < nrows; r += 2) {
+      acc0 += va[r] * cc[r];
+      acc1 += va[r + 1] * cc[r + 1];
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = g + kWarps * u;
-      if (c < ncols) W[a + c * ldw] = acc[u] + (C1 ? C1[a + c * ldc1] : S(0));
-    }
+    if (r < nrows) acc0 += va[r] * cc[r];
+    W[a + c * ldw] = (acc0 + acc1) + (C1 ? C1[a + c * ldc1] : S(0));
   }
   __syncthreads();
-  // W = op(T) W
-  S nw[4] = {0, 0, 0, 0};
-  if (a < kb) {
+  // W = op(T) W, every output formed before any is stored
+  S nw[kMaxOut];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = g + kWarps * u;
-      if (c >= ncols) continue;
+  for (int u = 0; u < kMaxOut; ++u) {
+    const int idx = tid + u * kThreads;
+    nw[u] = 0;
+    if (idx < kb * ncols) {
+      const int c = idx / kb, a = idx - c * kb;
       S s = 0;
       if (!transpose_q) {
         for (int b = 0; b <= a; ++b) s += T[b + a * ldt] * W[b + c * ldw];
@@ -380,31 +382,33 @@ __device__ void apply_block(S *C, int ldc, int nrows, S *C1, int ldc1, int ncols
     }
   }
   __syncthreads();
-  if (a < kb) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = g + kWarps * u;
-      if (c < ncols) {
-        W[a + c * ldw] = nw[u];
-        if (C1) C1[a + c * ldc1] -= nw[u];
-      }
+  for (int u = 0; u < kMaxOut; ++u) {
+    const int idx = tid + u * kThreads;
+    if (idx < kb * ncols) {
+      const int c = idx / kb, a = idx - c * kb;
+      W[a + c * ldw] = nw[u];
+      if (C1) C1[a + c * ldc1] -= nw[u];
     }
   }
   __syncthreads();
-  // C -= V W
-  constexpr int kCW = chunk_cols(sizeof(S));
-  for (int r = tid; r < nrows; r += kThreads) {
-    S acc[kCW];
+  // C -= V W: row r and four consecutive columns per thread step, r fastest
+  const int ngrp = (ncols + 3) / 4;
+  for (int idx = tid; idx < nrows * ngrp; idx += kThreads) {
+    const int g = idx / nrows, r = idx - g * nrows;
+    const int c0 = 4 * g;
+    const S *w[4];
 #pragma unroll
-    for (int c = 0; c < kCW; ++c) acc[c] = 0;
+    for (int u = 0; u < 4; ++u) w[u] = W + min(c0 + u, ncols - 1) * ldw;
+    S acc[4] = {0, 0, 0, 0};
     for (int b = 0; b < kb; ++b) {
       const S v = V[r + b * ldv];
 #pragma unroll
-      for (int c = 0; c < kCW; ++c) acc[c] += v * W[b + c * ldw];
+      for (int u = 0; u < 4; ++u) acc[u] += v * w[u][b];
     }
 #pragma unroll
-    for (int c = 0; c < kCW; ++c)
-      if (c < ncols) C[r + c * ldc] -= acc[c];
+    for (int u = 0; u < 4; ++u)
+      if (c0 + u < ncols) C[r + (c0 + u) * ldc] -= acc[u];
   }
   __syncthreads();
 }
@@ -653,18 +657,42 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
           if (u < count) part[u] += xv[w] * col(cc0 + u * step)[r];
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int u = 0; u < kG; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
     S tw[kG];
+    if constexpr (kF32) {
 #pragma unroll
-    for (int u = 0; u < kG; ++u) tw[u] = u < count ? t * (head(c, cc0 + u * step) + part[u]) : S(0);
-    __syncwarp();
-    if (lane == 0) {
+      for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int u = 0; u < kG; ++u)
-        if (u < count) head(c, cc0 + u * step) -= tw[u];
+        for (int u = 0; u < kG; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+#pragma unroll
+      for (int u = 0; u < kG; ++u) tw[u] = u < count ? t * (head(c, cc0 + u * step) + part[u]) : S(0);
+      __syncwarp();
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < kG; ++u)
+          if (u < count) head(c, cc0 + u * step) -= tw[u];
+      }
+    } else {
+      // FP64: a reduce-scatter butterfly (six additions on the narrow FP64 pipe instead
+      // of twenty) leaves lane l with the whole sum of slot (l >> 3) & 3; the lanes of a
+      // slot form its t * w and lane 8u hands it to the warp.
+      const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+      S k0 = up16 ? part[2] : part[0], k1 = up16 ? part[3] : part[1];
+      const S o0 = up16 ? part[0] : part[2], o1 = up16 ? part[1] : part[3];
+      k0 += __shfl_xor_sync(0xffffffffu, o0, 16);
+      k1 += __shfl_xor_sync(0xffffffffu, o1, 16);
+      S k = up8 ? k1 : k0;
+      const S o2 = up8 ? k0 : k1;
+      k += __shfl_xor_sync(0xffffffffu, o2, 8);
+      k += __shfl_xor_sync(0xffffffffu, k, 4);
+      k += __shfl_xor_sync(0xffffffffu, k, 2);
+      k += __shfl_xor_sync(0xffffffffu, k, 1);
+      const int slot = (lane >> 3) & 3;
+      S mine = 0;
+      if (slot < count) mine = t * (head(c, cc0 + slot * step) + k);
+#pragma unroll
+      for (int u = 0; u < kG; ++u) tw[u] = __shfl_sync(0xffffffffu, mine, 8 * u);
+      __syncwarp();
+      if ((lane & 7) == 0 && slot < count) head(c, cc0 + slot * step) -= mine;
     }
 #pragma unroll
     for (int w = 0; w < kR; ++w) {
@@ -688,9 +716,12 @@ __device__ void panel_factor(Smem<S> &s, int kb, int rows, int c0, int mb) {
     const S sc = s.scal_s[c];
     if (warp == 0) {
       if (c + 1 < kb) update_and_reflect(c, t, sc);
-    } else if (t != S(0)) {
-      constexpr int kStep = kWarps - 1;
-      for (int cc0 = c + 1 + warp; cc0 < kb; cc0 += kG * kStep) {
+    } else if (t != S(0) && (kF32 || warp != kWarps / 2)) {
+      // FP64: warp kWarps/2 shares warp 0's scheduler (and its FP64 unit), so it stays
+      // out of the updates and the reflector chain runs alone there
+      constexpr int kStep = kF32 ? kWarps - 1 : kWarps - 2;
+      const int widx = (!kF32 && warp > kWarps / 2) ? warp - 1 : warp;
+      for (int cc0 = c + 1 + widx; cc0 < kb; cc0 += kG * kStep) {
         const int count = min(kG, (kb - 1 - cc0) / kStep + 1);
         update_group(c, cc0, kStep, count, t, sc);
       }
@@ -717,29 +748,26 @@ __device__ void panel_factor_dispatch(Smem<S> &s, int kb, int rows, int c0, int 
   }
 }
 
-// Gram matrix G(a, c) = v_a . v_c (all a, c < kb) of a panel block's reflectors, held
+// Gram matrix G(a, c) = v_a . v_c (a < c < kb) of a panel block's reflectors, held
 // explicitly in s.V (GEQRT: unit diagonal and zeros above written in; TT: zeros below
-// the triangle from the load).  Lane a and warp g form G(a, g + 8u), u < 4; column
-// indices beyond kb are clamped (their results are not stored) so the row loop has no
-// branches and unrolls.
+// the triangle from the load).  Only the strict upper triangle is formed - the T
+// recurrence reads nothing else - one pair per thread step, a fastest within a column c
+// (a warp's V(r, a) loads hit distinct banks, its V(r, c) loads broadcast); each sum runs
+// over the rows in order.
 template <typename S>
 __device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
-  const int a = threadIdx.x & 31, cg = threadIdx.x >> 5;
-  const S *va = s.V + min(a, kb - 1) * s.ldv;
-  const S *vc[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) vc[u] = s.V + min(cg + kWarps * u, kb - 1) * s.ldv;
-  S acc[4] = {0, 0, 0, 0};
+  const int npairs = kb * (kb - 1) / 2;
+  for (int idx = threadIdx.x; idx < npairs; idx += kThreads) {
+    // column c holds the pairs c (c - 1) / 2 .. c (c + 1) / 2 - 1
+    int c = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(idx))) * 0.5f);
+    while (c * (c - 1) / 2 > idx) --c;
+    while (c * (c + 1) / 2 <= idx) ++c;
+    const int a = idx - c * (c - 1) / 2;
+    const S *va = s.V + a * s.ldv, *vc = s.V + c * s.ldv;
+    S acc = 0;
 #pragma unroll 4
-  for (int r = 0; r < nrows; ++r) {
-    const S x = va[r];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] += x * vc[u][r];
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int c = cg + kWarps * u;
-    if (a < kb && c < kb) s.G[a + c * s.ldt] = acc[u];
+    for (int r = 0; r < nrows; ++r) acc += va[r] * vc[r];
+    s.G[a + c * s.ldt] = acc;
   }
   __syncthreads();
 }
@@ -754,6 +782,26 @@ __device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
 // reflector) gives a zero row and column, as the recurrence does.
 template <typename S>
 __device__ void build_t(Smem<S> &s, int kb) {
+  if constexpr (sizeof(S) == sizeof(double)) {
+    // FP64 (each FP64 instruction costs the whole warp many cycles on this GPU): warp w
+    // forms columns j = w, w + kWarps, ..., lane a holding row a's running sum; a step per
+    // k from j down gives x_k (tau_j, or -tau_k acc_k from lane k), broadcast, then acc_a
+    // += G(a, k) x_k for a < k - the same operations in the same order as the one-warp
+    // form below, spread over the warps by column.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < kb; j += kWarps) {
+      S acc = 0;
+      for (int k = j; k >= 0; --k) {
+        const S mine = k == j ? s.tau_s[j] : -s.tau_s[k] * acc;  // meaningful in lane k
+        const S xk = __shfl_sync(0xffffffffu, mine, k);
+        if (lane == k) s.T[k + j * s.ldt] = xk;
+        if (lane < k) acc += s.G[lane + k * s.ldt] * xk;
+      }
+      if (lane > j && lane < kb) s.T[lane + j * s.ldt] = S(0);
+    }
+    __syncthreads();
+    return;
+  }
   if (threadIdx.x < 32) {
     const int j = threadIdx.x;
     if (j < kb) {
@@ -1023,6 +1071,22 @@ __device__ bool wait_ready(const ExecParams &p, int t) {
   }
 }
 
+// Target tile column of an update task, and the columns c0 .. c0+ncols-1 of that tile it
+// updates: the whole tile, or column part task_part(j) of colw columns (ncols may be 0 at
+// the ragged edge of the matrix).
+__device__ __forceinline__ int update_columns(const ExecParams &q, int j, int &ncols, int &c0) {
+  const int jc = task_col(j, q.colparts);
+  const int tcols = static_cast<int>(lmin(q.nb, q.n - int64_t(jc) * q.nb));
+  if (q.colparts > 1) {
+    c0 = task_part(j, q.colparts) * q.colw;
+    ncols = max(0, min(q.colw, tcols - c0));
+  } else {
+    c0 = 0;
+    ncols = tcols;
+  }
+  return jc;
+}
+
 // L2 prefetch hints for the tiles task ta reads and writes (GEQRT: its tile; TTQRT: the
 // two triangles' tiles; UNMQR / TTMQR: the target tile(s)), one tile column per thread in
 // 128-byte lines.  Every hinted address is an element of the matrix.  A hint only moves
@@ -1046,8 +1110,8 @@ __device__ void prefetch_task_tiles(const ExecParams &p, int ta) {
   switch (task.kind) {
     case kGeqrt: nt = 1; break;
     case kTtqrt: case kTsqrt: nt = 2; break;
-    case kUnmqr: tcol = task.j; nt = 1; break;
-    case kTtmqr: case kTsmqr: tcol = task.j; nt = 2; break;
+    case kUnmqr: tcol = task_col(task.j, p.colparts); nt = 1; break;
+    case kTtmqr: case kTsmqr: tcol = task_col(task.j, p.colparts); nt = 2; break;
     default: return;
   }
   for (int w = threadIdx.x; w < nt * nb; w += kThreads) {
@@ -1190,9 +1254,11 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
           break;
         }
         Real *A = static_cast<Real *>(q.A);
-        const int ncols = static_cast<int>(lmin(nb, q.n - int64_t(task.j) * nb));
-        task_unmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.i, task.j), q.lda,
-                                  ncols, false);
+        int ncols, c0;
+        const int jc = update_columns(q, task.j, ncols, c0);
+        if (ncols > 0)
+          task_unmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.i, jc) + int64_t(c0) * q.lda,
+                                    q.lda, ncols, false);
         break;
       }
       case kTtmqr:
@@ -1203,10 +1269,12 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
           break;
         }
         Real *A = static_cast<Real *>(q.A);
-        const int ncols = static_cast<int>(lmin(nb, q.n - int64_t(task.j) * nb));
-        task_ttmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.piv, task.j),
-                                  tile_ptr(A, q.lda, nb, task.i, task.j), q.lda, ncols, false,
-                                  task.kind == kTsmqr);
+        int ncols, c0;
+        const int jc = update_columns(q, task.j, ncols, c0);
+        if (ncols > 0)
+          task_ttmqr<Real, S, Real>(q, s, task.i, task.k, tile_ptr(A, q.lda, nb, task.piv, jc) + int64_t(c0) * q.lda,
+                                    tile_ptr(A, q.lda, nb, task.i, jc) + int64_t(c0) * q.lda, q.lda, ncols, false,
+                                    task.kind == kTsmqr);
         break;
       }
       case kUnmqrB:

@@ -63,10 +63,14 @@ struct Regions {
     L(q, i, j);
     U(q, i, j);
   }
+  void cps(int q, int i, int j) {
+    for (int c = 0; c < kColParts; ++c) add(region_cp(q, i, j, c));
+  }
 };
 }  // namespace
 
-std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square, bool prep) {
+std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square, bool prep,
+                                 int colparts) {
   std::vector<int> geqrt_ids;
   for (int i = k; i < p; ++i) {
     if (square && square[i]) {
@@ -75,6 +79,7 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const cha
     }
     Regions w;
     w.tile(q, i, k);
+    if (colparts > 1) w.cps(q, i, k);
     geqrt_ids.push_back(b.add(Task{kGeqrt, i, -1, (int16_t)k, -1}, kWGeqrt, nullptr, 0, w.r, w.n));
     if (prep) {
       const int rd[1] = {region_L(q, i, k)};
@@ -83,6 +88,13 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const cha
     }
     for (int j = k + 1; j < q; ++j) {
       const int rd[2] = {region_L(q, i, k), region_ops(q, i, k, 0)};
+      if (colparts > 1) {
+        for (int c = 0; c < colparts; ++c) {
+          const int wr[1] = {region_cp(q, i, j, c)};
+          b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)(j | (c << kColShift))}, kWUnmqr, rd, 1, wr, 1);
+        }
+        continue;
+      }
       Regions wj;
       wj.tile(q, i, j);
       b.add(Task{kUnmqr, i, -1, (int16_t)k, (int16_t)j}, kWUnmqr, rd, prep ? 2 : 1, wj.r, wj.n);
@@ -92,7 +104,7 @@ std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const cha
 }
 
 void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square, bool prep,
-                    bool split) {
+                    bool split, int colparts) {
   for (const Elim &e : col) {
     const bool ts = square && square[e.i];
     if (split) {
@@ -116,6 +128,10 @@ void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col,
         w.tile(q, e.i, k);
       else
         w.U(q, e.i, k);
+      if (colparts > 1) {
+        w.cps(q, e.piv, k);
+        w.cps(q, e.i, k);
+      }
       b.add(Task{ts ? kTsqrt : kTtqrt, e.i, e.piv, (int16_t)k, -1}, ts ? kWTsqrt : kWTtqrt, nullptr, 0, w.r, w.n);
     }
     if (prep) {
@@ -135,6 +151,14 @@ void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col,
       else
         rd.U(q, e.i, k);
       if (prep) rd.add(region_ops(q, e.i, k, 1));
+      if (colparts > 1) {
+        for (int c = 0; c < colparts; ++c) {
+          const int wr[2] = {region_cp(q, e.piv, j, c), region_cp(q, e.i, j, c)};
+          b.add(Task{ts ? kTsmqr : kTtmqr, e.i, e.piv, (int16_t)k, (int16_t)(j | (c << kColShift))},
+                ts ? kWTsmqr : kWTtmqr, rd.r, rd.n, wr, 2);
+        }
+        continue;
+      }
       Regions w4;
       w4.tile(q, e.piv, j);
       w4.tile(q, e.i, j);
@@ -314,7 +338,7 @@ std::vector<std::vector<char>> ts_square_rows(int p, int q, const std::vector<El
 }
 
 void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts, bool prep,
-                        bool split) {
+                        bool split, int colparts) {
   const int kmax = std::min(p, q);
   std::vector<std::vector<Elim>> by_col(kmax);
   for (const Elim &e : elims) by_col[e.k].push_back(e);
@@ -322,15 +346,15 @@ void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &
   if (ts) square = ts_square_rows(p, q, elims);
   for (int k = 0; k < kmax; ++k) {
     const char *sq = ts ? square[k].data() : nullptr;
-    add_panel_tasks(b, p, q, k, sq, prep);
-    add_elim_tasks(b, q, k, by_col[k], sq, prep, split);
+    add_panel_tasks(b, p, q, k, sq, prep, colparts);
+    add_elim_tasks(b, q, k, by_col[k], sq, prep, split, colparts);
   }
 }
 
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g, int64_t drop_edge,
-                        const OrderSpec *order, bool ts, bool prep, bool split) {
+                        const OrderSpec *order, bool ts, bool prep, bool split, int colparts) {
   GraphBuilder b(p * q * kRegionsPerTile);
-  add_factor_program(b, p, q, elims, ts, prep, split);
+  add_factor_program(b, p, q, elims, ts, prep, split, colparts);
   finalize_graph(b, g, drop_edge, order);
 }
 

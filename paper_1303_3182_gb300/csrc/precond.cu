@@ -73,7 +73,8 @@ __global__ void big_init_kernel(int64_t n, const double *Dinv64, double *Y, int 
 // One doubling step at half-width h for every pair of every big block, in two products:
 //   stage 0: Tmp = Y11 R12        stage 1: Y12 = -Tmp Y22
 // Y11 = Y[s](p, p), Y22 = Y[s](p+h, p+h) (h x h, already inverses), R12 = R(p, p+h) of
-// big block s (zero beyond n), p = 2 h q.  64 x 64 output tile per CTA, 4 x 4 per thread.
+// big block s (zero beyond n), p = 2 h q.  64 x 64 output tile per CTA, 4 x 4 per thread;
+// the k range stops at the triangle of the inverse factor.
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *R, int64_t ldr, double *Y,
                                                          double *Tmp, int h, int stage) {
@@ -89,7 +90,11 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < h; k0 += 32) {
+  // both factors with an inverse are upper triangular: Y11(row, k) = 0 for k < row (stage
+  // 0) and Y22(k, col) = 0 for k > col (stage 1), so those k-tiles are skipped
+  const int k_lo = stage == 0 ? tr * 64 : 0;
+  const int k_hi = stage == 0 ? h : (tc * 64 + 64 < h ? tc * 64 + 64 : h);
+  for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
     // A tile: 64 rows x 32 k;  B tile: 32 k x 64 cols
     for (int idx = tid; idx < 64 * 32; idx += kThreads) {
       const int kk = idx / 64, r = idx % 64;

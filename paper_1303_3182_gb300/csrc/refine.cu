@@ -48,15 +48,6 @@ __device__ double block_sum(double v) {
   return s;
 }
 
-__global__ void f64_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n) {
-  const int64_t total = m * n;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t j = idx / m, i = idx - j * m;
-    F[i + j * ldf] = static_cast<float>(A[i + j * lda]);
-  }
-}
-
 // Y(:, r) = sy(r) * Y(:, r) + A X(:, r)  for r < nrhs, rows [row0, row0 + 256) of this CTA,
 // columns [c0, c1) of A; partial sums are added atomically.  sy(r) is applied by the CTAs
 // of the first column chunk only.  ssq(r) += ||Y(:, r)||^2 is NOT formed here.
@@ -129,16 +120,34 @@ __device__ __forceinline__ DF df_sum(DF a, DF b) {
   return DF{t, a.lo + b.lo + err};
 }
 
-// P(i, j) = (hi, lo) split of A(i, j) (column-major, ld m).
-__global__ void split_pairs(int64_t m, int64_t n, const double *A, int64_t lda, float2 *P) {
-  const int64_t total = m * n;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t j = idx / m, i = idx - j * m;
-    const double a = A[i + j * lda];
-    const float hi = static_cast<float>(a);
-    P[idx] = make_float2(hi, static_cast<float>(a - static_cast<double>(hi)));
+// One pass over A before the factorization: F = fl32(A) (the matrix the tensor-core
+// factorization overwrites), P = A as FP32 pairs (column-major, ld m; hi is F's value, lo
+// the FP32 rounding of a - hi) and ||A||_F^2 added to *anorm2 in FP64.  Four columns per
+// thread step, so that four loads are in flight before the first store.
+__global__ void __launch_bounds__(kT) prepare_a(int64_t m, int64_t n, const double *__restrict__ A, int64_t lda,
+                                                float *__restrict__ F, int64_t ldf, float2 *__restrict__ P,
+                                                double *anorm2) {
+  double s = 0.0;
+  const int64_t i0 = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x;
+  const int64_t istep = static_cast<int64_t>(gridDim.x) * kT;
+  for (int64_t j0 = static_cast<int64_t>(blockIdx.y) * 4; j0 < n; j0 += static_cast<int64_t>(gridDim.y) * 4) {
+    for (int64_t i = i0; i < m; i += istep) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = j0 + u < n ? A[i + (j0 + u) * lda] : 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (j0 + u < n) {
+          const float hi = static_cast<float>(v[u]);
+          F[i + (j0 + u) * ldf] = hi;
+          P[i + (j0 + u) * m] = make_float2(hi, static_cast<float>(v[u] - static_cast<double>(hi)));
+          s = fma(v[u], v[u], s);
+        }
+      }
+    }
   }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(anorm2, s);
 }
 
 // Xp(:, r) = pair split of X(:, r), r < nrhs.
@@ -152,58 +161,77 @@ __global__ void split_vec(int64_t len, const double *X, int64_t ldx, float2 *Xp,
   }
 }
 
-// Y(:, r) += A X(:, r) with A and X as pairs (rows of this CTA, columns [c0, c1)).
-__global__ void gemv_n_pairs(int64_t m, int64_t n, const float2 *P, const float2 *Xp, double *Y, int64_t ldy,
-                             int nrhs, int64_t chunk) {
+// Y(:, r) += A X(:, r) with A and X as pairs (rows of this CTA, columns [c0, c1)); four
+// columns per step with their own accumulators, so that four loads of A are in flight.
+__global__ void __launch_bounds__(kT) gemv_n_pairs(int64_t m, int64_t n, const float2 *__restrict__ P,
+                                                   const float2 *__restrict__ Xp, double *Y, int64_t ldy, int nrhs,
+                                                   int64_t chunk) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x;
   const int64_t c0 = blockIdx.y * chunk, c1 = c0 + chunk < n ? c0 + chunk : n;
   if (i >= m) return;
   for (int r = 0; r < nrhs; ++r) {
     const float2 *x = Xp + r * n;
-    DF s0{0.f, 0.f}, s1{0.f, 0.f};
+    DF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     int64_t j = c0;
-    for (; j + 2 <= c1; j += 2) {
-      const float2 a0 = P[i + j * m], a1 = P[i + (j + 1) * m];
-      const float2 x0 = x[j], x1 = x[j + 1];
-      df_acc(s0, a0.x, a0.y, x0.x, x0.y);
-      df_acc(s1, a1.x, a1.y, x1.x, x1.y);
+    for (; j + 4 <= c1; j += 4) {
+      float2 a[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = P[i + (j + u) * m];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = x[j + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df_acc(s[u], a[u].x, a[u].y, xv[u].x, xv[u].y);
     }
     for (; j < c1; ++j) {
       const float2 a0 = P[i + j * m], x0 = x[j];
-      df_acc(s0, a0.x, a0.y, x0.x, x0.y);
+      df_acc(s[0], a0.x, a0.y, x0.x, x0.y);
     }
-    const DF s = df_sum(s0, s1);
-    atomicAdd(Y + i + r * ldy, static_cast<double>(s.hi) + static_cast<double>(s.lo));
+    const DF t = df_sum(df_sum(s[0], s[1]), df_sum(s[2], s[3]));
+    atomicAdd(Y + i + r * ldy, static_cast<double>(t.hi) + static_cast<double>(t.lo));
   }
 }
 
 // Y(j, r) = scale(r) sum_i A(i, j) U(i, r) with A and U as pairs: one warp per column j.
-__global__ void gemv_t_pairs(int64_t m, int64_t n, const float2 *P, const float2 *Up, double *Y, int64_t ldy,
-                             int nrhs, const double *scale) {
+// vec (m even, pair arrays 16-byte aligned): each lane reads two rows as one float4, four
+// float4 of A and of U per step (256 rows per warp step); else one row per lane and load.
+__global__ void __launch_bounds__(kT) gemv_t_pairs(int64_t m, int64_t n, const float2 *__restrict__ P,
+                                                   const float2 *__restrict__ Up, double *Y, int64_t ldy, int nrhs,
+                                                   const double *scale, int vec) {
   const int warp = (blockIdx.x * kT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const float2 *col = P + static_cast<int64_t>(warp) * m;
   for (int r = 0; r < nrhs; ++r) {
     const float2 *u = Up + r * m;
-    DF s0{0.f, 0.f}, s1{0.f, 0.f};
-    int64_t i = lane;
-    for (; i + 32 < m; i += 64) {
-      const float2 a0 = col[i], a1 = col[i + 32], u0 = u[i], u1 = u[i + 32];
-      df_acc(s0, a0.x, a0.y, u0.x, u0.y);
-      df_acc(s1, a1.x, a1.y, u1.x, u1.y);
+    DF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int64_t i = 0;
+    if (vec) {
+      const float4 *c4 = reinterpret_cast<const float4 *>(col);
+      const float4 *u4 = reinterpret_cast<const float4 *>(u);
+      for (; i + 256 <= m; i += 256) {
+        float4 a[4], w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = c4[(i >> 1) + 32 * q + lane];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = u4[(i >> 1) + 32 * q + lane];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          df_acc(s[q], a[q].x, a[q].y, w[q].x, w[q].y);
+          df_acc(s[q], a[q].z, a[q].w, w[q].z, w[q].w);
+        }
+      }
     }
-    for (; i < m; i += 32) {
+    for (i += lane; i < m; i += 32) {
       const float2 a0 = col[i], u0 = u[i];
-      df_acc(s0, a0.x, a0.y, u0.x, u0.y);
+      df_acc(s[0], a0.x, a0.y, u0.x, u0.y);
     }
-    DF s = df_sum(s0, s1);
+    DF t = df_sum(df_sum(s[0], s[1]), df_sum(s[2], s[3]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const DF t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
-      s = df_sum(s, t);
+      const DF v{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+      t = df_sum(t, v);
     }
     if (lane == 0)
-      Y[warp + r * ldy] = (static_cast<double>(s.hi) + static_cast<double>(s.lo)) * (scale ? scale[r] : 1.0);
+      Y[warp + r * ldy] = (static_cast<double>(t.hi) + static_cast<double>(t.lo)) * (scale ? scale[r] : 1.0);
   }
 }
 
@@ -334,20 +362,6 @@ __global__ void add_into(int64_t n, double *X, int64_t ldx, const double *D, int
     X[i + r * ldx] += D[i + r * ldd];
 }
 
-// out += sum of squares of an m x n column-major matrix
-__global__ void fro_norm2(int64_t m, int64_t n, const double *A, int64_t lda, double *out) {
-  double s = 0.0;
-  const int64_t total = m * n;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * kT) {
-    const int64_t j = idx / m, i = idx - j * m;
-    const double v = A[i + j * lda];
-    s += v * v;
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) atomicAdd(out, s);
-}
-
 // D(:, r) = f * S(:, r)
 __global__ void copy_scaled(int64_t n, double *D, int64_t ldd, const double *S, int64_t lds, double f, int nrhs) {
   const int r = blockIdx.y;
@@ -364,29 +378,61 @@ dim3 vgrid(int64_t len, int nrhs) {
 
 }  // namespace
 
+// Workspace (doubles).  Fixed part, set up once per least-squares call: ||A||_F^2 (padded to
+// two), A as FP32 pairs (one double's worth per entry), the inverses of R's 64 x 64
+// diagonal blocks and the preconditioner's set-up.  Per block of right-hand sides: U (m)
+// and V, W, Y, Z, Tt (n) per right-hand side, the scalar arrays, two LSQR state sets, and
+// the pair splits of one n- and one m-vector per right-hand side (16-byte aligned).
+namespace {
+struct FixedLayout {
+  double *anorm2;
+  float2 *Apair;
+  double *Dinv, *Pw;
+  double *end;
+};
+FixedLayout fixed_layout(int64_t m, int64_t n, double *work) {
+  FixedLayout l;
+  l.anorm2 = work;
+  l.Apair = reinterpret_cast<float2 *>(work + 2);
+  l.Dinv = work + 2 + static_cast<size_t>(m) * n;
+  l.Pw = l.Dinv + static_cast<size_t>((n + 63) / 64) * 64 * 64;
+  l.end = l.Pw + precond_work_doubles(n, false);
+  return l;
+}
+size_t even(size_t x) { return (x + 1) & ~static_cast<size_t>(1); }
+}  // namespace
+
 size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs) {
-  // U (m) and V, W, Y, Z, Tt (n) per right-hand side, five scalar arrays, ||A||_F^2, two
-  // LSQR state sets, and the inverses of R's 64 x 64 diagonal blocks
-  // plus A as FP32 pairs (one double's worth per entry) and the pair splits of one m- and
-  // one n-vector per right-hand side, for the inner products
   const size_t nblk = static_cast<size_t>((n + 63) / 64);
-  return static_cast<size_t>(nrhs) * (m + 5 * n) + 5 * static_cast<size_t>(nrhs) + 2 +
-         2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) + 8 + nblk * 64 * 64 +
-         2 * static_cast<size_t>(nrhs) + precond_work_doubles(n, false) + static_cast<size_t>(m) * n +
-         static_cast<size_t>(nrhs) * (m + n) + 2;
+  const size_t fixed = 2 + static_cast<size_t>(m) * n + nblk * 64 * 64 + precond_work_doubles(n, false);
+  const size_t per = static_cast<size_t>(nrhs) * (m + 5 * n) + 8 * static_cast<size_t>(nrhs) + 8 +
+                     2 * (sizeof(LsqrScalars) / sizeof(double)) * static_cast<size_t>(nrhs) +
+                     static_cast<size_t>(nrhs) * (m + n) + 8;
+  return fixed + per;
 }
 
-int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream) {
-  f64_to_f32<<<1216, kT, 0, static_cast<cudaStream_t>(stream)>>>(A, lda, F, ldf, m, n);
+int lsqr_prepare(int64_t m, int64_t n, const double *A, int64_t lda, float *F, int64_t ldf, double *work,
+                 void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const FixedLayout fl = fixed_layout(m, n, work);
+  cudaError_t e = cudaMemsetAsync(fl.anorm2, 0, sizeof(double), st);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  const int64_t gx = (m + kT - 1) / kT;
+  const int64_t gy = (n + 3) / 4;
+  const dim3 grid(static_cast<unsigned>(gx < 128 ? gx : 128), static_cast<unsigned>(gy < 64 ? gy : 64));
+  prepare_a<<<grid, kT, 0, st>>>(m, n, A, lda, F, ldf, fl.Apair, fl.anorm2);
   count_launch();
   return static_cast<int>(cudaGetLastError());
 }
 
 int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, const float *R, int64_t ldr,
                 const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter, int *iters_out,
-                double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream) {
+                bool setup, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  double *U = work;
+  const FixedLayout fl = fixed_layout(m, n, work);
+  const float2 *Apair = fl.Apair;
+  double *Dinv = fl.Dinv, *Pw = fl.Pw;
+  double *U = fl.end;
   double *V = U + static_cast<size_t>(m) * nrhs;
   double *W = V + static_cast<size_t>(n) * nrhs;
   double *Y = W + static_cast<size_t>(n) * nrhs;
@@ -396,17 +442,16 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
   double *ssq_b = ssq_a + nrhs;                         // [nrhs]
   double *inv_b = ssq_b + nrhs;                         // [nrhs]
   double *betas = inv_b + nrhs;                         // [nrhs]
-  double *anorm2 = betas + nrhs;                        // [1]  ||A||_F^2
+  double *anorm2 = betas + nrhs;                        // [1]  ||A||_F^2 (copied from the fixed part)
   double *eta2 = anorm2 + 1;                            // [nrhs] ||A^T u||^2, u = r / ||r||
   LsqrScalars *sc = reinterpret_cast<LsqrScalars *>(eta2 + nrhs + ((nrhs + 1) & 1));  // [2][nrhs]
-  double *Dinv = reinterpret_cast<double *>(sc + 2 * nrhs) + 4;                 // [nblk][64][64]
-  double *bn2 = Dinv + static_cast<size_t>((n + 63) / 64) * 64 * 64;               // [nrhs] ||b||^2
+  double *bn2 = reinterpret_cast<double *>(sc + 2 * nrhs);                         // [nrhs] ||b||^2
   double *xn2 = bn2 + nrhs;                                                       // [nrhs] ||x||^2
-  double *Pw = xn2 + nrhs;                                                        // preconditioner solves
-  // A as FP32 pairs and the pair splits of the inner products' vectors (8-byte aligned)
-  float2 *Apair = reinterpret_cast<float2 *>(Pw + precond_work_doubles(n, false));
-  float2 *Vpair = Apair + static_cast<size_t>(m) * n;   // n x nrhs
-  float2 *Upair = Vpair + static_cast<size_t>(n) * nrhs;  // m x nrhs
+  // the pair splits of the inner products' vectors, 16-byte aligned for float4 loads
+  const size_t pv = even(static_cast<size_t>((xn2 + nrhs) - work));
+  float2 *Vpair = reinterpret_cast<float2 *>(work + pv);                           // n x nrhs
+  float2 *Upair = reinterpret_cast<float2 *>(work + even(pv + static_cast<size_t>(n) * nrhs));  // m x nrhs
+  const int vec = (m % 2 == 0) ? 1 : 0;
   const int64_t chunk = 512;
   const dim3 ggrid(static_cast<unsigned>((m + kT - 1) / kT), static_cast<unsigned>((n + chunk - 1) / chunk));
   const unsigned tgrid = static_cast<unsigned>((n * 32 + kT - 1) / kT);
@@ -423,13 +468,11 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
     e = cudaGetLastError();                             \
     if (e != cudaSuccess) return static_cast<int>(e);   \
   } while (0)
-  TQR_CK(cudaMemsetAsync(anorm2, 0, sizeof(double), st));
-  fro_norm2<<<1216, kT, 0, st>>>(m, n, A, lda, anorm2);
-  TQR_CKL();
-  split_pairs<<<1216, kT, 0, st>>>(m, n, A, lda, Apair);
-  TQR_CKL();
-  if ((rc = launch_diag_inverse(n, R, ldr, false, Dinv, stream)) != 0) return rc;
-  if ((rc = precond_setup(n, R, ldr, false, Dinv, Pw, stream)) != 0) return rc;
+  TQR_CK(cudaMemcpyAsync(anorm2, fl.anorm2, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (setup) {
+    if ((rc = launch_diag_inverse(n, R, ldr, false, Dinv, stream)) != 0) return rc;
+    if ((rc = precond_setup(n, R, ldr, false, Dinv, Pw, stream)) != 0) return rc;
+  }
   // R^{-1} and R^{-T} applied with the inverses of R's 1024 x 1024 diagonal blocks
   auto solve_r = [&](double *Vec, bool lower_t) -> int {
     return precond_solve(n, R, ldr, false, Pw, Vec, n, nrhs, flags, status, wait_limit_ns, stream, lower_t);
@@ -528,7 +571,7 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
       TQR_CKL();
       split_vec<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, Upair, nrhs);
       TQR_CKL();
-      gemv_t_pairs<<<tgrid, kT, 0, st>>>(m, n, Apair, Upair, Z, n, nrhs, inv_b);
+      gemv_t_pairs<<<tgrid, kT, 0, st>>>(m, n, Apair, Upair, Z, n, nrhs, inv_b, vec);
       TQR_CKL();
       if ((rc = solve_r(Z, true)) != 0) return rc;
       axpy_norm<<<vgrid(n, nrhs), kT, 0, st>>>(n, Z, n, V, n, betas, ssq_a, nrhs);

@@ -57,6 +57,19 @@ enum TaskKind : int32_t {
 constexpr int kNumKinds = 13;
 constexpr int kPanelSplits = 4;     // 32-column blocks of a 128-column tile
 constexpr int kPanelSplitCols = 32;
+// Column parts of a small SIMT factorization: each update task (UNMQR, TTMQR, TSMQR)
+// becomes kColParts tasks on column slices of its target tile(s), so that the updates on
+// the critical path of a graph with fewer tasks than the GPU has SMs run on several SMs.
+// The part travels in bits 12.. of Task::j (target column < 4096 then).
+constexpr int kColParts = 4;
+constexpr int kColShift = 12;
+#ifdef __CUDACC__
+#define TQR_HOST_DEVICE __host__ __device__
+#else
+#define TQR_HOST_DEVICE
+#endif
+inline TQR_HOST_DEVICE int task_col(int j, int colparts) { return colparts > 1 ? (j & ((1 << kColShift) - 1)) : j; }
+inline TQR_HOST_DEVICE int task_part(int j, int colparts) { return colparts > 1 ? (j >> kColShift) : 0; }
 
 // A task as the device executor reads it (16 bytes).
 struct Task {
@@ -108,26 +121,31 @@ struct GraphBuilder {
 
 // Tile regions of the factorization graph: each tile (i,j) has a strictly-lower part
 // (GEQRT reflectors), an upper part (R, then TTQRT reflectors) kept as kPanelSplits row
-// blocks (a split panel task writes one row block of its pivot's R), and two operand-image
-// slots (tensor-core precisions: GEQRT's and the TT/TS elimination's images).  A task that
-// touches the upper part as a whole touches all of its row blocks.
-constexpr int kRegionsPerTile = 3 + kPanelSplits;
+// blocks (a split panel task writes one row block of its pivot's R), two operand-image
+// slots (tensor-core precisions: GEQRT's and the TT/TS elimination's images) and
+// kColParts column slices (written by column-part updates; a panel task on the tile
+// writes them all).  A task that touches the upper part as a whole touches all of its row
+// blocks.
+constexpr int kRegionsPerTile = 3 + kPanelSplits + kColParts;
 inline int region_L(int q, int i, int j) { return (i * q + j) * kRegionsPerTile; }
 inline int region_Ub(int q, int i, int j, int b) { return (i * q + j) * kRegionsPerTile + 1 + b; }
 inline int region_ops(int q, int i, int j, int which) {
   return (i * q + j) * kRegionsPerTile + 1 + kPanelSplits + which;
 }
+inline int region_cp(int q, int i, int j, int c) { return (i * q + j) * kRegionsPerTile + 3 + kPanelSplits + c; }
 // Adds GEQRT(i,k) and UNMQR(i,k,j) for every row i >= k of panel k except the rows with
 // square[i] != 0 (zeroed by TS kernels); returns the task ids of the GEQRTs (index i - k,
 // -1 for a skipped row).  prep: a PREP_G(i,k) task after each GEQRT writes its operand
 // images, which the UNMQRs read.
+// colparts > 1: each UNMQR as colparts column-part tasks (part in bits kColShift.. of j).
 std::vector<int> add_panel_tasks(GraphBuilder &b, int p, int q, int k, const char *square = nullptr,
-                                 bool prep = false);
+                                 bool prep = false, int colparts = 1);
 // Adds the eliminations of panel k in order: TSQRT / TSMQR(i,piv,k,j) when square[i] != 0,
 // TTQRT / TTMQR(i,piv,k,j) otherwise; prep: a PREP_T(i,k) task after each TTQRT / TSQRT;
-// split: each TTQRT / TSQRT as kPanelSplits block tasks (kTtqrtS / kTsqrtS, block in j).
+// split: each TTQRT / TSQRT as kPanelSplits block tasks (kTtqrtS / kTsqrtS, block in j);
+// colparts > 1: each TTMQR / TSMQR as colparts column-part tasks.
 void add_elim_tasks(GraphBuilder &b, int q, int k, const std::vector<Elim> &col, const char *square = nullptr,
-                    bool prep = false, bool split = false);
+                    bool prep = false, bool split = false, int colparts = 1);
 // Orders a built graph for the executor (earliest start, then longest remaining path)
 // and fills the successor CSR.
 // Executor (claim) order of a factorization graph.  mode 0: earliest start with
@@ -146,7 +164,7 @@ void finalize_graph(GraphBuilder &b, Graph &g, int64_t drop_edge = -1, const Ord
 // Tasks of the sequential program (all panels, in column order) added to b; ts: the TS
 // form of the list.
 void add_factor_program(GraphBuilder &b, int p, int q, const std::vector<Elim> &elims, bool ts = false,
-                        bool prep = false, bool split = false);
+                        bool prep = false, bool split = false, int colparts = 1);
 // Backflow priorities (a task's weight plus the largest priority of its successors) of
 // a graph in program order with successor lists succ and weights w.
 std::vector<int64_t> backflow_priorities(const std::vector<std::vector<int32_t>> &succ,
@@ -166,10 +184,11 @@ int64_t alap_derived_bound(const std::vector<int64_t> &w, const std::vector<int6
 // (column-by-column program of Algorithm "elimTR"; dependencies from the tile regions
 // each kernel reads and writes, Eq. ttdeps / ttdeps2).
 // prep: the tensor-core form, with operand-image preparation tasks (PREP_G / PREP_T);
-// split: its TTQRT / TSQRT split into 32-column block tasks.
+// split: its TTQRT / TSQRT split into 32-column block tasks; colparts > 1: its update
+// tasks split into column parts (SIMT executors).
 void build_factor_graph(int p, int q, const std::vector<Elim> &elims, Graph &g,
                         int64_t drop_edge = -1, const OrderSpec *order = nullptr, bool ts = false,
-                        bool prep = false, bool split = false);
+                        bool prep = false, bool split = false, int colparts = 1);
 // Builds the graph that applies Q^T (or Q when reverse) to a right-hand-side block.
 void build_applyq_graph(int p, int q, const std::vector<Elim> &elims, bool reverse, Graph &g, bool ts = false);
 
@@ -209,6 +228,8 @@ struct ExecParams {
   int vec4;              // A is 16-byte aligned with lda % 4 == 0 (vector loads allowed)
   int cplx;              // 1: double-complex storage (the complex executor runs the graph)
   int64_t *trace;        // optional: per task {claim, start, end, sm} globaltimer stamps
+  int colparts;          // > 1: update tasks cover column part task_part(j) of colw columns
+  int colw;
   // batched factorization: per-task matrix index and per-matrix geometry (else null)
   const int32_t *mat_of;
   const BatchMat *mats;
@@ -284,13 +305,17 @@ int precond_solve(int64_t n, const void *R, int64_t ldr, bool real_is_double, co
 
 // LSQR refinement (refine.cu): X (in: x0, out: refined) for min ||A X - B||, operator
 // A R^{-1} with the FP32 R of a tensor-core factorization.  work: lsqr_work_doubles()
-// doubles; flags: trsm_flag_count(n) int32; status: device status word.
+// doubles (16-byte aligned); flags: trsm_flag_count(n) int32; status: device status word.
+// lsqr_prepare runs once per least-squares call, before the factorization: F = fl32(A)
+// (ld ldf, the matrix to factor), and A's FP32 pairs and ||A||_F^2 into work.  setup:
+// build the preconditioner from R (the first block of right-hand sides; later blocks
+// reuse it).
 size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs);
+int lsqr_prepare(int64_t m, int64_t n, const double *A, int64_t lda, float *F, int64_t ldf, double *work,
+                 void *stream);
 int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, const float *R, int64_t ldr,
                 const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter,
-                int *iters_out, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
+                int *iters_out, bool setup, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
                 void *stream);
-// FP64 -> FP32 copy of an m x n matrix (column-major).
-int convert_to_f32(const double *A, int64_t lda, float *F, int64_t ldf, int64_t m, int64_t n, void *stream);
 
 }  // namespace tqr

@@ -305,3 +305,31 @@ def test_bounded_claim_order_gives_identical_factors(prec, nb, ib, m, n):
     for Ad, T in out[1:]:
         assert torch.equal(Ad, out[0][0])
         assert torch.equal(T, out[0][1])
+
+
+@pytest.mark.parametrize("prec,m,n,nb,ib,tree", [("fp64", 512, 128, 64, 16, "greedy"),
+                                                 ("fp64", 1000, 300, 64, 16, "plasma-ts"),
+                                                 ("fp64", 1000, 520, 256, 32, "plasma-ts"),
+                                                 ("fp64", 200, 140, 48, 20, "fibonacci"),
+                                                 ("fp32", 300, 200, 32, 8, "flat"),
+                                                 ("fp32", 640, 320, 128, 32, "greedy-ts")])
+def test_column_parts_bitwise_and_parity(prec, m, n, nb, ib, tree):
+    """Update tasks split into column parts (tqr_set_column_parts): every column of a
+    target tile gets the arithmetic of the whole-tile task, so R, the reflectors and T are
+    bitwise those of the unsplit graph, and both match the oracle."""
+    A = synthetic.gaussian(m, n, seed=1303318209 + m)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    out = []
+    try:
+        for mode in (0, 2):
+            tqr.set_column_parts(mode)
+            Ad = to_dev(A, dtype)
+            T = torch.zeros(tqr.workspace_size(m, n, nb, ib, prec), dtype=torch.uint8, device="cuda")
+            tqr.factor(Ad, nb, ib, tree, 2, prec, T=T)
+            torch.cuda.synchronize()
+            out.append((Ad.cpu(), T.cpu()))
+        compare_factor(A, nb, ib, tree, prec=prec)
+    finally:
+        tqr.set_column_parts(1)
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])

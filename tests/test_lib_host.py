@@ -106,6 +106,8 @@ def test_invalid_arguments():
     assert L.tqr_factor(8, 4, 4, 2, 4, 1, 0, vp(8), 8, None, None) == -10
     assert L.tqr_trsm(0, 0, vp(8), 1, vp(8), 1, 1, None) == -1
     assert L.tqr_strerror(3) == b"device dependency wait exceeded the limit"
+    assert L.tqr_set_column_parts(3) == -1 and L.tqr_set_column_parts(-1) == -1
+    assert L.tqr_set_column_parts(1) == 0
 
 
 def test_workspace_and_flops():
