@@ -694,7 +694,8 @@ def main_gpu(args):
                      "minimal_bytes_note": "A (FP32) read and written once plus the T factors (2 p q ib nb "
                                            "FP32) - the least traffic any tiled QR of this shape needs",
                      "traffic_over_minimal": flops * MIXED_TRAFFIC_PER_FLOP / minimal_bytes(args),
-                     "traffic_over_tile_task": flops * MIXED_TRAFFIC_PER_FLOP / tile_task_bytes(args)},
+                     "traffic_over_tile_task": flops * MIXED_TRAFFIC_PER_FLOP / tile_task_bytes(args),
+                     "tensor_issued": tensor_issued(args, fac_avg, bf16_sust)},
         "ls_optimality": {"mixed": eta_mixed, "fp64": eta64, "target": tol},
         "refinement_iterations": iters,
         "fp64": {"value": flops / (fp64_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": fp64_ms,
@@ -720,6 +721,20 @@ def main_gpu(args):
     if rank == 0:
         print(json.dumps(line))
     replicas.finalize()
+
+
+def tensor_issued(args, launch_ms, peak):
+    """The MMA work the tensor-core update tasks issue per factorization: 2 (UNMQR) or 3
+    (TTMQR / TSMQR) 128 x 128 x 128 products per task, each made of 1 (bf16, fp16), 3
+    (split x3) or 6 (split x6) part products - the tensor pipe's load, as against the
+    nominal flops, which count the method's arithmetic once."""
+    import paper_1303_3182_gb300 as tqr
+    parts = {"bf16": 1, "fp16": 1, "bf16x3": 3, "bf16x6": 6}[args.prec]
+    c = tqr.plan_counts(args.m, args.n, 128, args.tree, args.bs)
+    f = (2 * c["UNMQR"] + 3 * (c["TTMQR"] + c["TSMQR"])) * parts * 2.0 * 128 ** 3
+    tf = f / (launch_ms * 1e-3) / 1e12
+    return {"flops_per_launch": f, "achieved": tf, "frac": tf / peak, "unit": "TFLOP/s",
+            "note": "MMA flops issued by the update tasks (products x part products) per executor launch"}
 
 
 def minimal_bytes(args, nb=128, ib=32, esz=4):

@@ -150,6 +150,11 @@ int tqr_set_claim_order(int mode, const int64_t *weights);
 /* tqr_set_claim_order with six weights (GEQRT, TTQRT, UNMQR, TTMQR, TSQRT, TSMQR) for
  * mode 1 (NULL = 4, 2, 6, 6, 6, 12).  Errors as tqr_set_claim_order. */
 int tqr_set_claim_order_ts(int mode, const int64_t *weights);
+/* tqr_set_claim_order with the nine weights of the tensor-core task graph (GEQRT, TTQRT,
+ * UNMQR, TTMQR, TSQRT, TSMQR, operand-image preparation, 32-column TTQRT block, TSQRT
+ * block; the weights of tqr_schedule_ts) for mode 1 (NULL = the built-in tensor-core
+ * weights).  Errors as tqr_set_claim_order. */
+int tqr_set_claim_order_tc(int mode, const int64_t *weights);
 /* Column parts of later TQR_FP64 / TQR_FP32 factorization plans.  The critical path of a
  * small task graph (Section 3.2: the lower bound on its execution time however many
  * cores run it) is a chain of panel and update kernels; with column parts each update
@@ -436,6 +441,11 @@ int tqr_plan_stats(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[6
  *   #UNMQR, #TTMQR, #TSQRT, #TSMQR, #edges, critical path (tree may carry TQR_TS). */
 int tqr_plan_counts(int64_t m, int64_t n, int nb, int tree, int bs, int64_t out[8]);
 void tqr_debug_drop_edge(int64_t e);
+/* tqr_debug_split_pairs: the FP32 pair split of the least-squares refinement (hi = the
+ *   FP32 rounding of x, lo = the FP32 rounding of x - hi; integer instructions on the
+ *   device) run on the host for n values: host arrays x (in), hi, lo (out).  Host only.
+ *   Errors: -1 n < 0, -2 a NULL array with n > 0. */
+int tqr_debug_split_pairs(int64_t n, const double *x, float *hi, float *lo);
 int tqr_debug_claim_order(int p, int q, int tree, int bs, int mode, int nproc, const int64_t *weights,
                           int32_t *tasks, int64_t *ntask);
 

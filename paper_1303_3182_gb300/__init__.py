@@ -55,6 +55,7 @@ def lib() -> ctypes.CDLL:
             "tqr_set_claim_order": (i32, [i32, c_i64p]),
             "tqr_set_claim_order_ts": (i32, [i32, c_i64p]),
             "tqr_set_column_parts": (i32, [i32]),
+            "tqr_set_claim_order_tc": (i32, [i32, c_i64p]),
             "tqr_schedule_ts": (i32, [i32, i32, i32, i32, i32, c_i64p, c_i64p, c_i64p, c_i64p]),
             "tqr_debug_claim_order": (i32, [i32, i32, i32, i32, i32, i32, c_i64p, ctypes.POINTER(ctypes.c_int32),
                                              c_i64p]),
@@ -192,9 +193,12 @@ def schedule(p: int, q: int, tree="greedy", bs: int = 1, nproc: int = 1, weights
 def set_claim_order(mode: int, weights=None) -> None:
     """Executor claim order of later factorization plans: 0 = earliest start on unbounded
     processors, 1 = start order of the bounded-processor CP-method schedule with the given
-    kernel weights (GEQRT, TTQRT, UNMQR, TTMQR[, TSQRT, TSMQR]), 2 = the default (1 with
+    kernel weights (GEQRT, TTQRT, UNMQR, TTMQR[, TSQRT, TSMQR[, preparation, TTQRT block,
+    TSQRT block]]), 2 = the default (1 with
     built-in GB300 weights for the tensor-core precisions and fp64, 0 for fp32)."""
-    if weights is not None and len(weights) == 6:
+    if weights is not None and len(weights) == 9:
+        _check("tqr_set_claim_order_tc", lib().tqr_set_claim_order_tc(mode, _weights4(weights)))
+    elif weights is not None and len(weights) == 6:
         _check("tqr_set_claim_order_ts", lib().tqr_set_claim_order_ts(mode, _weights4(weights)))
     else:
         _check("tqr_set_claim_order", lib().tqr_set_claim_order(mode, _weights4(weights)))

@@ -513,6 +513,28 @@ int tqr_set_claim_order_ts(int mode, const int64_t *weights) {
   return set_claim_order_impl(mode, w);
 }
 
+int tqr_debug_split_pairs(int64_t n, const double *x, float *hi, float *lo) {
+  if (n < 0) return -1;
+  if (n > 0 && (!x || !hi || !lo)) return -2;
+  for (int64_t i = 0; i < n; ++i) split_pair(x[i], hi[i], lo[i]);
+  return TQR_OK;
+}
+
+int tqr_set_claim_order_tc(int mode, const int64_t *weights) {
+  if (mode < 0 || mode > 2) return -1;
+  int64_t w[kNumKinds];
+  for (int c = 0; c < kNumKinds; ++c) w[c] = kTensorOrderWeights[c];
+  if (weights && mode == 1) {
+    for (int c = 0; c < 9; ++c)
+      if (weights[c] < 1) return -2;
+    weights6(weights, w);
+    w[kPrepG] = w[kPrepT] = weights[6];
+    w[kTtqrtS] = weights[7];
+    w[kTsqrtS] = weights[8];
+  }
+  return set_claim_order_impl(mode, w);
+}
+
 namespace {
 int g_colparts_mode = 1;  // tqr_set_column_parts: 0 never, 1 automatic, 2 always
 

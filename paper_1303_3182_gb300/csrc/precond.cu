@@ -73,14 +73,17 @@ __global__ void big_init_kernel(int64_t n, const double *Dinv64, double *Y, int 
 // One doubling step at half-width h for every pair of every big block, in two products:
 //   stage 0: Tmp = Y11 R12        stage 1: Y12 = -Tmp Y22
 // Y11 = Y[s](p, p), Y22 = Y[s](p+h, p+h) (h x h, already inverses), R12 = R(p, p+h) of
-// big block s (zero beyond n), p = 2 h q.  64 x 64 output tile per CTA, 4 x 4 per thread;
-// the k range stops at the triangle of the inverse factor.
+// big block s (zero beyond n), p = 2 h q.  32 x 32 output tile per CTA, 2 x 2 per thread:
+// both factors with an inverse are upper triangular (Y11(row, k) = 0 for k < row in
+// stage 0, Y22(k, col) = 0 for k > col in stage 1), so each tile's k range stops at the
+// triangle, and the small tiles spread the uneven ranges over all SMs.
 template <typename Real>
 __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *R, int64_t ldr, double *Y,
                                                          double *Tmp, int h, int stage) {
-  __shared__ double As[64][33];
-  __shared__ double Bs[32][65];
-  const int tiles = h / 64;
+  constexpr int kM = 32;
+  __shared__ double As[kM][kM + 1];
+  __shared__ double Bs[kM][kM + 1];
+  const int tiles = h / kM;
   const int tr = blockIdx.x % tiles, tc = blockIdx.x / tiles;  // output tile
   const int q = blockIdx.y, s = blockIdx.z;
   const int p = 2 * h * q;
@@ -89,21 +92,19 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *
   const int64_t g0 = static_cast<int64_t>(s) * kBig;  // first row of the big block in R
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
-  double acc[4][4] = {};
-  // both factors with an inverse are upper triangular: Y11(row, k) = 0 for k < row (stage
-  // 0) and Y22(k, col) = 0 for k > col (stage 1), so those k-tiles are skipped
-  const int k_lo = stage == 0 ? tr * 64 : 0;
-  const int k_hi = stage == 0 ? h : (tc * 64 + 64 < h ? tc * 64 + 64 : h);
-  for (int k0 = k_lo; k0 < k_hi; k0 += 32) {
-    // A tile: 64 rows x 32 k;  B tile: 32 k x 64 cols
-    for (int idx = tid; idx < 64 * 32; idx += kThreads) {
-      const int kk = idx / 64, r = idx % 64;
-      const int row = tr * 64 + r, k = k0 + kk;
+  double acc[2][2] = {};
+  const int k_lo = stage == 0 ? tr * kM : 0;
+  const int k_hi = stage == 0 ? h : (tc * kM + kM < h ? tc * kM + kM : h);
+  for (int k0 = k_lo; k0 < k_hi; k0 += kM) {
+    // A tile: kM rows x kM k;  B tile: kM k x kM cols
+    for (int idx = tid; idx < kM * kM; idx += kThreads) {
+      const int kk = idx / kM, r = idx % kM;
+      const int row = tr * kM + r, k = k0 + kk;
       As[r][kk] = stage == 0 ? Ys[(p + row) + static_cast<int64_t>(p + k) * kBig] : Tq[row + static_cast<int64_t>(k) * h];
     }
-    for (int idx = tid; idx < 32 * 64; idx += kThreads) {
-      const int c = idx / 32, kk = idx % 32;
-      const int col = tc * 64 + c, k = k0 + kk;
+    for (int idx = tid; idx < kM * kM; idx += kThreads) {
+      const int c = idx / kM, kk = idx % kM;
+      const int col = tc * kM + c, k = k0 + kk;
       double v;
       if (stage == 0) {
         const int64_t gr = g0 + p + k, gc = g0 + p + h + col;
@@ -115,24 +116,21 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *
     }
     __syncthreads();
 #pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[ty * 4 + u][kk];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx * 4 + v];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    for (int kk = 0; kk < kM; ++kk) {
+      const double a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
+      const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int row = tr * 64 + ty * 4 + u, col = tc * 64 + tx * 4 + v;
+    for (int v = 0; v < 2; ++v) {
+      const int row = tr * kM + ty * 2 + u, col = tc * kM + tx * 2 + v;
       if (stage == 0)
         Tq[row + static_cast<int64_t>(col) * h] = acc[u][v];
       else
@@ -252,19 +250,27 @@ __device__ void tile_apply_r(double (*st)[33], int64_t i0, int64_t ilim, int64_t
     va[j] = c0 + lane < clim ? __ldcg(v + (c0 + lane) + j * ldv) : 0.0;
     vb[j] = c0 + 32 + lane < clim ? __ldcg(v + (c0 + 32 + lane) + j * ldv) : 0.0;
   }
-  double acc[kR];
+  // four partial sums (columns c mod 4) keep four FMA chains in flight instead of one
+  double acc[kR][4];
 #pragma unroll
-  for (int j = 0; j < kR; ++j) acc[j] = 0.0;
-#pragma unroll 8
-  for (int c = 0; c < 64; ++c) {
-    const double m = st[c][lane];
+  for (int j = 0; j < kR; ++j)
 #pragma unroll
-    for (int j = 0; j < kR; ++j) acc[j] = fma(m, __shfl_sync(0xffffffffu, c < 32 ? va[j] : vb[j], c & 31), acc[j]);
+    for (int t = 0; t < 4; ++t) acc[j][t] = 0.0;
+#pragma unroll 4
+  for (int c = 0; c < 64; c += 4) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const double m = st[c + t][lane];
+#pragma unroll
+      for (int j = 0; j < kR; ++j)
+        acc[j][t] = fma(m, __shfl_sync(0xffffffffu, c + t < 32 ? va[j] : vb[j], (c + t) & 31), acc[j][t]);
+    }
   }
   const int64_t i = i0 + lane;
   if (i < ilim) {
 #pragma unroll
-    for (int j = 0; j < kR; ++j) atomicAdd(out + i + j * ldo, sign * acc[j]);
+    for (int j = 0; j < kR; ++j)
+      atomicAdd(out + i + j * ldo, sign * ((acc[j][0] + acc[j][1]) + (acc[j][2] + acc[j][3])));
   }
   __syncwarp();  // the slice may be refilled next
 }
@@ -387,7 +393,7 @@ int setup_typed(int64_t n, const Real *R, int64_t ldr, const double *Dinv64, dou
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return static_cast<int>(e);
   for (int h = kSmall; h < kBig; h *= 2) {
-    const int tiles = (h / 64) * (h / 64);
+    const int tiles = (h / 32) * (h / 32);
     const dim3 grid(static_cast<unsigned>(tiles), static_cast<unsigned>(kBig / (2 * h)), static_cast<unsigned>(nbig));
     for (int stage = 0; stage < 2; ++stage) {
       merge_kernel<Real><<<grid, kThreads, 0, st>>>(n, R, ldr, Y, Tmp, h, stage);

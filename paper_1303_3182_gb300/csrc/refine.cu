@@ -122,12 +122,14 @@ __device__ __forceinline__ DF df_sum(DF a, DF b) {
 
 // One pass over A before the factorization: F = fl32(A) (the matrix the tensor-core
 // factorization overwrites), P = A as FP32 pairs (column-major, ld m; hi is F's value, lo
-// the FP32 rounding of a - hi) and ||A||_F^2 added to *anorm2 in FP64.  Four columns per
+// the FP32 rounding of a - hi; split_pair, in integer instructions) and ||A||_F^2 added to
+// *anorm2, accumulated per thread in double-float (hi^2 exactly as p + e, plus 2 hi lo;
+// about 2^-44 relative, ample for the stopping tests that use it).  Four columns per
 // thread step, so that four loads are in flight before the first store.
 __global__ void __launch_bounds__(kT) prepare_a(int64_t m, int64_t n, const double *__restrict__ A, int64_t lda,
                                                 float *__restrict__ F, int64_t ldf, float2 *__restrict__ P,
                                                 double *anorm2) {
-  double s = 0.0;
+  DF acc{0.f, 0.f};
   const int64_t i0 = blockIdx.x * static_cast<int64_t>(kT) + threadIdx.x;
   const int64_t istep = static_cast<int64_t>(gridDim.x) * kT;
   for (int64_t j0 = static_cast<int64_t>(blockIdx.y) * 4; j0 < n; j0 += static_cast<int64_t>(gridDim.y) * 4) {
@@ -138,15 +140,21 @@ __global__ void __launch_bounds__(kT) prepare_a(int64_t m, int64_t n, const doub
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (j0 + u < n) {
-          const float hi = static_cast<float>(v[u]);
+          float hi, lo;
+          split_pair(v[u], hi, lo);
           F[i + (j0 + u) * ldf] = hi;
-          P[i + (j0 + u) * m] = make_float2(hi, static_cast<float>(v[u] - static_cast<double>(hi)));
-          s = fma(v[u], v[u], s);
+          P[i + (j0 + u) * m] = make_float2(hi, lo);
+          const float pp = hi * hi;
+          const float t = acc.hi + pp;
+          const float bb = t - acc.hi;
+          const float err = (acc.hi - (t - bb)) + (pp - bb);
+          acc.lo += err + fmaf(hi, hi, -pp) + 2.f * hi * lo;
+          acc.hi = t;
         }
       }
     }
   }
-  s = block_sum(s);
+  const double s = block_sum(static_cast<double>(acc.hi) + static_cast<double>(acc.lo));
   if (threadIdx.x == 0) atomicAdd(anorm2, s);
 }
 
@@ -192,38 +200,58 @@ __global__ void __launch_bounds__(kT) gemv_n_pairs(int64_t m, int64_t n, const f
 }
 
 // Y(j, r) = scale(r) sum_i A(i, j) U(i, r) with A and U as pairs: one warp per column j.
-// vec (m even, pair arrays 16-byte aligned): each lane reads two rows as one float4, four
-// float4 of A and of U per step (256 rows per warp step); else one row per lane and load.
+// Every column reads all of U, so a CTA (kT / 32 columns) stages U through shared memory
+// in chunks of kTChunk rows, read from L2 once per CTA instead of once per warp; each lane
+// then takes two rows per float4 of A (m even and 16-byte aligned pair arrays: vec), else
+// one row per load.
+constexpr int kTChunk = 2048;
 __global__ void __launch_bounds__(kT) gemv_t_pairs(int64_t m, int64_t n, const float2 *__restrict__ P,
                                                    const float2 *__restrict__ Up, double *Y, int64_t ldy, int nrhs,
                                                    const double *scale, int vec) {
-  const int warp = (blockIdx.x * kT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const float2 *col = P + static_cast<int64_t>(warp) * m;
+  __shared__ __align__(16) float2 us[kTChunk];
+  const int lane = threadIdx.x & 31;
+  const int64_t col = (static_cast<int64_t>(blockIdx.x) * kT + threadIdx.x) >> 5;
+  const bool active = col < n;
+  const float2 *cp = P + (active ? col : 0) * m;
   for (int r = 0; r < nrhs; ++r) {
     const float2 *u = Up + r * m;
     DF s[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    int64_t i = 0;
-    if (vec) {
-      const float4 *c4 = reinterpret_cast<const float4 *>(col);
-      const float4 *u4 = reinterpret_cast<const float4 *>(u);
-      for (; i + 256 <= m; i += 256) {
-        float4 a[4], w[4];
+    for (int64_t r0 = 0; r0 < m; r0 += kTChunk) {
+      const int len = static_cast<int>(m - r0 < kTChunk ? m - r0 : kTChunk);
+      __syncthreads();  // the previous chunk is no longer read
+      if (vec) {
+        const float4 *u4 = reinterpret_cast<const float4 *>(u + r0);
+        for (int x = threadIdx.x; x < len / 2; x += kT) reinterpret_cast<float4 *>(us)[x] = u4[x];
+        if ((len & 1) && threadIdx.x == 0) us[len - 1] = u[r0 + len - 1];
+      } else {
+        for (int x = threadIdx.x; x < len; x += kT) us[x] = u[r0 + x];
+      }
+      __syncthreads();
+      if (!active) continue;
+      const float2 *c = cp + r0;
+      int i = 0;
+      if (vec) {
+        const float4 *c4 = reinterpret_cast<const float4 *>(c);
+        const float4 *w4 = reinterpret_cast<const float4 *>(us);
+        for (; i + 256 <= len; i += 256) {
+          float4 a[4], w[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a[q] = c4[(i >> 1) + 32 * q + lane];
+          for (int q = 0; q < 4; ++q) a[q] = c4[(i >> 1) + 32 * q + lane];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = u4[(i >> 1) + 32 * q + lane];
+          for (int q = 0; q < 4; ++q) w[q] = w4[(i >> 1) + 32 * q + lane];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          df_acc(s[q], a[q].x, a[q].y, w[q].x, w[q].y);
-          df_acc(s[q], a[q].z, a[q].w, w[q].z, w[q].w);
+          for (int q = 0; q < 4; ++q) {
+            df_acc(s[q], a[q].x, a[q].y, w[q].x, w[q].y);
+            df_acc(s[q], a[q].z, a[q].w, w[q].z, w[q].w);
+          }
         }
       }
+      for (i += lane; i < len; i += 32) {
+        const float2 a0 = c[i], u0 = us[i];
+        df_acc(s[0], a0.x, a0.y, u0.x, u0.y);
+      }
     }
-    for (i += lane; i < m; i += 32) {
-      const float2 a0 = col[i], u0 = u[i];
-      df_acc(s[0], a0.x, a0.y, u0.x, u0.y);
-    }
+    if (!active) continue;
     DF t = df_sum(df_sum(s[0], s[1]), df_sum(s[2], s[3]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -231,7 +259,7 @@ __global__ void __launch_bounds__(kT) gemv_t_pairs(int64_t m, int64_t n, const f
       t = df_sum(t, v);
     }
     if (lane == 0)
-      Y[warp + r * ldy] = (static_cast<double>(t.hi) + static_cast<double>(t.lo)) * (scale ? scale[r] : 1.0);
+      Y[col + r * ldy] = (static_cast<double>(t.hi) + static_cast<double>(t.lo)) * (scale ? scale[r] : 1.0);
   }
 }
 

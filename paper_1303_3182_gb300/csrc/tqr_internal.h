@@ -3,6 +3,7 @@
 
 #include <array>
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -68,6 +69,50 @@ constexpr int kColShift = 12;
 #else
 #define TQR_HOST_DEVICE
 #endif
+// FP32 pair of a double: hi = fl32(v) (round to nearest even), lo = fl32(v - hi) (the
+// difference is exact in FP64), formed from the bit pattern with integer instructions -
+// GB300 runs FP64 -> FP32 conversions and FP64 arithmetic on its narrow FP64 unit, which
+// would bound a pass over a large matrix.  hi's 23 fraction bits are the top of v's 52,
+// rounded by the 29 below (a carry moves into the exponent, as rounding does); the
+// residual is those 29 bits minus the rounding, an integer of at most 29 bits converted
+// with one rounding and scaled by the power of two of its last place.  v with |v| outside
+// [2^-74, 2^127) (zero, tiny, huge, inf, NaN) takes the plain conversions.
+inline TQR_HOST_DEVICE void split_pair(double v, float &hi, float &lo) {
+#ifdef __CUDA_ARCH__
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(v));
+#else
+  uint64_t b;
+  std::memcpy(&b, &v, sizeof b);
+#endif
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  if (e < 949 || e > 1149) {
+    hi = static_cast<float>(v);
+    lo = static_cast<float>(v - static_cast<double>(hi));
+    return;
+  }
+  const uint32_t sign = static_cast<uint32_t>(b >> 63) << 31;
+  const uint64_t frac = b & ((uint64_t(1) << 52) - 1);
+  const uint32_t keep = static_cast<uint32_t>(frac >> 29);
+  const uint32_t rem = static_cast<uint32_t>(frac & ((uint64_t(1) << 29) - 1));
+  const uint32_t half = uint32_t(1) << 28;
+  const uint32_t up = (rem > half || (rem == half && (keep & 1u))) ? 1u : 0u;
+  const uint32_t hbits = sign | ((static_cast<uint32_t>(e - 896) << 23) + keep + up);
+  const int32_t r = static_cast<int32_t>(rem) - static_cast<int32_t>(up << 29);
+  const uint32_t sbits = static_cast<uint32_t>(e - 948) << 23;  // 2^(e - 1075)
+#ifdef __CUDA_ARCH__
+  hi = __uint_as_float(hbits);
+  const float scale = __uint_as_float(sbits);
+  const float rf = __int2float_rn(r);
+#else
+  std::memcpy(&hi, &hbits, sizeof hi);
+  float scale;
+  std::memcpy(&scale, &sbits, sizeof scale);
+  const float rf = static_cast<float>(r);
+#endif
+  const float mag = rf * scale;
+  lo = r == 0 ? 0.f : (sign ? -mag : mag);
+}
+
 inline TQR_HOST_DEVICE int task_col(int j, int colparts) { return colparts > 1 ? (j & ((1 << kColShift) - 1)) : j; }
 inline TQR_HOST_DEVICE int task_part(int j, int colparts) { return colparts > 1 ? (j >> kColShift) : 0; }
 

@@ -206,3 +206,39 @@ def test_complex_precision_arguments():
     ptrs = (ctypes.c_void_p * 1)(1)
     h = ctypes.c_void_p(0)
     assert L.tqr_batch_plan_create(1, m, m, ptrs, m, None, tqr.Z64, ptrs, ctypes.byref(h)) == -7
+
+
+def test_split_pairs_match_fp32_rounding():
+    """The refinement's FP32 pair split (integer instructions) against its definition:
+    hi = fl32(x) and lo = fl32(x - hi) rounded to nearest even by numpy, bit for bit -
+    random magnitudes over the whole range, rounding ties (even and odd), carries into
+    the exponent, both signs, and the values outside the integer path's range (zero,
+    subnormal, tiny, huge, inf) that take the plain conversions."""
+    L = tqr.lib()
+    rng = np.random.default_rng(1303318210)
+    parts = [rng.standard_normal(20000),
+             rng.standard_normal(20000) * np.exp2(rng.integers(-80, 130, 20000)),
+             np.array([0.0, -0.0, 1.0, -1.0, 5e-324, 2.0 ** -1022, 2.0 ** -75, 2.0 ** -74, 2.0 ** -73,
+                       2.0 ** 126, 2.0 ** 127 * 0.999, 1e300, -1e300, np.inf, -np.inf, 3.4e38])]
+    # ties at the 29-bit boundary: keep bit even / odd, and the all-ones carry
+    base = np.float64(1.0) + np.arange(64) * 2.0 ** -23
+    parts.append(base + 2.0 ** -24)
+    parts.append(-(base + 2.0 ** -24))
+    parts.append(np.nextafter(np.float64(2.0), 0.0) * np.exp2(np.arange(-60, 60)))
+    x = np.ascontiguousarray(np.concatenate(parts), dtype=np.float64)
+    n = x.size
+    hi = np.empty(n, dtype=np.float32)
+    lo = np.empty(n, dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    assert L.tqr_debug_split_pairs(n, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), hi.ctypes.data_as(fp),
+                                   lo.ctypes.data_as(fp)) == 0
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref_hi = x.astype(np.float32)
+        ref_lo = (x - ref_hi.astype(np.float64)).astype(np.float32)
+    fin = np.isfinite(x)
+    assert np.array_equal(hi.view(np.uint32)[fin], ref_hi.view(np.uint32)[fin])
+    same = ref_lo.view(np.uint32) == lo.view(np.uint32)
+    both_zero = (ref_lo == 0) & (lo == 0)  # +0 / -0 of an exact split are the same value
+    assert np.all((same | both_zero)[fin])
+    assert L.tqr_debug_split_pairs(-1, None, None, None) == -1
+    assert L.tqr_debug_split_pairs(3, None, None, None) == -2
