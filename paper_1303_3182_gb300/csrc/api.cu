@@ -806,7 +806,7 @@ int tqr_lstsq(int64_t m, int64_t n, int64_t nrhs, int nb, int ib, int tree, int 
     const int nr = static_cast<int>(std::min<int64_t>(64, nrhs - r0));
     int it = 0;
     const int lrc = lsqr_refine(m, n, nr, A, lda, Af, ldf, B + r0 * ldb, ldb, X + r0 * ldx, ldx,
-                                tol > 0 ? tol : 1e-14, max_iter > 0 ? max_iter : 100, &it, r0 == 0, lw, s->flags, status,
+                                tol > 0 ? tol : 1e-14, max_iter > 0 ? max_iter : 100, &it, r0 == 0, true, lw, s->flags, status,
                                 g_wait_limit_ns, stream);
     if (lrc > 0) return cuda_fail(static_cast<cudaError_t>(lrc), "lstsq refinement");
     if (lrc < 0) converged = false;

@@ -420,6 +420,7 @@ __device__ void task_geqrt_resident(const ExecParams &p, unsigned char *raw, uin
   const int mb = geo.rows(i), ncol = geo.cols(k), K = min(mb, ncol);
   load_block(rb.Ct, kMLD, tile, p.lda, mb, ncol);
   __syncthreads();
+  phase_mark(s.ph, 3);  // trace phases: 3 the loads, then per ib-block 0 panel, 1 T, 2 trailing update
   for (int c0 = 0; c0 < kMNB; c0 += ib) {
     const int width = min(ib, kMNB - c0), kb = max(0, min(ib, K - c0));
     if (kb == 0) {
@@ -478,6 +479,7 @@ __device__ void task_pairqrt_resident(const ExecParams &p, unsigned char *raw, u
   load_block_mode(rb.Ct, kMLD, t2, p.lda, mb, K,
                   [](int r, int c) { return (kTS || r <= c) ? static_cast<int>(kLoad) : static_cast<int>(kZero); });
   __syncthreads();
+  phase_mark(s.ph, 3);
   for (int c0 = 0; c0 < kMNB; c0 += ib) {
     const int width = min(ib, kMNB - c0), kb = max(0, min(ib, K - c0));
     if (kb == 0) {
@@ -544,6 +546,7 @@ __device__ void task_pairqrt_split(const ExecParams &p, unsigned char *raw, uint
     return (kTS || r <= c0 + c) ? static_cast<int>(kLoad) : static_cast<int>(kZero);
   });
   __syncthreads();
+  phase_mark(s.ph, 3);
   for (int cb = c0; cb < c1; cb += ib) {
     const int width = min(ib, kMNB - cb), kb = max(0, min(ib, K - cb));
     if (kb == 0) {

@@ -250,27 +250,19 @@ __device__ void tile_apply_r(double (*st)[33], int64_t i0, int64_t ilim, int64_t
     va[j] = c0 + lane < clim ? __ldcg(v + (c0 + lane) + j * ldv) : 0.0;
     vb[j] = c0 + 32 + lane < clim ? __ldcg(v + (c0 + 32 + lane) + j * ldv) : 0.0;
   }
-  // four partial sums (columns c mod 4) keep four FMA chains in flight instead of one
-  double acc[kR][4];
+  double acc[kR];
 #pragma unroll
-  for (int j = 0; j < kR; ++j)
+  for (int j = 0; j < kR; ++j) acc[j] = 0.0;
+#pragma unroll 8
+  for (int c = 0; c < 64; ++c) {
+    const double m = st[c][lane];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[j][t] = 0.0;
-#pragma unroll 4
-  for (int c = 0; c < 64; c += 4) {
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const double m = st[c + t][lane];
-#pragma unroll
-      for (int j = 0; j < kR; ++j)
-        acc[j][t] = fma(m, __shfl_sync(0xffffffffu, c + t < 32 ? va[j] : vb[j], (c + t) & 31), acc[j][t]);
-    }
+    for (int j = 0; j < kR; ++j) acc[j] = fma(m, __shfl_sync(0xffffffffu, c < 32 ? va[j] : vb[j], c & 31), acc[j]);
   }
   const int64_t i = i0 + lane;
   if (i < ilim) {
 #pragma unroll
-    for (int j = 0; j < kR; ++j)
-      atomicAdd(out + i + j * ldo, sign * ((acc[j][0] + acc[j][1]) + (acc[j][2] + acc[j][3])));
+    for (int j = 0; j < kR; ++j) atomicAdd(out + i + j * ldo, sign * acc[j]);
   }
   __syncwarp();  // the slice may be refilled next
 }

@@ -455,7 +455,8 @@ int lsqr_prepare(int64_t m, int64_t n, const double *A, int64_t lda, float *F, i
 
 int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, const float *R, int64_t ldr,
                 const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter, int *iters_out,
-                bool setup, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns, void *stream) {
+                bool setup, bool x_zero, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
+                void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const FixedLayout fl = fixed_layout(m, n, work);
   const float2 *Apair = fl.Apair;
@@ -520,10 +521,12 @@ int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, co
     // FP64 residual of the current solution: u = r = B - A X, beta = ||r||
     TQR_CK(cudaMemcpy2DAsync(U, m * sizeof(double), B, ldb * sizeof(double), m * sizeof(double), nrhs,
                              cudaMemcpyDeviceToDevice, st));
-    copy_scaled<<<vgrid(n, nrhs), kT, 0, st>>>(n, Tt, n, X, ldx, -1.0, nrhs);
-    TQR_CKL();
-    gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
-    TQR_CKL();
+    if (outer > 0 || !x_zero) {  // a zero start has the residual B itself
+      copy_scaled<<<vgrid(n, nrhs), kT, 0, st>>>(n, Tt, n, X, ldx, -1.0, nrhs);
+      TQR_CKL();
+      gemv_n<<<ggrid, kT, 0, st>>>(m, n, A, lda, Tt, n, U, m, nrhs, chunk);
+      TQR_CKL();
+    }
     TQR_CK(cudaMemsetAsync(ssq_a, 0, sizeof(double) * 2 * nrhs, st));
     TQR_CK(cudaMemsetAsync(eta2, 0, sizeof(double) * nrhs, st));
     colnorm<<<vgrid(m, nrhs), kT, 0, st>>>(m, U, m, ssq_b, nrhs);

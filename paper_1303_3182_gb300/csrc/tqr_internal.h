@@ -354,13 +354,13 @@ int precond_solve(int64_t n, const void *R, int64_t ldr, bool real_is_double, co
 // lsqr_prepare runs once per least-squares call, before the factorization: F = fl32(A)
 // (ld ldf, the matrix to factor), and A's FP32 pairs and ||A||_F^2 into work.  setup:
 // build the preconditioner from R (the first block of right-hand sides; later blocks
-// reuse it).
+// reuse it).  x_zero: X holds zeros on entry (the first residual is B itself).
 size_t lsqr_work_doubles(int64_t m, int64_t n, int nrhs);
 int lsqr_prepare(int64_t m, int64_t n, const double *A, int64_t lda, float *F, int64_t ldf, double *work,
                  void *stream);
 int lsqr_refine(int64_t m, int64_t n, int nrhs, const double *A, int64_t lda, const float *R, int64_t ldr,
                 const double *B, int64_t ldb, double *X, int64_t ldx, double tol, int max_iter,
-                int *iters_out, bool setup, double *work, int32_t *flags, int32_t *status, int64_t wait_limit_ns,
-                void *stream);
+                int *iters_out, bool setup, bool x_zero, double *work, int32_t *flags, int32_t *status,
+                int64_t wait_limit_ns, void *stream);
 
 }  // namespace tqr

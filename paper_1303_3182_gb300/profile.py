@@ -9,7 +9,9 @@ Default mode: tqr_factor of an N(0,1) matrix; one JSON line per repetition (devi
 of the factorization executor and the nominal TFLOP/s).  With --trace, the last
 repetition records the executor's per-task stamps (tqr_set_trace) and writes them as a
 list of {kind, i, piv, k, j, sm, start_us, end_us, phases_us} records - a Gantt chart of
-the task graph.
+the task graph.  phases_us: four time slots of the task - panel tasks: panel, T, in-tile
+trailing update (summed over ib-blocks) and the resident tiles' loads; tensor-core updates:
+the first product with its operand images, its wait, the second product(s), the epilogue.
 --batch N: one batched launch (tqr_batch_plan_run, built-in size classes) over the
 first N matrices of the 2048-matrix distribution (rows uniform in [256, 8192], columns
 in {32, 64, 128, 256}).
