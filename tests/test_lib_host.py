@@ -108,6 +108,10 @@ def test_invalid_arguments():
     assert L.tqr_strerror(3) == b"device dependency wait exceeded the limit"
     assert L.tqr_set_column_parts(3) == -1 and L.tqr_set_column_parts(-1) == -1
     assert L.tqr_set_column_parts(1) == 0
+    w9 = (ctypes.c_int64 * 9)(265, 285, 20, 32, 320, 32, 66, 80, 0)
+    assert L.tqr_set_claim_order_tc(3, None) == -1
+    assert L.tqr_set_claim_order_tc(1, w9) == -2
+    assert L.tqr_set_claim_order_tc(2, None) == 0
 
 
 def test_workspace_and_flops():
