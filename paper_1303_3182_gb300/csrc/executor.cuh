@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "tqr_internal.h"
 
@@ -297,36 +298,48 @@ __device__ void apply_block_f32(float *C, int ldc, int nrows, float *C1, int ldc
     __syncthreads();
   }
   {
-    // C -= V W: thread -> rows rt + 64 x, columns 8 cg .. 8 cg + 7
+    // C -= V W: thread -> rows rt + 64 x (x < NX, the row groups the block has),
+    // columns 8 cg .. 8 cg + 7
     const int rt = tid & 63, cg = tid >> 6;
-    float acc[4][8];
+    auto rows_times_w = [&](auto nx) {
+      constexpr int NX = decltype(nx)::value;
+      float acc[NX][8];
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < NX; ++x)
 #pragma unroll
-      for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
-    int rr[4];
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+      int rr[NX];
 #pragma unroll
-    for (int x = 0; x < 4; ++x) rr[x] = min(rt + 64 * x, nrows - 1);
-    for (int b = 0; b < kb; ++b) {
-      const float4 w0 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg);
-      const float4 w1 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg + 4);
-      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+      for (int x = 0; x < NX; ++x) rr[x] = min(rt + 64 * x, nrows - 1);
+      for (int b = 0; b < kb; ++b) {
+        const float4 w0 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg);
+        const float4 w1 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg + 4);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const float v = V[rr[x] + b * ldv];
+        for (int x = 0; x < NX; ++x) {
+          const float v = V[rr[x] + b * ldv];
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] += v * w[y];
-      }
-    }
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      const int r = rt + 64 * x;
-      if (r < nrows) {
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-          const int c = 8 * cg + y;
-          if (c < ncols) C[r + c * ldc] -= acc[x][y];
+          for (int y = 0; y < 8; ++y) acc[x][y] += v * w[y];
         }
+      }
+#pragma unroll
+      for (int x = 0; x < NX; ++x) {
+        const int r = rt + 64 * x;
+        if (r < nrows) {
+#pragma unroll
+          for (int y = 0; y < 8; ++y) {
+            const int c = 8 * cg + y;
+            if (c < ncols) C[r + c * ldc] -= acc[x][y];
+          }
+        }
+      }
+    };
+    if (8 * cg < ncols) {
+      switch ((nrows + 63) / 64) {
+        case 1: rows_times_w(std::integral_constant<int, 1>{}); break;
+        case 2: rows_times_w(std::integral_constant<int, 2>{}); break;
+        case 3: rows_times_w(std::integral_constant<int, 3>{}); break;
+        default: rows_times_w(std::integral_constant<int, 4>{}); break;
       }
     }
     __syncthreads();
@@ -776,52 +789,25 @@ __device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
 // (Schreiber-Van Loan) T(c,c) = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c) makes
 // T the inverse of the upper-triangular S with S(c,c) = 1/tau_c and S(a,c) = G(a,c)
 // above the diagonal (the inverse of [S1 g; 0 1/tau] has last column
-// [-tau S1^{-1} g; tau]).  Lane j forms column j of T by back substitution without a
-// division: x_j = tau_j, x_a = -tau_a sum_{a<k<=j} G(a,k) x_k, accumulating the sums
-// right to left so that each step is independent FMAs.  tau_c = 0 (an identity
-// reflector) gives a zero row and column, as the recurrence does.
+// [-tau S1^{-1} g; tau]).  Column j of T by back substitution without a division:
+// x_j = tau_j, x_a = -tau_a sum_{a<k<=j} G(a,k) x_k, the sums accumulated right to left
+// (k from j down), so that each step is one FMA per row.  Warp w forms columns j = w,
+// w + kWarps, ...: lane a holds row a's running sum, lane k hands x_k to the warp at step
+// k.  The longest chain is the last column's j steps, shared out by column over the warps
+// (one warp doing all columns would issue kb^2 / 2 dependent steps).  tau_c = 0 (an
+// identity reflector) gives a zero row and column, as the recurrence does.
 template <typename S>
 __device__ void build_t(Smem<S> &s, int kb) {
-  if constexpr (sizeof(S) == sizeof(double)) {
-    // FP64 (each FP64 instruction costs the whole warp many cycles on this GPU): warp w
-    // forms columns j = w, w + kWarps, ..., lane a holding row a's running sum; a step per
-    // k from j down gives x_k (tau_j, or -tau_k acc_k from lane k), broadcast, then acc_a
-    // += G(a, k) x_k for a < k - the same operations in the same order as the one-warp
-    // form below, spread over the warps by column.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = warp; j < kb; j += kWarps) {
-      S acc = 0;
-      for (int k = j; k >= 0; --k) {
-        const S mine = k == j ? s.tau_s[j] : -s.tau_s[k] * acc;  // meaningful in lane k
-        const S xk = __shfl_sync(0xffffffffu, mine, k);
-        if (lane == k) s.T[k + j * s.ldt] = xk;
-        if (lane < k) acc += s.G[lane + k * s.ldt] * xk;
-      }
-      if (lane > j && lane < kb) s.T[lane + j * s.ldt] = S(0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = warp; j < kb; j += kWarps) {
+    S acc = 0;
+    for (int k = j; k >= 0; --k) {
+      const S mine = k == j ? s.tau_s[j] : -s.tau_s[k] * acc;  // meaningful in lane k
+      const S xk = __shfl_sync(0xffffffffu, mine, k);
+      if (lane == k) s.T[k + j * s.ldt] = xk;
+      if (lane < k) acc += s.G[lane + k * s.ldt] * xk;
     }
-    __syncthreads();
-    return;
-  }
-  if (threadIdx.x < 32) {
-    const int j = threadIdx.x;
-    if (j < kb) {
-      S acc[32];
-#pragma unroll
-      for (int a = 0; a < 32; ++a) acc[a] = 0;
-#pragma unroll
-      for (int k = 31; k >= 0; --k) {
-        if (k < kb) {
-          S xk = 0;
-          if (k == j)
-            xk = s.tau_s[j];
-          else if (k < j)
-            xk = -s.tau_s[k] * acc[k];
-          s.T[k + j * s.ldt] = xk;  // zero below the diagonal (k > j)
-#pragma unroll
-          for (int a = 0; a < k; ++a) acc[a] += s.G[a + k * s.ldt] * xk;
-        }
-      }
-    }
+    if (lane > j && lane < kb) s.T[lane + j * s.ldt] = S(0);  // zero below the diagonal
   }
   __syncthreads();
 }
