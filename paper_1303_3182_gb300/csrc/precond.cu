@@ -3,15 +3,17 @@
 //
 // Set-up (once per refinement): a transposed copy of R's upper triangle (so that both
 // solves read R along contiguous columns) and the inverses of R's 1024 x 1024 diagonal
-// blocks in FP64,
-// built from the 64 x 64 block inverses by four doubling steps
-//   inv([R11 R12; 0 R22]) = [R11^{-1}, -R11^{-1} R12 R22^{-1}; 0, R22^{-1}].
+// blocks, formed in FP64 from the 64 x 64 block inverses by four doubling steps
+//   inv([R11 R12; 0 R22]) = [R11^{-1}, -R11^{-1} R12 R22^{-1}; 0, R22^{-1}]
+// and kept as FP32 pairs (hi, lo) for the solves.
 // Solve: one cooperative launch walks the big blocks (4 for n = 4096); each step is two
 // grid-wide phases separated by a grid barrier - x_s = Y_s b_s over all SMs, then the
 // update of the remaining right-hand-side rows with R's off-diagonal column block - so
-// the sequential depth is ceil(n / 1024) steps instead of ceil(n / 64).  Partial sums
-// meet in FP64 atomics (results reproducible to rounding, not bit for bit).  Every grid
-// barrier wait is bounded and reports kStatusTimeout like the executor's waits.
+// the sequential depth is ceil(n / 1024) steps instead of ceil(n / 64).  The products
+// run in double-float arithmetic (about 2^-44 relative: a preconditioner applied to the
+// same accuracy as the refinement's pair products with A); partial sums meet in FP64
+// atomics (results reproducible to rounding, not bit for bit).  Every grid barrier wait
+// is bounded and reports kStatusTimeout like the executor's waits.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -194,14 +196,26 @@ __device__ bool grid_barrier(int32_t *bar, int &gen, int32_t *status, int64_t li
   return s_ok != 0;
 }
 
+// Operator entries as FP32 pairs (hi, lo): an FP32 entry of R is (x, 0); an FP64 entry
+// is split (split_pair); a pair of the block inverses (stored as pairs) is itself.
+__device__ __forceinline__ float2 as_pair(float x) { return make_float2(x, 0.f); }
+__device__ __forceinline__ float2 as_pair(double x) {
+  float2 r;
+  split_pair(x, r.x, r.y);
+  return r;
+}
+__device__ __forceinline__ float2 as_pair(float2 x) { return x; }
+template <typename Mt> __device__ __forceinline__ Mt zero_of() { return Mt(0); }
+template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
+
 // One warp's 32 x 64 tile of an operator, Op(i, c) for rows i0.. (i < ilim) and columns
-// c0.. (c < clim), staged in the warp's shared-memory slice as st[c][i - i0]:
+// c0.. (c < clim), staged in the warp's shared-memory slice as FP32 pairs st[c][i - i0]:
 // Op(i, c) = M[i + c*ldm] (kTrans = false: lanes read consecutive rows) or M[c + i*ldm]
 // (kTrans = true: lanes read consecutive columns).  The loads are unrolled so that many
 // are in flight; the tile does not depend on the solution, so it is fetched before the
 // grid barrier that precedes its use.
 template <typename Mt, bool kTrans>
-__device__ void tile_load(double (*st)[33], const Mt *M, int64_t ldm, int64_t i0, int64_t ilim, int64_t c0,
+__device__ void tile_load(float2 (*st)[33], const Mt *M, int64_t ldm, int64_t i0, int64_t ilim, int64_t c0,
                           int64_t clim) {
   const int lane = threadIdx.x & 31;
   // groups of 32 loads into registers, then the shared-memory stores: every load of a
@@ -213,9 +227,10 @@ __device__ void tile_load(double (*st)[33], const Mt *M, int64_t ldm, int64_t i0
     for (int cb = 0; cb < 64; cb += kGroup) {
       Mt v[kGroup];
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) v[u] = (ok && c0 + cb + u < clim) ? __ldcg(M + i + (c0 + cb + u) * ldm) : Mt(0);
+      for (int u = 0; u < kGroup; ++u)
+        v[u] = (ok && c0 + cb + u < clim) ? __ldcg(M + i + (c0 + cb + u) * ldm) : zero_of<Mt>();
 #pragma unroll
-      for (int u = 0; u < kGroup; ++u) st[cb + u][lane] = static_cast<double>(v[u]);
+      for (int u = 0; u < kGroup; ++u) st[cb + u][lane] = as_pair(v[u]);
     }
   } else {
     constexpr int kRows = kGroup / 2;
@@ -225,13 +240,13 @@ __device__ void tile_load(double (*st)[33], const Mt *M, int64_t ldm, int64_t i0
       for (int u = 0; u < kRows; ++u) {
         const int64_t row = i0 + ib + u;
         const bool ok = row < ilim;
-        v[2 * u] = (ok && c0 + lane < clim) ? __ldcg(M + (c0 + lane) + row * ldm) : Mt(0);
-        v[2 * u + 1] = (ok && c0 + 32 + lane < clim) ? __ldcg(M + (c0 + 32 + lane) + row * ldm) : Mt(0);
+        v[2 * u] = (ok && c0 + lane < clim) ? __ldcg(M + (c0 + lane) + row * ldm) : zero_of<Mt>();
+        v[2 * u + 1] = (ok && c0 + 32 + lane < clim) ? __ldcg(M + (c0 + 32 + lane) + row * ldm) : zero_of<Mt>();
       }
 #pragma unroll
       for (int u = 0; u < kRows; ++u) {
-        st[lane][ib + u] = static_cast<double>(v[2 * u]);
-        st[lane + 32][ib + u] = static_cast<double>(v[2 * u + 1]);
+        st[lane][ib + u] = as_pair(v[2 * u]);
+        st[lane + 32][ib + u] = as_pair(v[2 * u + 1]);
       }
     }
   }
@@ -239,35 +254,49 @@ __device__ void tile_load(double (*st)[33], const Mt *M, int64_t ldm, int64_t i0
 }
 
 // out(i, j) += sign * sum_c st[c][i - i0] v(c0 + c, j) for the staged tile; kR right-hand
-// sides (the FP64 products are the cost of a phase, so none is spent on absent ones).
+// sides.  The products run in double-float arithmetic on the FP32 units (operator entry
+// and vector entry as FP32 pairs: the leading product exact as p + e by an FMA, the cross
+// terms added to the error; Knuth's TwoSum keeps the running sum as an unevaluated pair) -
+// about 2^-44 relative, with FP32 instructions instead of FP64 ones, which on this GPU
+// bound a phase at one FP64 instruction per element; partial sums meet in FP64 atomics.
 template <int kR>
-__device__ void tile_apply_r(double (*st)[33], int64_t i0, int64_t ilim, int64_t c0, int64_t clim, const double *v,
+__device__ void tile_apply_r(float2 (*st)[33], int64_t i0, int64_t ilim, int64_t c0, int64_t clim, const double *v,
                              int64_t ldv, double *out, int64_t ldo, double sign) {
   const int lane = threadIdx.x & 31;
-  double va[kR], vb[kR];
+  float2 va[kR], vb[kR];
 #pragma unroll
   for (int j = 0; j < kR; ++j) {
-    va[j] = c0 + lane < clim ? __ldcg(v + (c0 + lane) + j * ldv) : 0.0;
-    vb[j] = c0 + 32 + lane < clim ? __ldcg(v + (c0 + 32 + lane) + j * ldv) : 0.0;
+    va[j] = as_pair(c0 + lane < clim ? __ldcg(v + (c0 + lane) + j * ldv) : 0.0);
+    vb[j] = as_pair(c0 + 32 + lane < clim ? __ldcg(v + (c0 + 32 + lane) + j * ldv) : 0.0);
   }
-  double acc[kR];
+  float hi[kR], lo[kR];
 #pragma unroll
-  for (int j = 0; j < kR; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kR; ++j) hi[j] = lo[j] = 0.f;
 #pragma unroll 8
   for (int c = 0; c < 64; ++c) {
-    const double m = st[c][lane];
+    const float2 m = st[c][lane];
 #pragma unroll
-    for (int j = 0; j < kR; ++j) acc[j] = fma(m, __shfl_sync(0xffffffffu, c < 32 ? va[j] : vb[j], c & 31), acc[j]);
+    for (int j = 0; j < kR; ++j) {
+      const float xh = __shfl_sync(0xffffffffu, c < 32 ? va[j].x : vb[j].x, c & 31);
+      const float xl = __shfl_sync(0xffffffffu, c < 32 ? va[j].y : vb[j].y, c & 31);
+      const float p = m.x * xh;
+      const float e = fmaf(m.x, xh, -p) + fmaf(m.x, xl, m.y * xh);
+      const float t = hi[j] + p;
+      const float bb = t - hi[j];
+      lo[j] += ((hi[j] - (t - bb)) + (p - bb)) + e;
+      hi[j] = t;
+    }
   }
   const int64_t i = i0 + lane;
   if (i < ilim) {
 #pragma unroll
-    for (int j = 0; j < kR; ++j) atomicAdd(out + i + j * ldo, sign * acc[j]);
+    for (int j = 0; j < kR; ++j)
+      atomicAdd(out + i + j * ldo, sign * (static_cast<double>(hi[j]) + static_cast<double>(lo[j])));
   }
   __syncwarp();  // the slice may be refilled next
 }
 
-__device__ void tile_apply(double (*st)[33], int64_t i0, int64_t ilim, int64_t c0, int64_t clim, const double *v,
+__device__ void tile_apply(float2 (*st)[33], int64_t i0, int64_t ilim, int64_t c0, int64_t clim, const double *v,
                            int64_t ldv, double *out, int64_t ldo, int nrhs, double sign) {
   switch (nrhs) {
     case 1: tile_apply_r<1>(st, i0, ilim, c0, clim, v, ldv, out, ldo, sign); break;
@@ -284,11 +313,11 @@ __device__ void tile_apply(double (*st)[33], int64_t i0, int64_t ilim, int64_t c
 // before the barrier that precedes the phase.
 template <typename Real, bool kLowerT>
 __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Real *R, int64_t ldr, const Real *Rt,
-                                                            const double *Y, double *B, int64_t ldb, int nrhs,
+                                                            const float2 *Y, double *B, int64_t ldb, int nrhs,
                                                             double *xs, int32_t *bar, int32_t *status,
                                                             int64_t limit_ns) {
-  extern __shared__ double pc_smem[];
-  double(*st)[33] = reinterpret_cast<double(*)[33]>(pc_smem + (threadIdx.x >> 5) * 64 * 33);
+  extern __shared__ float2 pc_smem[];
+  float2(*st)[33] = reinterpret_cast<float2(*)[33]>(pc_smem + (threadIdx.x >> 5) * 64 * 33);
   const int nbig = static_cast<int>((n + kBig - 1) / kBig);
   const int warp = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
@@ -308,7 +337,7 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
     const int s = block_of(step);
     const int64_t g0 = static_cast<int64_t>(s) * kBig;
     const int rb = static_cast<int>(lmin(kBig, n - g0));
-    tile_load<double, kLowerT>(st, Y + static_cast<int64_t>(s) * kBig * kBig, kBig, (item / kCT) * 32, rb,
+    tile_load<float2, kLowerT>(st, Y + static_cast<int64_t>(s) * kBig * kBig, kBig, (item / kCT) * 32, rb,
                                (item % kCT) * 64, rb);
   };
   // phase-2 rows of step: [lo, hi)
@@ -369,6 +398,19 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
   }
 }
 
+// Y[i] (FP64) -> the FP32 pair (hi, lo) of the same value, in place (8 bytes either way;
+// each element is read and rewritten by one thread).
+__global__ void pairs_in_place(double *Y, int64_t count) {
+  float2 *P = reinterpret_cast<float2 *>(Y);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < count;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    const double v = Y[i];
+    float2 r;
+    split_pair(v, r.x, r.y);
+    P[i] = r;
+  }
+}
+
 template <typename Real>
 int setup_typed(int64_t n, const Real *R, int64_t ldr, const double *Dinv64, double *Y, double *Tmp, Real *Rt,
                 cudaStream_t st) {
@@ -393,14 +435,17 @@ int setup_typed(int64_t n, const Real *R, int64_t ldr, const double *Dinv64, dou
       if ((e = cudaGetLastError()) != cudaSuccess) return static_cast<int>(e);
     }
   }
-  return 0;
+  // the solves read the inverses as FP32 pairs, written over their FP64 values
+  pairs_in_place<<<1216, kThreads, 0, st>>>(Y, static_cast<int64_t>(nbig) * kBig * kBig);
+  count_launch();
+  return static_cast<int>(cudaGetLastError());
 }
 
 template <typename Real, bool kLowerT>
-int solve_typed(int64_t n, const Real *R, int64_t ldr, const Real *Rt, const double *Y, double *B, int64_t ldb,
+int solve_typed(int64_t n, const Real *R, int64_t ldr, const Real *Rt, const float2 *Y, double *B, int64_t ldb,
                 int64_t nrhs, double *xs, int32_t *bar, int32_t *status, int64_t limit_ns, cudaStream_t st) {
   auto kern = big_trsv_kernel<Real, kLowerT>;
-  const size_t smem = sizeof(double) * kWarps * 64 * 33;
+  const size_t smem = sizeof(float2) * kWarps * 64 * 33;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return static_cast<int>(e);
   int dev = 0, nsm = 0, per_sm = 0;
@@ -438,12 +483,14 @@ size_t precond_work_doubles(int64_t n, bool real_is_double) {
 namespace {
 struct Layout {
   double *Y, *Tmp, *xs;
+  const float2 *Yp;  // Y after the set-up: FP32 pairs in the same storage
   void *Rt;
 };
 Layout layout(int64_t n, const double *work) {
   const size_t nbig = static_cast<size_t>((n + kBig - 1) / kBig);
   Layout l;
   l.Y = const_cast<double *>(work);
+  l.Yp = reinterpret_cast<const float2 *>(work);
   l.Tmp = l.Y + nbig * kBig * kBig;
   l.xs = l.Tmp + nbig * (kBig / 2) * (kBig / 2);
   l.Rt = l.xs + 2 * kBig * kRhsMax;
@@ -467,15 +514,15 @@ int precond_solve(int64_t n, const void *R, int64_t ldr, bool real_is_double, co
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (real_is_double) {
     const double *Rd = static_cast<const double *>(R), *Rt = static_cast<const double *>(l.Rt);
-    return lower_transposed ? solve_typed<double, true>(n, Rd, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status,
+    return lower_transposed ? solve_typed<double, true>(n, Rd, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status,
                                                         wait_limit_ns, st)
-                            : solve_typed<double, false>(n, Rd, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status,
+                            : solve_typed<double, false>(n, Rd, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status,
                                                          wait_limit_ns, st);
   }
   const float *Rf = static_cast<const float *>(R), *Rt = static_cast<const float *>(l.Rt);
   return lower_transposed
-             ? solve_typed<float, true>(n, Rf, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st)
-             : solve_typed<float, false>(n, Rf, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st);
+             ? solve_typed<float, true>(n, Rf, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st)
+             : solve_typed<float, false>(n, Rf, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st);
 }
 
 }  // namespace tqr
