@@ -50,9 +50,9 @@ __device__ __forceinline__ double ld_cg(const float *p) { return static_cast<dou
 
 // ---- set-up ---------------------------------------------------------------------------
 
-// Y[s] (kBig x kBig, column-major): the 64 x 64 inverses on the diagonal (identity for
-// 64-blocks beyond n), zeros elsewhere.
-__global__ void big_init_kernel(int64_t n, const double *Dinv64, double *Y, int nbig) {
+// Y[s] (kBig x kBig, column-major, FP32 pairs): the 64 x 64 inverses on the diagonal
+// (identity for 64-blocks beyond n), zeros elsewhere.
+__global__ void big_init_kernel(int64_t n, const double *Dinv64, float2 *Y, int nbig) {
   const int nblk64 = static_cast<int>((n + kSmall - 1) / kSmall);
   const int64_t total = static_cast<int64_t>(nbig) * kBig * kBig;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; idx < total;
@@ -68,33 +68,64 @@ __global__ void big_init_kernel(int64_t n, const double *Dinv64, double *Y, int 
       else
         v = r == c ? 1.0 : 0.0;
     }
-    Y[idx] = v;
+    float2 pv;
+    split_pair(v, pv.x, pv.y);
+    Y[idx] = pv;
   }
+}
+
+// Operator entries as FP32 pairs (hi, lo): an FP32 entry of R is (x, 0); an FP64 entry
+// is split (split_pair); a pair of the block inverses (stored as pairs) is itself.
+__device__ __forceinline__ float2 as_pair(float x) { return make_float2(x, 0.f); }
+__device__ __forceinline__ float2 as_pair(double x) {
+  float2 r;
+  split_pair(x, r.x, r.y);
+  return r;
+}
+__device__ __forceinline__ float2 as_pair(float2 x) { return x; }
+template <typename Mt> __device__ __forceinline__ Mt zero_of() { return Mt(0); }
+template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
+
+// acc (an unevaluated FP32 pair) += a * b for FP32 pairs a, b: the leading product exact
+// as p + e by an FMA, the cross terms added to the error, Knuth's TwoSum for the sum.
+__device__ __forceinline__ void df_mac(float2 &acc, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x);
+  const float t = acc.x + p;
+  const float bb = t - acc.x;
+  acc.y += ((acc.x - (t - bb)) + (p - bb)) + e;
+  acc.x = t;
 }
 
 // One doubling step at half-width h for every pair of every big block, in two products:
 //   stage 0: Tmp = Y11 R12        stage 1: Y12 = -Tmp Y22
 // Y11 = Y[s](p, p), Y22 = Y[s](p+h, p+h) (h x h, already inverses), R12 = R(p, p+h) of
-// big block s (zero beyond n), p = 2 h q.  32 x 32 output tile per CTA, 2 x 2 per thread:
-// both factors with an inverse are upper triangular (Y11(row, k) = 0 for k < row in
-// stage 0, Y22(k, col) = 0 for k > col in stage 1), so each tile's k range stops at the
-// triangle, and the small tiles spread the uneven ranges over all SMs.
+// big block s (zero beyond n), p = 2 h q; Y and Tmp hold FP32 pairs and the products run
+// in double-float arithmetic on the FP32 units (about 2^-44 relative per sum).  32 x 32
+// output tile per CTA, 2 x 2 per thread: both factors with an inverse are upper triangular
+// (Y11(row, k) = 0 for k < row in stage 0, Y22(k, col) = 0 for k > col in stage 1), so
+// each tile's k range stops at the triangle, and the small tiles spread the uneven ranges
+// over all SMs.
 template <typename Real>
-__global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *R, int64_t ldr, double *Y,
-                                                         double *Tmp, int h, int stage) {
+__global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *R, int64_t ldr, float2 *Y,
+                                                         float2 *Tmp, int h, int stage) {
   constexpr int kM = 32;
-  __shared__ double As[kM][kM + 1];
-  __shared__ double Bs[kM][kM + 1];
+  __shared__ float2 As[kM][kM + 1];
+  __shared__ float2 Bs[kM][kM + 1];
   const int tiles = h / kM;
   const int tr = blockIdx.x % tiles, tc = blockIdx.x / tiles;  // output tile
   const int q = blockIdx.y, s = blockIdx.z;
   const int p = 2 * h * q;
-  double *Ys = Y + static_cast<int64_t>(s) * kBig * kBig;
-  double *Tq = Tmp + (static_cast<int64_t>(s) * (kBig / (2 * h)) + q) * h * h;
+  float2 *Ys = Y + static_cast<int64_t>(s) * kBig * kBig;
+  float2 *Tq = Tmp + (static_cast<int64_t>(s) * (kBig / (2 * h)) + q) * h * h;
   const int64_t g0 = static_cast<int64_t>(s) * kBig;  // first row of the big block in R
   const int tid = threadIdx.x;
   const int ty = tid / 16, tx = tid % 16;
-  double acc[2][2] = {};
+  float2 acc[2][2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) acc[u][v] = make_float2(0.f, 0.f);
   const int k_lo = stage == 0 ? tr * kM : 0;
   const int k_hi = stage == 0 ? h : (tc * kM + kM < h ? tc * kM + kM : h);
   for (int k0 = k_lo; k0 < k_hi; k0 += kM) {
@@ -107,24 +138,24 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *
     for (int idx = tid; idx < kM * kM; idx += kThreads) {
       const int c = idx / kM, kk = idx % kM;
       const int col = tc * kM + c, k = k0 + kk;
-      double v;
+      float2 v;
       if (stage == 0) {
         const int64_t gr = g0 + p + k, gc = g0 + p + h + col;
-        v = (gr < n && gc < n) ? ld_cg(R + gr + gc * ldr) : 0.0;
+        v = (gr < n && gc < n) ? as_pair(__ldcg(R + gr + gc * ldr)) : make_float2(0.f, 0.f);
       } else {
         v = Ys[(p + h + k) + static_cast<int64_t>(p + h + col) * kBig];
       }
       Bs[kk][c] = v;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int kk = 0; kk < kM; ++kk) {
-      const double a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
-      const double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
+      const float2 a0 = As[ty * 2][kk], a1 = As[ty * 2 + 1][kk];
+      const float2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      df_mac(acc[0][0], a0, b0);
+      df_mac(acc[0][1], a0, b1);
+      df_mac(acc[1][0], a1, b0);
+      df_mac(acc[1][1], a1, b1);
     }
     __syncthreads();
   }
@@ -133,10 +164,13 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(int64_t n, const Real *
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
       const int row = tr * kM + ty * 2 + u, col = tc * kM + tx * 2 + v;
+      // renormalised pair (|lo| <= half an ulp of hi)
+      const float hi = acc[u][v].x + acc[u][v].y;
+      const float lo = acc[u][v].y - (hi - acc[u][v].x);
       if (stage == 0)
-        Tq[row + static_cast<int64_t>(col) * h] = acc[u][v];
+        Tq[row + static_cast<int64_t>(col) * h] = make_float2(hi, lo);
       else
-        Ys[(p + row) + static_cast<int64_t>(p + h + col) * kBig] = -acc[u][v];
+        Ys[(p + row) + static_cast<int64_t>(p + h + col) * kBig] = make_float2(-hi, -lo);
     }
 }
 
@@ -195,18 +229,6 @@ __device__ bool grid_barrier(int32_t *bar, int &gen, int32_t *status, int64_t li
   __syncthreads();
   return s_ok != 0;
 }
-
-// Operator entries as FP32 pairs (hi, lo): an FP32 entry of R is (x, 0); an FP64 entry
-// is split (split_pair); a pair of the block inverses (stored as pairs) is itself.
-__device__ __forceinline__ float2 as_pair(float x) { return make_float2(x, 0.f); }
-__device__ __forceinline__ float2 as_pair(double x) {
-  float2 r;
-  split_pair(x, r.x, r.y);
-  return r;
-}
-__device__ __forceinline__ float2 as_pair(float2 x) { return x; }
-template <typename Mt> __device__ __forceinline__ Mt zero_of() { return Mt(0); }
-template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
 
 // One warp's 32 x 64 tile of an operator, Op(i, c) for rows i0.. (i < ilim) and columns
 // c0.. (c < clim), staged in the warp's shared-memory slice as FP32 pairs st[c][i - i0]:
@@ -398,21 +420,8 @@ __global__ void __launch_bounds__(kThreads) big_trsv_kernel(int64_t n, const Rea
   }
 }
 
-// Y[i] (FP64) -> the FP32 pair (hi, lo) of the same value, in place (8 bytes either way;
-// each element is read and rewritten by one thread).
-__global__ void pairs_in_place(double *Y, int64_t count) {
-  float2 *P = reinterpret_cast<float2 *>(Y);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < count;
-       i += static_cast<int64_t>(gridDim.x) * kThreads) {
-    const double v = Y[i];
-    float2 r;
-    split_pair(v, r.x, r.y);
-    P[i] = r;
-  }
-}
-
 template <typename Real>
-int setup_typed(int64_t n, const Real *R, int64_t ldr, const double *Dinv64, double *Y, double *Tmp, Real *Rt,
+int setup_typed(int64_t n, const Real *R, int64_t ldr, const double *Dinv64, float2 *Y, float2 *Tmp, Real *Rt,
                 cudaStream_t st) {
   const int nbig = static_cast<int>((n + kBig - 1) / kBig);
   {
@@ -435,10 +444,7 @@ int setup_typed(int64_t n, const Real *R, int64_t ldr, const double *Dinv64, dou
       if ((e = cudaGetLastError()) != cudaSuccess) return static_cast<int>(e);
     }
   }
-  // the solves read the inverses as FP32 pairs, written over their FP64 values
-  pairs_in_place<<<1216, kThreads, 0, st>>>(Y, static_cast<int64_t>(nbig) * kBig * kBig);
-  count_launch();
-  return static_cast<int>(cudaGetLastError());
+  return 0;
 }
 
 template <typename Real, bool kLowerT>
@@ -482,17 +488,17 @@ size_t precond_work_doubles(int64_t n, bool real_is_double) {
 
 namespace {
 struct Layout {
-  double *Y, *Tmp, *xs;
-  const float2 *Yp;  // Y after the set-up: FP32 pairs in the same storage
+  float2 *Y, *Tmp;  // FP32 pairs (one double's storage each)
+  double *xs;
   void *Rt;
 };
 Layout layout(int64_t n, const double *work) {
   const size_t nbig = static_cast<size_t>((n + kBig - 1) / kBig);
   Layout l;
-  l.Y = const_cast<double *>(work);
-  l.Yp = reinterpret_cast<const float2 *>(work);
-  l.Tmp = l.Y + nbig * kBig * kBig;
-  l.xs = l.Tmp + nbig * (kBig / 2) * (kBig / 2);
+  double *w = const_cast<double *>(work);
+  l.Y = reinterpret_cast<float2 *>(w);
+  l.Tmp = reinterpret_cast<float2 *>(w + nbig * kBig * kBig);
+  l.xs = w + nbig * kBig * kBig + nbig * (kBig / 2) * (kBig / 2);
   l.Rt = l.xs + 2 * kBig * kRhsMax;
   return l;
 }
@@ -514,15 +520,15 @@ int precond_solve(int64_t n, const void *R, int64_t ldr, bool real_is_double, co
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (real_is_double) {
     const double *Rd = static_cast<const double *>(R), *Rt = static_cast<const double *>(l.Rt);
-    return lower_transposed ? solve_typed<double, true>(n, Rd, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status,
+    return lower_transposed ? solve_typed<double, true>(n, Rd, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status,
                                                         wait_limit_ns, st)
-                            : solve_typed<double, false>(n, Rd, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status,
+                            : solve_typed<double, false>(n, Rd, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status,
                                                          wait_limit_ns, st);
   }
   const float *Rf = static_cast<const float *>(R), *Rt = static_cast<const float *>(l.Rt);
   return lower_transposed
-             ? solve_typed<float, true>(n, Rf, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st)
-             : solve_typed<float, false>(n, Rf, ldr, Rt, l.Yp, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st);
+             ? solve_typed<float, true>(n, Rf, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st)
+             : solve_typed<float, false>(n, Rf, ldr, Rt, l.Y, B, ldb, nrhs, l.xs, bar, status, wait_limit_ns, st);
 }
 
 }  // namespace tqr
