@@ -890,7 +890,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
 // 0..127, C1^T added in FP32 while W's image is written);  P2 = Z2 (-W) (TMEM 128..255),
 // P1 = T^T (-W) (256..383);  C2 = C2_old + P2 (C2_old kept in TMEM 384..511), C1 = C1_old
 // + P1 (C1_old read again from global memory).  The first two products are issued in two
-// K halves like UNMQR's.
+// K halves like UNMQR's; with two operand buffers C2 is written while T^T arrives.
 __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int piv, int k,
                                 int j) {
   const TileGeom geo{p.m, p.n, kMNB};
@@ -964,7 +964,8 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   ms.ld_phase ^= 1;
   phase_mark(ms.ph, 2);
   if (!b.Zb) {
-    // Y held Z2: wait for that product, then bring T^T into Y
+    // Y held Z2: wait for that product, bring T^T into Y and write C2 (from P2 and the old
+    // tile, both in TMEM) while the copy is in flight; then P1 = -T^T W
     wait_or_flag(p, ms, ms.bar_mma, ms.mma_phase);
     ms.mma_phase ^= 1;
     umma::fence_after();
@@ -973,11 +974,12 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
     if (threadIdx.x == 0) {
       expect_loads(ms, b.bytes);
       umma::bulk_g2s(b.Y, imgT, b.bytes, ms.bar_ld);
-      if (wait_loads(p, ms)) {
-        umma::fence_after();
-        issue_product(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1);
-        umma::commit(ms.bar_mma);
-      }
+    }
+    tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 384);
+    if (threadIdx.x == 0 && wait_loads(p, ms)) {
+      umma::fence_after();
+      issue_product(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1);
+      umma::commit(ms.bar_mma);
     }
     ms.ld_phase ^= 1;
   }
@@ -986,7 +988,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   umma::fence_after();
   sync_all_tc();
   if (task_failed(ms)) return;
-  tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 384);
+  if (b.Zb) tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 384);
   tile_plus_tmem(C1, p.lda, kMNB, ncols, ms.tmem + 256, 0);
   sync_all_tc();
   phase_mark(ms.ph, 3);
