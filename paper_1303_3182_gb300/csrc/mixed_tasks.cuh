@@ -639,23 +639,13 @@ __device__ __forceinline__ void issue_product(uint32_t d_tmem, const unsigned ch
   issue_product_half(d_tmem, bufA, bufB, nparts, fmt, neg_b, acc, 1);
 }
 
-// Loads this thread's row r of a tile (half the columns, by warp group) and stores it
-// into TMEM at column base tcol (lane r).
-__device__ void tile_rows_to_tmem(const float *C, int64_t ldc, int nrows, int ncols, uint32_t tmem, uint32_t tcol) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = (warp & 3) * 32 + lane;
-  const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
-  for (int g = 0; g < 2; ++g) {
-    const int c0 = (warp >> 2) * 64 + g * 32;
-    float v[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = c0 + j;
-      v[j] = (r < nrows && c < ncols) ? __ldcg(C + r + static_cast<int64_t>(c) * ldc) : 0.f;
-    }
-    umma::tmem_st32(tmem + lane_base + tcol + c0, v);
+// L2 prefetch hints for the ncols 512-byte columns of a 128-row FP32 tile.
+__device__ __forceinline__ void prefetch_tile_l2(const float *C, int64_t ldc, int ncols) {
+  for (int c = threadIdx.x; c < ncols; c += kThreads) {
+    const char *col = reinterpret_cast<const char *>(C + static_cast<int64_t>(c) * ldc);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(col));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(col + 256));
   }
-  umma::tmem_wait_st();
 }
 
 // Split image of C^T (row c, k = r) in shared memory, K half h only (rows r of C in
@@ -817,7 +807,7 @@ __device__ __forceinline__ OperandBufs operand_bufs(unsigned char *raw, int npar
 }
 
 // UNMQR(i,k,j) on tensor cores:  W^T = C^T V (TMEM 0..127),  P = Z (-W) (TMEM 128..255),
-// C = C_old + P (C_old kept in TMEM 256..383, added in FP32).  Each product is issued in
+// C = C_old + P (C_old read again, from L2, and added in FP32).  Each product is issued in
 // two K halves: the MMAs of the first half run while the second half of its split operand
 // (C^T, then W) is being written.
 __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int k, int j) {
@@ -833,7 +823,7 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   }
   float *C = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  tile_rows_to_tmem(C, p.lda, mb, ncols, ms.tmem, 256);
+  prefetch_tile_l2(C, p.lda, ncols);  // read twice more: transposed for the image, then by the epilogue
   uint32_t acc = 0u;
   for (int h = 0; h < 2; ++h) {
     c_transposed_image(b.X, C, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
@@ -881,16 +871,16 @@ __device__ void task_unmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   umma::fence_after();
   sync_all_tc();
   if (task_failed(ms)) return;
-  tile_plus_tmem(C, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 256);
+  tile_plus_tmem(C, p.lda, mb, ncols, ms.tmem + 128, 0);
   sync_all_tc();
   phase_mark(ms.ph, 3);
 }
 
 // TTMQR(i,piv,k,j) / TSMQR (V2 dense):  W^T = C1^T + C2^T V2 (the product fresh in TMEM
 // 0..127, C1^T added in FP32 while W's image is written);  P2 = Z2 (-W) (TMEM 128..255),
-// P1 = T^T (-W) (256..383);  C2 = C2_old + P2 (C2_old kept in TMEM 384..511), C1 = C1_old
-// + P1 (C1_old read again from global memory).  The first two products are issued in two
-// K halves like UNMQR's; with two operand buffers C2 is written while T^T arrives.
+// P1 = T^T (-W) (256..383);  C2 = C2_old + P2, C1 = C1_old + P1 (the old tiles read again,
+// from L2, where the task's first step pulled them).  The first two products are issued in
+// two K halves like UNMQR's; with two operand buffers C2 is written while T^T arrives.
 __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedState &ms, int i, int piv, int k,
                                 int j) {
   const TileGeom geo{p.m, p.n, kMNB};
@@ -905,13 +895,10 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   float *C1 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, piv, j);
   float *C2 = tile_ptr(static_cast<float *>(p.A), p.lda, kMNB, i, j);
   const int mb = geo.rows(i), ncols = geo.cols(j);
-  // C1 is read twice more (transposed for W, then by the epilogue): pull it into L2 now
-  for (int c = threadIdx.x; c < ncols; c += kThreads) {
-    const char *col = reinterpret_cast<const char *>(C1 + static_cast<int64_t>(c) * p.lda);
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(col));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(col + 256));
-  }
-  tile_rows_to_tmem(C2, p.lda, mb, ncols, ms.tmem, 384);
+  // C2 and C1 are each read twice (transposed for the first product / W, then by the
+  // epilogue): pull them into L2 now
+  prefetch_tile_l2(C2, p.lda, ncols);
+  prefetch_tile_l2(C1, p.lda, ncols);
   uint32_t acc = 0u;
   for (int h = 0; h < 2; ++h) {
     c_transposed_image(b.X, C2, p.lda, mb, ncols, p.fmt, p.nparts, p.vec4 != 0, h);
@@ -975,7 +962,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
       expect_loads(ms, b.bytes);
       umma::bulk_g2s(b.Y, imgT, b.bytes, ms.bar_ld);
     }
-    tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 384);
+    tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, 0);
     if (threadIdx.x == 0 && wait_loads(p, ms)) {
       umma::fence_after();
       issue_product(ms.tmem + 256, b.Y, b.X, p.nparts, p.fmt, 1);
@@ -988,7 +975,7 @@ __device__ void task_ttmqr_umma(const ExecParams &p, unsigned char *raw, MixedSt
   umma::fence_after();
   sync_all_tc();
   if (task_failed(ms)) return;
-  if (b.Zb) tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, ms.tmem + 384);
+  if (b.Zb) tile_plus_tmem(C2, p.lda, mb, ncols, ms.tmem + 128, 0);
   tile_plus_tmem(C1, p.lda, kMNB, ncols, ms.tmem + 256, 0);
   sync_all_tc();
   phase_mark(ms.ph, 3);
