@@ -51,7 +51,7 @@ BF16_FALLBACK = (1900.0, 1700.0)
 # block (the tensor-core graph splits its TT / TS panels into 32-column block tasks, so the
 # whole-panel TTQRT / TSQRT weights do not occur in it).
 TENSOR_CLAIM_WEIGHTS = (265, 285, 20, 32, 320, 32, 66, 80, 85)
-TENSOR_TASK_MEAN_US = (219, 286, 23, 27, 270, 27, 72, 61, 70)
+TENSOR_TASK_MEAN_US = (217, 286, 21, 26, 270, 26, 72, 60, 69)
 
 
 def parse_args():
