@@ -274,17 +274,22 @@ __device__ void apply_block_f32(float *C, int ldc, int nrows, float *C1, int ldc
     const int a = tid & 31, g = tid >> 5;
     float nw[4] = {0.f, 0.f, 0.f, 0.f};
     if (a < kb) {
+      // the four columns' sums advance together (one T load, four independent FMA chains
+      // per step); each sum still runs over b in order.  Columns beyond ncols read
+      // unused slots of red and are not stored.
+      const float *r0 = red + g * 33;
+      if (!transpose_q) {
+        for (int b = 0; b <= a; ++b) {
+          const float t = T[b + a * ldt];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = g + kWarps * u;
-        if (c >= ncols) continue;
-        float sum = 0.f;
-        if (!transpose_q) {
-          for (int b = 0; b <= a; ++b) sum += T[b + a * ldt] * red[b + c * 33];
-        } else {
-          for (int b = a; b < kb; ++b) sum += T[a + b * ldt] * red[b + c * 33];
+          for (int u = 0; u < 4; ++u) nw[u] += t * r0[b + kWarps * 33 * u];
         }
-        nw[u] = sum;
+      } else {
+        for (int b = a; b < kb; ++b) {
+          const float t = T[a + b * ldt];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) nw[u] += t * r0[b + kWarps * 33 * u];
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -311,6 +316,7 @@ __device__ void apply_block_f32(float *C, int ldc, int nrows, float *C1, int ldc
       int rr[NX];
 #pragma unroll
       for (int x = 0; x < NX; ++x) rr[x] = min(rt + 64 * x, nrows - 1);
+#pragma unroll 4
       for (int b = 0; b < kb; ++b) {
         const float4 w0 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg);
         const float4 w1 = *reinterpret_cast<const float4 *>(Wv + b * kWvLd + 8 * cg + 4);
