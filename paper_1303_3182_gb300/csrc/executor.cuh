@@ -234,7 +234,7 @@ __device__ void apply_block_f32(float *C, int ldc, int nrows, float *C1, int ldc
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
     for (int r = rg; r < nrows; r += 4) {
       float v[4], c[4];
 #pragma unroll
@@ -770,23 +770,35 @@ __device__ void panel_factor_dispatch(Smem<S> &s, int kb, int rows, int c0, int 
 // Gram matrix G(a, c) = v_a . v_c (a < c < kb) of a panel block's reflectors, held
 // explicitly in s.V (GEQRT: unit diagonal and zeros above written in; TT: zeros below
 // the triangle from the load).  Only the strict upper triangle is formed - the T
-// recurrence reads nothing else - one pair per thread step, a fastest within a column c
-// (a warp's V(r, a) loads hit distinct banks, its V(r, c) loads broadcast); each sum runs
-// over the rows in order.
+// recurrence reads nothing else - pair idx by thread idx mod kThreads, a fastest within a
+// column c (a warp's V(r, a) loads hit distinct banks, its V(r, c) loads broadcast); each
+// sum runs over the rows in order.
 template <typename S>
 __device__ void panel_gram(Smem<S> &s, int kb, int nrows) {
   const int npairs = kb * (kb - 1) / 2;
-  for (int idx = threadIdx.x; idx < npairs; idx += kThreads) {
-    // column c holds the pairs c (c - 1) / 2 .. c (c + 1) / 2 - 1
-    int c = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(idx))) * 0.5f);
+  // column c holds the pairs c (c - 1) / 2 .. c (c + 1) / 2 - 1
+  auto pair_of = [](int idx, int &a, int &c) {
+    c = static_cast<int>((1.0f + sqrtf(1.0f + 8.0f * static_cast<float>(idx))) * 0.5f);
     while (c * (c - 1) / 2 > idx) --c;
     while (c * (c + 1) / 2 <= idx) ++c;
-    const int a = idx - c * (c - 1) / 2;
-    const S *va = s.V + a * s.ldv, *vc = s.V + c * s.ldv;
-    S acc = 0;
+    a = idx - c * (c - 1) / 2;
+  };
+  // a thread's two pairs (idx and idx + kThreads) advance together: two independent sums
+  for (int idx = threadIdx.x; idx < npairs; idx += 2 * kThreads) {
+    const bool two = idx + kThreads < npairs;
+    int a0, c0, a1, c1;
+    pair_of(idx, a0, c0);
+    pair_of(two ? idx + kThreads : idx, a1, c1);
+    const S *va0 = s.V + a0 * s.ldv, *vc0 = s.V + c0 * s.ldv;
+    const S *va1 = s.V + a1 * s.ldv, *vc1 = s.V + c1 * s.ldv;
+    S acc0 = 0, acc1 = 0;
 #pragma unroll 4
-    for (int r = 0; r < nrows; ++r) acc += va[r] * vc[r];
-    s.G[a + c * s.ldt] = acc;
+    for (int r = 0; r < nrows; ++r) {
+      acc0 += va0[r] * vc0[r];
+      acc1 += va1[r] * vc1[r];
+    }
+    s.G[a0 + c0 * s.ldt] = acc0;
+    if (two) s.G[a1 + c1 * s.ldt] = acc1;
   }
   __syncthreads();
 }
