@@ -1245,11 +1245,11 @@ __global__ void __launch_bounds__(kThreads, 1) executor_kernel(ExecParams p) {
         if (kMixed) task_pairqrt_split<true>(q, smem_raw, s.ph, task.i, task.piv, task.k, task.j);
         break;
       case kPrepG:  // tensor-core graphs only: the operand images of GEQRT(i,k)
-        if (kMixed) prep_geqrt_ops(q, smem_raw, task.i, task.k);
+        if (kMixed) prep_geqrt_ops(q, smem_raw, s.ph, task.i, task.k);
         phase_mark(s.ph, 3);
         break;
       case kPrepT:  // ... of the TTQRT (piv >= 0 and tile upper part) or TSQRT that zeroed (i,k)
-        if (kMixed) prep_ttqrt_ops(q, smem_raw, task.i, task.k, task.j != 0);
+        if (kMixed) prep_ttqrt_ops(q, smem_raw, s.ph, task.i, task.k, task.j != 0);
         phase_mark(s.ph, 3);
         break;
       case kUnmqr: {

@@ -131,6 +131,14 @@ __device__ void write_image(unsigned char *img, F get, int fmt, int nparts) {
   });
 }
 
+// The column group of warp w in V T^T: groups g and 7 - g (long and short ranges of the
+// triangular T) go to warps g and g + 4, which share a scheduler, so every scheduler gets
+// the same work.
+__device__ __forceinline__ int prep_group(int warp) {
+  static_assert(kWarps == 8, "eight warps, eight 16-column groups");
+  return warp < 4 ? warp : 11 - warp;
+}
+
 // G(a, c) = sum_r V(r, a) V(r, c) for a < c.  Thread (warp w, lane l) forms rows
 // a = l + 32x (x < 4) of columns c = 16w .. 16w+15: the V(r, a) loads of a warp hit
 // consecutive words, the V(r, c) loads are broadcasts.  range(c_lo, r0, r1) bounds r.
@@ -145,6 +153,7 @@ __device__ void gram_upper(float *G, const float *V, RowRange range) {
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 16; ++y) acc[x][y] = 0.f;
+#pragma unroll 2
   for (int r = r0; r < r1; ++r) {
     float va[4], vc[16];
 #pragma unroll
@@ -180,6 +189,7 @@ __device__ void assemble_t(float *Ts, float *Gs, int ib) {
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 4
     for (int b = 0; b < w; ++b) {
       float g[4], t[4];
 #pragma unroll
@@ -208,6 +218,7 @@ __device__ void assemble_t(float *Ts, float *Gs, int ib) {
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 4
     for (int b = 0; b < c0; ++b) {
       float t[4], xv[4];
 #pragma unroll
@@ -235,11 +246,12 @@ __device__ void assemble_t(float *Ts, float *Gs, int ib) {
 }
 
 // Z(r, a) = sum_b V(r, b) T(a, b) (= V T^T).  Thread (warp w, lane l) forms rows
-// r = l + 32x of columns a = 16w .. 16w+15; bounds(a_lo, b0, b1) limits b.
+// r = l + 32x of the columns a of its warp's 16-column group; bounds(a_lo, b0, b1)
+// limits b.
 template <typename Bounds>
 __device__ void v_times_tt(float *Z, const float *V, const float *Ts, Bounds bounds) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ab = warp * 16;
+  const int ab = prep_group(warp) * 16;
   int b0, b1;
   bounds(ab, b0, b1);
   float acc[4][16];
@@ -247,6 +259,7 @@ __device__ void v_times_tt(float *Z, const float *V, const float *Ts, Bounds bou
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 16; ++y) acc[x][y] = 0.f;
+#pragma unroll 2
   for (int b = b0; b < b1; ++b) {
     float vr[4], tt[16];
 #pragma unroll
@@ -296,7 +309,7 @@ __device__ void load_t_blocks(float *Ts, const float *Tg, int ib) {
 }
 
 // Operand images of GEQRT(i,k): V and Z = V T_full^T.
-__device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, int k) {
+__device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, uint64_t *ph, int i, int k) {
   const TileGeom geo{p.m, p.n, kMNB};
   float *Vs = reinterpret_cast<float *>(raw);
   float *Ts = Vs + kMNB * kMLD;
@@ -310,13 +323,16 @@ __device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   });
   load_t_blocks(Ts, Tg, p.ib);
   __syncthreads();
+  phase_mark(ph, 0);  // trace phases: 0 loads, 1 Gram and T_full, 2 Z, 3 the images
   // G(a, c) = v_a . v_c over rows r >= c (v_c is zero above its diagonal)
   gram_upper(Gs, Vs, [](int c_lo, int &r0, int &r1) { r0 = c_lo; r1 = kMNB; });
   __syncthreads();
   assemble_t(Ts, Gs, p.ib);
+  phase_mark(ph, 1);
   // Z = V T^T: Z(r, a) = sum_{a <= b <= r} V(r, b) T(a, b)
   v_times_tt(Gs, Vs, Ts, [](int a_lo, int &b0, int &b1) { b0 = a_lo; b1 = kMNB; });
   __syncthreads();
+  phase_mark(ph, 2);
   unsigned char *slot = ops_slot(p, i, k, 0);
   const int np = p.nparts;
   write_image(slot, [&](int row, int kk) { return Vs[kk + row * kMLD]; }, p.fmt, np);
@@ -326,7 +342,7 @@ __device__ void prep_geqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
 
 // Operand images of TTQRT(i,piv,k): V2 (upper part of tile i), Z2 = V2 T_full^T, T_full^T.
 // ts: of TSQRT(i,piv,k), whose V2 is the whole tile i (Algorithm "elimSQ").
-__device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, int k, bool ts) {
+__device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, uint64_t *ph, int i, int k, bool ts) {
   const TileGeom geo{p.m, p.n, kMNB};
   float *Vs = reinterpret_cast<float *>(raw);
   float *Ts = Vs + kMNB * kMLD;
@@ -339,6 +355,7 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
   });
   load_t_blocks(Ts, Tt, p.ib);
   __syncthreads();
+  phase_mark(ph, 0);
   // G(a, c) = v_a . v_c over the rows the tails occupy (TT: r <= a, within the upper
   // triangle; TS: every row)
   if (ts)
@@ -347,9 +364,11 @@ __device__ void prep_ttqrt_ops(const ExecParams &p, unsigned char *raw, int i, i
     gram_upper(Gs, Vs, [](int c_lo, int &r0, int &r1) { r0 = 0; r1 = min(c_lo + 16, kMNB); });
   __syncthreads();
   assemble_t(Ts, Gs, p.ib);
+  phase_mark(ph, 1);
   // Z2(r, a) = sum_{b >= a} V2(r, b) T(a, b)
   v_times_tt(Gs, Vs, Ts, [](int a_lo, int &b0, int &b1) { b0 = a_lo; b1 = kMNB; });
   __syncthreads();
+  phase_mark(ph, 2);
   unsigned char *slot = ops_slot(p, i, k, 1);
   const int np = p.nparts;
   write_image(slot, [&](int row, int kk) { return Vs[kk + row * kMLD]; }, p.fmt, np);

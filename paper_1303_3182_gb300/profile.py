@@ -11,7 +11,8 @@ repetition records the executor's per-task stamps (tqr_set_trace) and writes the
 list of {kind, i, piv, k, j, sm, start_us, end_us, phases_us} records - a Gantt chart of
 the task graph.  phases_us: four time slots of the task - panel tasks: panel, T, in-tile
 trailing update (summed over ib-blocks) and the resident tiles' loads; tensor-core updates:
-the first product with its operand images, its wait, the second product(s), the epilogue.
+the first product with its operand images, its wait, the second product(s), the epilogue;
+operand preparation: loads, Gram matrix and T_full, Z = V T_full^T, the split images.
 --batch N: one batched launch (tqr_batch_plan_run, built-in size classes) over the
 first N matrices of the 2048-matrix distribution (rows uniform in [256, 8192], columns
 in {32, 64, 128, 256}).
