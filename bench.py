@@ -37,11 +37,11 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BATCH_COUNT = 2048
 # DRAM bytes (read + write) per nominal flop of the two executors, from one ncu capture
 # each of the unchanged kernels on smaller inputs of the same kind (the tensor-core
-# executor, PlasmaTree-TS(16), on a 24576 x 2048 matrix: 7.522 GB for 2.004e11 nominal
+# executor, PlasmaTree-TS(16), on a 24576 x 2048 matrix: 7.527 GB for 2.004e11 nominal
 # flops, traffic growing with the number of tile updates as the flops do; the batched FP32
-# executor on the first 256 matrices of the batch: 1.321 GB for 4.907e10 flops).
-MIXED_TRAFFIC_PER_FLOP = 7.522e9 / 2.004e11
-BATCH_TRAFFIC_PER_FLOP = 1.321e9 / 4.907e10
+# executor on the first 256 matrices of the batch: 1.317 GB for 4.907e10 flops).
+MIXED_TRAFFIC_PER_FLOP = 7.527e9 / 2.004e11
+BATCH_TRAFFIC_PER_FLOP = 1.317e9 / 4.907e10
 BF16_FALLBACK = (1900.0, 1700.0)
 # Kernel weights of the library's default claim order for the tensor-core precisions
 # (tqr_set_claim_order mode 2 at nb 128, bf16x6: measured task durations with tuned panel
@@ -51,7 +51,7 @@ BF16_FALLBACK = (1900.0, 1700.0)
 # block (the tensor-core graph splits its TT / TS panels into 32-column block tasks, so the
 # whole-panel TTQRT / TSQRT weights do not occur in it).
 TENSOR_CLAIM_WEIGHTS = (265, 285, 20, 32, 320, 32, 66, 80, 85)
-TENSOR_TASK_MEAN_US = (217, 286, 21, 26, 270, 26, 72, 60, 69)
+TENSOR_TASK_MEAN_US = (205, 286, 22, 26, 270, 26, 62, 57, 67)
 
 
 def parse_args():
