@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kT) gemv_n_pairs(int64_t m, int64_t n, const f
 // in chunks of kTChunk rows, read from L2 once per CTA instead of once per warp; each lane
 // then takes two rows per float4 of A (m even and 16-byte aligned pair arrays: vec), else
 // one row per load.
-constexpr int kTChunk = 2048;
+constexpr int kTChunk = 4096;
 __global__ void __launch_bounds__(kT) gemv_t_pairs(int64_t m, int64_t n, const float2 *__restrict__ P,
                                                    const float2 *__restrict__ Up, double *Y, int64_t ldy, int nrhs,
                                                    const double *scale, int vec) {
@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(kT) gemv_t_pairs(int64_t m, int64_t n, const f
       if (vec) {
         const float4 *c4 = reinterpret_cast<const float4 *>(c);
         const float4 *w4 = reinterpret_cast<const float4 *>(us);
+#pragma unroll 2
         for (; i + 256 <= len; i += 256) {
           float4 a[4], w[4];
 #pragma unroll
