@@ -45,9 +45,6 @@ __device__ __forceinline__ int ld_acq(const int32_t *p) {
   return v;
 }
 
-__device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
-__device__ __forceinline__ double ld_cg(const float *p) { return static_cast<double>(__ldcg(p)); }
-
 // ---- set-up ---------------------------------------------------------------------------
 
 // Y[s] (kBig x kBig, column-major, FP32 pairs): the 64 x 64 inverses on the diagonal
